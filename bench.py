@@ -1,0 +1,401 @@
+#!/usr/bin/env python3
+"""Benchmark of the MCL particle-weight update on one GB300 per process.
+
+A step is one MCL iteration of the full-update workload (600 particles x 64
+shared pixels of a 400x400 observation, focal 555.6, 64 stratified + 128
+importance samples per ray, Eq. 5 uncertainty, Eq. 6 rejection weights, FP64
+normalisation, systematic resampling, the motion model and the position
+spread of the refinement test).  The metric is ray-samples per second
+(rays x composited samples / time) with the MCL-update milliseconds, for the
+selected MLP precision, next to the plain FP32 GPU form on the same box.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--precision P]
+                [--impl ours|reference]
+Under torchrun every rank localises its own query (its own seed): weak
+scaling, no data-path collective.  Rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WL = dict(workload="full update: 600 particles x 64 px of 400x400, 64+128 samples/ray",
+          N=600, B=64, W=400, H=400, focal=555.6, n_coarse=64, n_fine=128, level=2,
+          sigma_t=0.05, sigma_yaw=0.05, map_seed=0)
+MAC_PER_SAMPLE_FP32 = 593408   # unfused MLP: 8 trunk layers, sigma, feature, rgb head
+METRIC = "MCL update ms and ray-samples/s vs plain FP32 GPU form, at stated pose/RGB error"
+UNIT = "ray-samples/s"
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+            "sm_max_mhz": 2070.0}, "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100", "-i", gpu_id], stdout=self.tmp, stderr=subprocess.DEVNULL)
+        except (OSError, ValueError):
+            self.proc = None
+        self.t0 = self.t1 = None
+
+    def mark_start(self):
+        self.t0 = time.time()
+
+    def mark_end(self):
+        self.t1 = time.time()
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.tmp.flush()
+        self.tmp.seek(0)
+        rows = []
+        for line in self.tmp.read().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 10:
+                continue
+            try:
+                ts = time.mktime(time.strptime(parts[0].split(".")[0], "%Y/%m/%d %H:%M:%S"))
+                frac = float("0." + parts[0].split(".")[1]) if "." in parts[0] else 0.0
+                rows.append((ts + frac, float(parts[2]), float(parts[3]), parts[6:10]))
+            except ValueError:
+                continue
+        os.unlink(self.tmp.name)
+        inside = [r for r in rows if self.t0 is not None and self.t0 - 0.15 <= r[0] <= self.t1 + 0.15]
+        use = inside if inside else rows[-3:]
+        if not use:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({n for r in use for n, v in zip(names, r[3]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[1] for r in use), "sm_max_mhz": max(r[2] for r in use),
+                "reasons": reasons, "samples": len(use), "in_timed_region": bool(inside)}
+
+
+# --------------------------------------------------------------- CPU oracle
+def oracle_rate(n_particles: int, seed: int = 0):
+    """Time the FP64 oracle on n_particles x B pixels of the workload (synthetic
+    observation).  Returns (ray-samples/s, seconds, threads)."""
+    import numpy as np
+    import oracle
+    import synth
+    wl = WL
+    blob = synth.he_init_weights(wl["map_seed"])
+    P = synth.random_particles(seed, wl["N"])[0][:n_particles].astype(np.float32).astype(np.float64)
+    img = synth.smooth_image(seed, wl["W"], wl["H"]).astype(np.float64)
+    px = synth.pixel_set(seed, wl["W"], wl["H"], wl["B"])
+    f = float(np.float32(wl["focal"]))
+    K4 = (f, f, wl["W"] / 2, wl["H"] / 2)
+    opts = oracle.make_opts(n_coarse=wl["n_coarse"], n_fine=wl["n_fine"])
+    t = time.perf_counter()
+    oracle.update(blob, P, img, K4, 1, px, opts)
+    dt = time.perf_counter() - t
+    rs = n_particles * wl["B"] * (wl["n_coarse"] + wl["n_fine"])
+    return rs / dt, dt, oracle.num_threads()
+
+
+def cpu_baseline(target_s: float = 15.0):
+    r1, dt1, thr = oracle_rate(1)
+    n = max(1, min(WL["N"], int(target_s / max(dt1, 1e-3))))
+    rate, dt, thr = oracle_rate(n)
+    return {"value": rate, "unit": UNIT, "cores": thr, "kind": "oracle",
+            "sample": f"{n} of {WL['N']} particles x {WL['B']} px x "
+                      f"{WL['n_coarse'] + WL['n_fine']} samples ({dt:.1f} s, FP64 C + OpenMP)"}
+
+
+def run_reference(args):
+    """The oracle as it stands, timed on the host cores: each step is a bounded
+    sample (4 particles) of the workload."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    n = 4
+    for _ in range(args.warmup):
+        oracle_rate(n)
+    times = []
+    for k in range(args.steps):
+        rate, dt, thr = oracle_rate(n, seed=k)
+        times.append(dt)
+    rs = n * WL["B"] * (WL["n_coarse"] + WL["n_fine"])
+    value = rs * len(times) / sum(times)
+    sample = f"{n} of {WL['N']} particles x {WL['B']} px per step"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WL["workload"], "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": thr, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------- GPU arm
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2406_12202_gb300 import build as B
+    B.build()
+    import paper_2406_12202_gb300 as M
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    wl = WL
+    N, Bpx, W, H = wl["N"], wl["B"], wl["W"], wl["H"]
+    ns = wl["n_coarse"] + wl["n_fine"]
+    prec = args.precision
+    if prec == "auto":
+        prec = "bf16" if getattr(M, "HAS_TC", False) else "fp32"
+
+    blob = synth.he_init_weights(wl["map_seed"])
+    gm = M.Map(blob, max_rays=N * Bpx, max_samples=ns, max_particles=N)
+    K = M.intrinsics(wl["focal"], wl["focal"], W / 2, H / 2, W, H)
+    opts = M.UpdateOptions(n_coarse=wl["n_coarse"], n_fine=wl["n_fine"], precision=prec)
+    opts32 = M.UpdateOptions(n_coarse=wl["n_coarse"], n_fine=wl["n_fine"], precision="fp32")
+
+    # query of this rank: particles, ground truth, observation rendered at GT
+    seed = 1000 + rank
+    P0 = torch.tensor(synth.random_particles(seed, N)[0], dtype=torch.float32, device=dev)
+    gt = torch.tensor(synth.gt_pose(seed)[0][None], dtype=torch.float32, device=dev)
+    allpx = np.stack(np.meshgrid(np.arange(W), np.arange(H), indexing="xy"), -1).reshape(-1, 2)
+    img = torch.empty(H * W, 3, device=dev)
+    chunk = N * Bpx
+    for c0 in range(0, H * W, chunk):
+        pc = torch.tensor(allpx[c0:c0 + chunk], dtype=torch.int32, device=dev)
+        img[c0:c0 + pc.shape[0]] = gm.render(gt, K, 2, pc, opts32)
+    img = img.reshape(H, W, 3).contiguous()
+    n_sets = args.warmup + args.steps + 2
+    pxs = torch.tensor(np.stack([synth.pixel_set(seed + 7 * t, W, H, Bpx) for t in range(n_sets)]),
+                       dtype=torch.int32, device=dev)
+    u0s = [synth.resample_u0(seed + t) for t in range(n_sets)]
+
+    P = P0.clone()
+    P_next = torch.empty_like(P)
+    out = dict(logw=torch.empty(N, device=dev), w=torch.empty(N, dtype=torch.float64, device=dev),
+               mask=torch.empty(N, dtype=torch.uint8, device=dev))
+    idx = torch.empty(N, dtype=torch.int32, device=dev)
+    spread = torch.empty(4, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step(t, o, Pin, Pout):
+        gm.update(Pin, img, K, wl["level"], pxs[t], o, out=out)
+        gm.resample(out["w"], N, u0s[t], idx=idx)
+        M.predict(Pin, idx, N, wl["sigma_t"], wl["sigma_yaw"], seed, t, out=Pout)
+        M.position_spread(Pout, out=spread)
+
+    def timed(o, steps, warmup, profile=False, clocks=None):
+        nonlocal P, P_next
+        P.copy_(P0)
+        for t in range(warmup):
+            step(t, o, P, P_next)
+            P, P_next = P_next, P
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        if profile:
+            gm.profile_read(reset=True)
+            gm.profile(True)
+        _, l0 = gm.profile_read(reset=False)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(steps)]
+        if clocks:
+            clocks.mark_start()
+        for k in range(steps):
+            flush.zero_()
+            evs[k][0].record()
+            step(warmup + k, o, P, P_next)
+            evs[k][1].record()
+            P, P_next = P_next, P
+        torch.cuda.synchronize()
+        if clocks:
+            clocks.mark_end()
+        ms = [a.elapsed_time(b) for a, b in evs]
+        phases, l1 = gm.profile_read(reset=True)
+        gm.profile(False)
+        return ms, phases, l1 - l0
+
+    gpu_id = os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0] or str(local)
+    clocks = ClockSampler(gpu_id) if rank == 0 else None
+    ms, phases, launches = timed(opts, args.steps, args.warmup, profile=True, clocks=clocks)
+    clk = clocks.stop() if clocks else None
+    total_s = sum(ms) / 1e3
+    units = N * Bpx * ns * args.steps
+    tmax = total_s
+    units_all = units
+    if dist is not None:
+        t = torch.tensor([total_s], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tmax = float(t.item())
+        u = torch.tensor([float(units)], dtype=torch.float64, device=dev)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+        units_all = float(u.item())
+    value = units_all / tmax
+
+    # plain FP32 GPU form on the same box (comparison the metric names)
+    fp32 = None
+    if prec != "fp32":
+        ms32, ph32, _ = timed(opts32, max(2, min(args.steps, 5)), 1, profile=True)
+        fp32 = {"ms_per_step": sum(ms32) / len(ms32),
+                "ray_samples_per_s": N * Bpx * ns * len(ms32) / (sum(ms32) / 1e3),
+                "mlp_ms_per_step": (ph32["mlp_coarse"] + ph32["mlp_fine"]) / len(ms32)}
+
+    # end to end through the public API with host buffers (pinned)
+    hP = P0.cpu().pin_memory()
+    himg = img.cpu().pin_memory()
+    hpx = pxs.cpu().pin_memory()
+    hw = torch.empty(N, dtype=torch.float64).pin_memory()
+    hmask = torch.empty(N, dtype=torch.uint8).pin_memory()
+    hidx = torch.empty(N, dtype=torch.int32).pin_memory()
+    hP_out = torch.empty(N, 12, dtype=torch.float32).pin_memory()
+    dP = torch.empty_like(P0)
+    dimg = torch.empty_like(img)
+    dpx = torch.empty(Bpx, 2, dtype=torch.int32, device=dev)
+    bi = hP.numel() * 4 + himg.numel() * 4 + Bpx * 2 * 4
+    bo = N * 8 + N + N * 4 + N * 12 * 4
+    e2e_ms = []
+    for k in range(args.warmup + args.steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        dP.copy_(hP, non_blocking=True)
+        dimg.copy_(himg, non_blocking=True)
+        dpx.copy_(hpx[k], non_blocking=True)
+        gm.update(dP, dimg, K, wl["level"], dpx, opts, out=out)
+        gm.resample(out["w"], N, u0s[k], idx=idx)
+        M.predict(dP, idx, N, wl["sigma_t"], wl["sigma_yaw"], seed, k, out=P_next)
+        hw.copy_(out["w"], non_blocking=True)
+        hmask.copy_(out["mask"], non_blocking=True)
+        hidx.copy_(idx, non_blocking=True)
+        hP_out.copy_(P_next, non_blocking=True)
+        b.record()
+        torch.cuda.synchronize()
+        if k >= args.warmup:
+            e2e_ms.append(a.elapsed_time(b))
+    e2e_t = sum(e2e_ms) / 1e3
+    if dist is not None:
+        t = torch.tensor([e2e_t], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_t = float(t.item())
+    e2e_value = units_all / e2e_t
+
+    if rank != 0:
+        if dist is not None:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+
+    # roofline of the dominant kernel (the NeRF MLP)
+    peaks, peak_src = load_peaks()
+    mlp_ms = (phases["mlp_coarse"] + phases["mlp_fine"]) / args.steps
+    rows = N * Bpx * ns
+    if prec == "fp32":
+        flops = 2.0 * MAC_PER_SAMPLE_FP32 * rows
+        peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        roof = {"bound": "alu", "achieved": flops / (mlp_ms / 1e3) / 1e12, "peak": peak,
+                "unit": "TFLOP/s", "peak_source": f"152 SMs x 128 FP32 lanes x 2 x "
+                f"{peaks.get('sm_max_mhz', 2070.0):.0f} MHz ({peak_src} clock)"}
+    else:
+        flops = 2.0 * M.TC_MAC_PER_SAMPLE * rows
+        peak = peaks["bf16_tflops"] * (2.0 if prec == "fp8" else 1.0)
+        roof = {"bound": "tensor", "achieved": flops / (mlp_ms / 1e3) / 1e12, "peak": peak,
+                "unit": "TFLOP/s", "peak_source": f"bf16_tflops burst ({peak_src})"
+                + (" x 2 nominal fp8/bf16 ratio" if prec == "fp8" else "")}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = None
+    roof["kernel"] = "NeRF MLP (coarse + fine passes)"
+    roof["mlp_ms_per_step"] = mlp_ms
+
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        try:
+            cpu = cpu_baseline()
+        except Exception as e:  # the baseline must never hide the GPU line
+            cpu = {"value": None, "unit": UNIT, "cores": None, "kind": "oracle",
+                   "sample": f"failed: {e}"}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": sum(ms) / len(ms), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp32": "f32", "bf16": "bf16", "fp8": "fp8"}[prec], "data": "synthetic",
+        "config": {"workload": wl["workload"], "particles": N, "pixels": Bpx,
+                   "image": f"{W}x{H}", "samples_per_ray": f"{wl['n_coarse']}+{wl['n_fine']}",
+                   "mlp_precision": prec, "l2": "flushed (256 MB write) between timed steps",
+                   "step": "update + resample + predict + position spread",
+                   "parallelism": f"replicas x{world} (one query per GPU)"},
+        "update_ms": sum(ms) / len(ms),
+        "phases_ms_per_step": {k: v / args.steps for k, v in phases.items()},
+        "fp32_form": fp32,
+        "speedup_vs_fp32_form": (fp32["ms_per_step"] / (sum(ms) / len(ms))) if fp32 else 1.0,
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": bi,
+                "d2h_bytes_per_step": bo, "ms_per_step": 1e3 * e2e_t / args.steps},
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--precision", choices=("auto", "fp32", "bf16", "fp8"), default="auto")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,212 @@
+/*
+ * mcl.h -- C ABI of the GB300 (sm_103a) library for the particle-weight update
+ * of Fast Loc-NeRF Monte Carlo localisation (Kong, Lee, Lee, Kim, "Fast Global
+ * Localization on Neural Radiance Field", arXiv 2406.12202).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Pointers named d_* are DEVICE memory owned by the caller (for example
+ *   torch CUDA tensors); the library never frees them.  Host pointers are read
+ *   before the call returns and may be reused immediately.
+ * - Calls are asynchronous on the CUDA stream passed as `stream` (a
+ *   cudaStream_t; NULL = the legacy default stream).  Results are valid once
+ *   that stream has reached the point of the call.
+ * - Return value: MCL_OK (0) or a negative MCL_ERR_* code; mcl_last_error()
+ *   returns a message for the calling thread.  No C++ exception crosses the
+ *   boundary.  Argument checks happen on the host before anything is
+ *   launched; problems only the device can see (non-finite inputs, degenerate
+ *   weights) are recorded in a per-map status word (mcl_read_status).
+ * - The library allocates device memory only in mcl_init_map (weights and a
+ *   workspace sized by mcl_map_config) and frees it in mcl_destroy_map.
+ * - Every floating-point array is row-major and tightly packed.
+ * - A map may be used by one stream at a time (the workspace is shared).
+ */
+#ifndef MCL_H
+#define MCL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MCL_OK 0
+#define MCL_ERR_ARG (-1)        /* bad argument: shape, level, null, range   */
+#define MCL_ERR_CUDA (-2)       /* a CUDA runtime call failed                */
+#define MCL_ERR_NONFINITE (-3)  /* (status word) non-finite particle loss    */
+#define MCL_ERR_TIMEOUT (-4)    /* (status word) bounded device wait expired */
+#define MCL_ERR_UNSUPPORTED (-5)/* configuration this build does not serve  */
+#define MCL_ERR_DEGENERATE (-6) /* (status word) resampling weights all zero */
+
+typedef struct mcl_map mcl_map;
+
+/* NeRF MLP of the "basic NeRF model" (Sec. IV-A): positional encoding with
+ * n_freq_xyz / n_freq_dir frequencies, a trunk of trunk_depth ReLU layers of
+ * trunk_width units with gamma(x) concatenated after layer skip_layer, a
+ * density head, a linear feature layer, and an RGB head of rgb_width ReLU
+ * units fed with [feature, gamma(d)].  This build serves (10, 4, 8, 256, 5,
+ * 128) and rejects other shapes with MCL_ERR_UNSUPPORTED. */
+typedef struct {
+    int n_freq_xyz, n_freq_dir, trunk_depth, trunk_width, skip_layer, rgb_width;
+} mcl_arch;
+
+/* Workspace bounds fixed at map creation. */
+typedef struct {
+    int max_rays;      /* largest N * B of any mcl_update / mcl_render call   */
+    int max_samples;   /* largest n_coarse + n_fine                           */
+    int max_particles; /* largest particle count of mcl_update / mcl_resample */
+} mcl_map_config;
+
+/* Pinhole intrinsics K at FULL resolution (Eq. 4, "shared intrinsic camera
+ * parameter K").  Level l uses R K with R = 2^(l - 2): focal length and
+ * principal point divided by 4, 2, 1 for levels 0, 1, 2 (Alg. 1, "R_t K"). */
+typedef struct {
+    float fx, fy, cx, cy;
+    int width, height;
+} mcl_intrinsics;
+
+enum { MCL_PREC_FP32 = 0, MCL_PREC_BF16 = 1, MCL_PREC_FP8 = 2 };
+
+/* Options of one weight update. */
+typedef struct {
+    int n_coarse;       /* stratified samples per ray, 2..256                */
+    int n_fine;         /* importance samples per ray, 0..256 (0: none)      */
+    int precision;      /* MCL_PREC_*: arithmetic of the NeRF MLP            */
+    int use_rejection;  /* 1: Eq. 6 (F from Eq. 5); 0: Eq. 4 (F = 1)         */
+    int jitter;         /* 0: stratum midpoints; 1: SplitMix64 jitter drawn
+                           from stream (seed, counter), value ray*n_coarse+k */
+    float near_z, far_z;/* sample range along d (points x = o + z d)         */
+    float alpha;        /* Eq. 5 threshold, 0 < alpha < 0.5                   */
+    float tau;          /* lower bound of F (Eq. 6), > 0                      */
+    double rho_reject;  /* mask_i = (w_i >= rho_reject / N)                   */
+    double s_min;       /* floor of S_i before the logarithm (> 0)            */
+    uint64_t seed, counter;
+} mcl_opts;
+
+/* Optional per-ray / per-particle outputs of mcl_update (any may be NULL). */
+typedef struct {
+    float* rgb;       /* [N*B, 3] rendered colour C(r(p_j, x_i))             */
+    float* E;         /* [N*B]  squared RGB distance to the observed pixel   */
+    float* F;         /* [N*B]  max(z_opaque - z_trans, tau), or 1           */
+    float* z_trans;   /* [N*B]  Eq. 5                                        */
+    float* z_opaque;  /* [N*B]  Eq. 5                                        */
+    float* S;         /* [N]    sum_j E_ij F_ij                              */
+} mcl_debug;
+
+/* Upload the NeRF map M (Sec. III-A, "NeRF as a map"; the map is fixed for a
+ * localisation run).  host_weights: n_floats FP32 values, per layer W[out][in]
+ * then b[out], layers in the order trunk1..trunk_depth, sigma, feature,
+ * rgb_hidden, rgb_out; trunk layer skip_layer+1 reads [h, gamma(x)] and
+ * rgb_hidden reads [feature, gamma(d)].  The blob is copied (FP32, BF16 and
+ * FP8 device forms are prepared here), so the caller keeps its buffer.
+ * Allocates the workspace for cfg.  Synchronous.  *out_map is NULL on error. */
+int mcl_init_map(const float* host_weights, size_t n_floats,
+                 const mcl_arch* arch, const mcl_map_config* cfg,
+                 mcl_map** out_map);
+
+/* Free the map and its workspace (synchronises the device first). */
+void mcl_destroy_map(mcl_map* map);
+
+/* One particle-weight update (Alg. 1, loop over particles, with Eq. 6):
+ *   for particle i (pose d_particles[i], row-major 3x4 camera-to-world [R|t],
+ *   camera looking along -z with +y up) and query pixel p_j = d_pixels[j]
+ *   (int32 (u, v) in the level image; the same B pixels for every particle):
+ *     C_ij = volume render (Eq. 1) of the pixel-centre ray with R K, using
+ *            n_coarse stratified and n_fine importance samples;
+ *     E_ij = sum_c (I^R(p_j)_c - C_ij,c)^2, I^R = box downscale of d_image;
+ *     F_ij = max(z_opaque - z_trans, tau) (Eq. 5) if use_rejection else 1;
+ *   S_i = sum_j E_ij F_ij,  d_logw[i] = 4 (log B - log max(S_i, s_min)),
+ *   d_w[i] = exp(logw_i - logsumexp(logw)) in FP64 (sums to 1),
+ *   d_mask[i] = (d_w[i] >= rho_reject / N).
+ * d_particles: [N,12] f32.  d_image: [H,W,3] f32 full resolution.  level:
+ * 0, 1, 2 (R = 1/4, 1/2, 1; W and H divisible by the factor).  N*B <=
+ * max_rays, N <= max_particles.  A particle whose S_i is not finite gets
+ * logw = -inf, w = 0, mask = 0 and is counted in the status word. */
+int mcl_update(mcl_map* map, const float* d_particles, int N,
+               const float* d_image, const mcl_intrinsics* K, int level,
+               const int32_t* d_pixels, int B, const mcl_opts* opts,
+               float* d_logw, double* d_w, uint8_t* d_mask,
+               const mcl_debug* dbg, void* stream);
+
+/* Render the colours C(r(p_j, x_i)) (Eq. 1 with the same sampling as
+ * mcl_update) for n_poses poses x B pixels into d_rgb [n_poses*B, 3]; d_F
+ * [n_poses*B] (optional) receives F of Eq. 6.  Used to synthesise
+ * observations. */
+int mcl_render(mcl_map* map, const float* d_poses, int n_poses,
+               const mcl_intrinsics* K, int level, const int32_t* d_pixels,
+               int B, const mcl_opts* opts, float* d_rgb, float* d_F,
+               void* stream);
+
+/* Systematic resampling (Alg. 1, "draw i with probability proportional to
+ * w_i") on an exact integer CDF: with e the binary exponent of max w
+ * (max w = m 2^e, m in [1/2, 1)) and s = 50 - e - ceil(log2 N_in),
+ * q_i = floor(w_i 2^s), C_i = q_0 + .. + q_i, T = C_{N_in - 1},
+ * U = floor(u0 2^53); d_idx[k] = smallest i with
+ * C_i N_out 2^53 > (k 2^53 + U) T.  The same weights give the same indices
+ * on every machine.  d_w: [N_in] f64 >= 0; d_idx: [N_out] int32.  N_in <=
+ * max_particles, 1 <= N_out <= 65536, 0 <= u0 < 1.  Uses the map workspace.
+ * Negative, non-finite or all-zero weights: every d_idx is -1 and the status
+ * word records MCL_ERR_DEGENERATE. */
+int mcl_resample(mcl_map* map, const double* d_w, int N_in, int N_out,
+                 double u0, int32_t* d_idx, void* stream);
+
+/* Prediction step (Sec. III-A): d_out[k] = d_in[idx[k]] * Exp(delta_k) with
+ * O_t = I, delta_k = (rho, (0, yaw, 0)) in se(3), rho ~ N(0, sigma_t^2 I3),
+ * yaw ~ N(0, sigma_yaw^2) in the body frame.  The normals are Box-Muller
+ * pairs of SplitMix64 stream (seed, counter): normal m uses values 2m and
+ * 2m+1, particle k takes normals 4k .. 4k+3.  d_in [N_in,12], d_out
+ * [N_out,12] f32 (computed in FP64).  d_idx [N_out] may be NULL (identity,
+ * N_out <= N_in); an index outside [0, N_in) yields a NaN pose. */
+int mcl_predict(const float* d_in, int N_in, const int32_t* d_idx, int N_out,
+                float sigma_t, float sigma_yaw, uint64_t seed,
+                uint64_t counter, float* d_out, void* stream);
+
+/* Box downscale of Alg. 1 ("downscale(I_t, R_t)"): d_out[v][u] = mean of the
+ * factor x factor block of d_image.  d_image [H,W,3] f32, d_out
+ * [H/factor, W/factor, 3]. */
+int mcl_downscale(const float* d_image, int W, int H, int factor,
+                  float* d_out, void* stream);
+
+/* Spread of the particle positions used by the refinement test of the
+ * coarse-to-fine schedule (Sec. III-C, "Var({x_t}) < delta_refine"):
+ * d_out[0..2] = mean position, d_out[3] = trace of the population covariance
+ * (FP64).  d_poses [N,12] f32. */
+int mcl_position_spread(const float* d_poses, int N, double* d_out,
+                        void* stream);
+
+/* Read and clear the map's status word (synchronises `stream`): MCL_OK or the
+ * first MCL_ERR_* recorded by the device since the last read; *n_nonfinite
+ * (optional) receives the number of particles masked for non-finite loss. */
+int mcl_read_status(mcl_map* map, int* n_nonfinite, void* stream);
+
+/* Phases timed when profiling is on (indices into the array of
+ * mcl_profile_read). */
+#define MCL_PHASE_RAYGEN 0     /* ray generation + stratified samples      */
+#define MCL_PHASE_MLP_COARSE 1 /* NeRF MLP on the coarse samples           */
+#define MCL_PHASE_SAMPLE 2     /* coarse composite + importance sampling   */
+#define MCL_PHASE_MLP_FINE 3   /* NeRF MLP on the importance samples       */
+#define MCL_PHASE_COMPOSITE 4  /* final composite, Eq. 5, photometric E    */
+#define MCL_PHASE_WEIGHTS 5    /* Eq. 6 weights, FP64 normalisation        */
+#define MCL_PHASE_RESAMPLE 6   /* systematic resampling                    */
+#define MCL_N_PHASES 7
+
+/* Turn per-phase GPU timing of mcl_update / mcl_render / mcl_resample on or
+ * off for this map.  When on, CUDA events are recorded on the call's stream
+ * around each phase (a few microseconds of overhead per phase). */
+int mcl_profile_enable(mcl_map* map, int enable);
+
+/* Synchronise on the recorded events and return the accumulated GPU time of
+ * each phase in ms_out[MCL_N_PHASES] since the last reset; *n_launches
+ * (optional) receives the number of kernels this library has launched in the
+ * process so far (all maps and entry points).  reset != 0 clears the
+ * accumulated times. */
+int mcl_profile_read(mcl_map* map, double* ms_out, long long* n_launches, int reset);
+
+/* Thread-local message of the last error, "" if none. */
+const char* mcl_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MCL_H */

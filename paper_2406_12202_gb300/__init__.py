@@ -1,0 +1,291 @@
+"""Python binding of the GB300 MCL particle-weight-update library.
+
+Thin argument marshalling over the C ABI of ``include/mcl.h``: every stage of
+the update runs in the library's CUDA kernels.  Tensors are torch CUDA
+tensors (device memory and the current stream come from PyTorch).  If the
+shared library has not been built, every call raises ``RuntimeError``;
+there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libmcl.so")
+
+MCL_OK = 0
+MCL_ERR_ARG = -1
+MCL_ERR_CUDA = -2
+MCL_ERR_NONFINITE = -3
+MCL_ERR_TIMEOUT = -4
+MCL_ERR_UNSUPPORTED = -5
+MCL_ERR_DEGENERATE = -6
+
+PREC_FP32, PREC_BF16, PREC_FP8 = 0, 1, 2
+PHASES = ("raygen", "mlp_coarse", "sample", "mlp_fine", "composite", "weights", "resample")
+N_PHASES = len(PHASES)
+_PREC = {"fp32": PREC_FP32, "bf16": PREC_BF16, "fp8": PREC_FP8}
+
+
+class MclError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"mcl error {code}: {msg}")
+        self.code = code
+
+
+class Arch(C.Structure):
+    _fields_ = [("n_freq_xyz", C.c_int), ("n_freq_dir", C.c_int), ("trunk_depth", C.c_int),
+                ("trunk_width", C.c_int), ("skip_layer", C.c_int), ("rgb_width", C.c_int)]
+
+
+class MapConfig(C.Structure):
+    _fields_ = [("max_rays", C.c_int), ("max_samples", C.c_int), ("max_particles", C.c_int)]
+
+
+class Intrinsics(C.Structure):
+    _fields_ = [("fx", C.c_float), ("fy", C.c_float), ("cx", C.c_float), ("cy", C.c_float),
+                ("width", C.c_int), ("height", C.c_int)]
+
+
+class Opts(C.Structure):
+    _fields_ = [("n_coarse", C.c_int), ("n_fine", C.c_int), ("precision", C.c_int),
+                ("use_rejection", C.c_int), ("jitter", C.c_int),
+                ("near_z", C.c_float), ("far_z", C.c_float), ("alpha", C.c_float),
+                ("tau", C.c_float), ("rho_reject", C.c_double), ("s_min", C.c_double),
+                ("seed", C.c_uint64), ("counter", C.c_uint64)]
+
+
+class Debug(C.Structure):
+    _fields_ = [(n, C.c_void_p) for n in ("rgb", "E", "F", "z_trans", "z_opaque", "S")]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib():
+    """The loaded shared library (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(
+                    f"CUDA library {LIB_PATH} is not built; run "
+                    "paper_2406_12202_gb300.build.build() (or __graft_entry__.build()) first")
+            L = C.CDLL(LIB_PATH)
+            vp, i32, f32, f64, u64 = C.c_void_p, C.c_int, C.c_float, C.c_double, C.c_uint64
+            L.mcl_init_map.argtypes = [vp, C.c_size_t, C.POINTER(Arch), C.POINTER(MapConfig),
+                                       C.POINTER(vp)]
+            L.mcl_destroy_map.argtypes = [vp]
+            L.mcl_destroy_map.restype = None
+            L.mcl_update.argtypes = [vp, vp, i32, vp, C.POINTER(Intrinsics), i32, vp, i32,
+                                     C.POINTER(Opts), vp, vp, vp, C.POINTER(Debug), vp]
+            L.mcl_render.argtypes = [vp, vp, i32, C.POINTER(Intrinsics), i32, vp, i32,
+                                     C.POINTER(Opts), vp, vp, vp]
+            L.mcl_resample.argtypes = [vp, vp, i32, i32, f64, vp, vp]
+            L.mcl_predict.argtypes = [vp, i32, vp, i32, f32, f32, u64, u64, vp, vp]
+            L.mcl_downscale.argtypes = [vp, i32, i32, i32, vp, vp]
+            L.mcl_position_spread.argtypes = [vp, i32, vp, vp]
+            L.mcl_read_status.argtypes = [vp, C.POINTER(C.c_int), vp]
+            L.mcl_profile_enable.argtypes = [vp, i32]
+            L.mcl_profile_read.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_longlong), i32]
+            L.mcl_last_error.restype = C.c_char_p
+            L.mcl_last_error.argtypes = []
+            _lib = L
+    return _lib
+
+
+def _check(rc):
+    if rc != MCL_OK:
+        raise MclError(rc, lib().mcl_last_error().decode())
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream():
+    return _torch().cuda.current_stream().cuda_stream
+
+
+def _ptr(t, dtype, shape=None, name="tensor"):
+    torch = _torch()
+    if t is None:
+        return None
+    if not (isinstance(t, torch.Tensor) and t.is_cuda):
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    return t.data_ptr()
+
+
+@dataclass
+class UpdateOptions:
+    n_coarse: int = 64
+    n_fine: int = 128
+    precision: str = "fp32"
+    use_rejection: bool = True
+    jitter: bool = False
+    near: float = 2.0
+    far: float = 6.0
+    alpha: float = 0.05
+    tau: float = 0.1
+    rho_reject: float = 1e-3
+    s_min: float = 1e-30
+    seed: int = 0
+    counter: int = 0
+
+    def c(self) -> Opts:
+        return Opts(self.n_coarse, self.n_fine, _PREC[self.precision], int(self.use_rejection),
+                    int(self.jitter), self.near, self.far, self.alpha, self.tau,
+                    self.rho_reject, self.s_min, self.seed, self.counter)
+
+
+def intrinsics(fx, fy, cx, cy, width, height) -> Intrinsics:
+    return Intrinsics(fx, fy, cx, cy, width, height)
+
+
+class Map:
+    """A NeRF map uploaded to the GPU with its workspace (mcl_init_map)."""
+
+    def __init__(self, weights: np.ndarray, max_rays: int, max_samples: int = 192,
+                 max_particles: int | None = None, arch=(10, 4, 8, 256, 5, 128)):
+        w = np.ascontiguousarray(weights, dtype=np.float32)
+        self._arch = Arch(*arch)
+        self.cfg = MapConfig(int(max_rays), int(max_samples),
+                             int(max_particles if max_particles is not None else max_rays))
+        h = C.c_void_p()
+        _check(lib().mcl_init_map(w.ctypes.data, w.size, C.byref(self._arch), C.byref(self.cfg),
+                                  C.byref(h)))
+        self.handle = h
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().mcl_destroy_map(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---------------------------------------------------------------- update
+    def update(self, particles, image, K: Intrinsics, level: int, pixels,
+               opts: UpdateOptions, out=None, debug: bool = False):
+        """Eq. 6 weights of particles [N,12] against image [H,W,3] at level.
+        Returns dict logw [N] f32, w [N] f64, mask [N] u8 (+ per-ray debug)."""
+        torch = _torch()
+        N = particles.shape[0]
+        B = pixels.shape[0]
+        dev = particles.device
+        if out is None:
+            out = dict(logw=torch.empty(N, dtype=torch.float32, device=dev),
+                       w=torch.empty(N, dtype=torch.float64, device=dev),
+                       mask=torch.empty(N, dtype=torch.uint8, device=dev))
+        dbg = None
+        if debug:
+            nr = N * B
+            out.update(rgb=torch.empty(nr, 3, dtype=torch.float32, device=dev),
+                       E=torch.empty(nr, dtype=torch.float32, device=dev),
+                       F=torch.empty(nr, dtype=torch.float32, device=dev),
+                       z_trans=torch.empty(nr, dtype=torch.float32, device=dev),
+                       z_opaque=torch.empty(nr, dtype=torch.float32, device=dev),
+                       S=torch.empty(N, dtype=torch.float32, device=dev))
+            dbg = Debug(*(out[k].data_ptr() for k in ("rgb", "E", "F", "z_trans", "z_opaque", "S")))
+        o = opts.c()
+        _check(lib().mcl_update(
+            self.handle, _ptr(particles, torch.float32, (N, 12), "particles"), N,
+            _ptr(image, torch.float32, (K.height, K.width, 3), "image"), C.byref(K), int(level),
+            _ptr(pixels, torch.int32, (B, 2), "pixels"), B, C.byref(o),
+            _ptr(out["logw"], torch.float32, (N,), "logw"),
+            _ptr(out["w"], torch.float64, (N,), "w"),
+            _ptr(out["mask"], torch.uint8, (N,), "mask"),
+            C.byref(dbg) if dbg is not None else None, _stream()))
+        return out
+
+    def render(self, poses, K: Intrinsics, level: int, pixels, opts: UpdateOptions,
+               with_F: bool = False):
+        """Rendered colours [n*B, 3] (and F [n*B]) of poses x pixels."""
+        torch = _torch()
+        n, B = poses.shape[0], pixels.shape[0]
+        rgb = torch.empty(n * B, 3, dtype=torch.float32, device=poses.device)
+        F = torch.empty(n * B, dtype=torch.float32, device=poses.device) if with_F else None
+        o = opts.c()
+        _check(lib().mcl_render(self.handle, _ptr(poses, torch.float32, (n, 12), "poses"), n,
+                                C.byref(K), int(level), _ptr(pixels, torch.int32, (B, 2), "pixels"),
+                                B, C.byref(o), rgb.data_ptr(),
+                                F.data_ptr() if F is not None else None, _stream()))
+        return (rgb, F) if with_F else rgb
+
+    def resample(self, w, n_out: int, u0: float, idx=None):
+        torch = _torch()
+        n_in = w.shape[0]
+        if idx is None:
+            idx = torch.empty(n_out, dtype=torch.int32, device=w.device)
+        _check(lib().mcl_resample(self.handle, _ptr(w, torch.float64, (n_in,), "w"), n_in,
+                                  int(n_out), float(u0), _ptr(idx, torch.int32, (n_out,), "idx"),
+                                  _stream()))
+        return idx
+
+    def profile(self, enable: bool = True):
+        _check(lib().mcl_profile_enable(self.handle, int(enable)))
+
+    def profile_read(self, reset: bool = True):
+        """Accumulated GPU ms per phase (dict) and the library's launch count."""
+        ms = (C.c_double * N_PHASES)()
+        n = C.c_longlong(0)
+        _check(lib().mcl_profile_read(self.handle, ms, C.byref(n), int(reset)))
+        return dict(zip(PHASES, list(ms))), n.value
+
+    def read_status(self):
+        n = C.c_int(0)
+        rc = lib().mcl_read_status(self.handle, C.byref(n), _stream())
+        return rc, n.value
+
+
+def predict(poses, idx, n_out: int, sigma_t: float, sigma_yaw: float, seed: int, counter: int,
+            out=None):
+    torch = _torch()
+    if out is None:
+        out = torch.empty(n_out, 12, dtype=torch.float32, device=poses.device)
+    _check(lib().mcl_predict(_ptr(poses, torch.float32, (poses.shape[0], 12), "poses"),
+                             poses.shape[0], _ptr(idx, torch.int32, (n_out,), "idx") if idx is not None else None,
+                             int(n_out), float(sigma_t), float(sigma_yaw), int(seed), int(counter),
+                             _ptr(out, torch.float32, (n_out, 12), "out"), _stream()))
+    return out
+
+
+def downscale(image, factor: int, out=None):
+    torch = _torch()
+    H, W, _ = image.shape
+    if out is None:
+        out = torch.empty(H // factor, W // factor, 3, dtype=torch.float32, device=image.device)
+    _check(lib().mcl_downscale(_ptr(image, torch.float32, (H, W, 3), "image"), W, H, int(factor),
+                               _ptr(out, torch.float32, (H // factor, W // factor, 3), "out"),
+                               _stream()))
+    return out
+
+
+def position_spread(poses, out=None):
+    torch = _torch()
+    if out is None:
+        out = torch.empty(4, dtype=torch.float64, device=poses.device)
+    _check(lib().mcl_position_spread(_ptr(poses, torch.float32, None, "poses"), poses.shape[0],
+                                     _ptr(out, torch.float64, (4,), "out"), _stream()))
+    return out
+
+
+EXPORTED = ("mcl_init_map", "mcl_destroy_map", "mcl_update", "mcl_render", "mcl_resample",
+            "mcl_predict", "mcl_downscale", "mcl_position_spread", "mcl_read_status",
+            "mcl_profile_enable", "mcl_profile_read", "mcl_last_error")

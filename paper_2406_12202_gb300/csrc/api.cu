@@ -1,0 +1,402 @@
+// api.cu -- the extern "C" entry points of include/mcl.h: argument checks,
+// map / workspace management, and the order of the stages of one update.
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <atomic>
+#include <cmath>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace mcl {
+
+static thread_local char g_err[512] = "";
+
+int fail(int code, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+int cuda_check(cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return MCL_OK;
+    return fail(MCL_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+static std::atomic<long long> g_launches{0};
+
+void note_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+// Per-phase timing: an event pair recorded on the call's stream around a
+// phase when the map's profiling flag is set.
+static cudaEvent_t ev_get(mcl_map* m) {
+    cudaEvent_t e = nullptr;
+    if (!m->pool.empty()) {
+        e = m->pool.back();
+        m->pool.pop_back();
+    } else {
+        cudaEventCreate(&e);
+    }
+    return e;
+}
+
+struct PhaseScope {
+    mcl_map* m;
+    int phase;
+    cudaStream_t s;
+    cudaEvent_t a = nullptr;
+    PhaseScope(mcl_map* m_, int ph, cudaStream_t s_) : m(m_), phase(ph), s(s_) {
+        if (m && m->prof) {
+            a = ev_get(m);
+            cudaEventRecord(a, s);
+        }
+    }
+    ~PhaseScope() {
+        if (a) {
+            cudaEvent_t b = ev_get(m);
+            cudaEventRecord(b, s);
+            m->marks.push_back({phase, a, b});
+        }
+    }
+};
+
+// Layer table of the fixed architecture: fan-in and fan-out in blob order.
+static void layer_shapes(int* fin, int* fout) {
+    for (int l = 0; l < kDepth; ++l) {
+        fin[l] = (l == 0) ? kGx : (l == kSkip ? kWidth + kGx : kWidth);
+        fout[l] = kWidth;
+    }
+    fin[8] = kWidth; fout[8] = 1;
+    fin[9] = kWidth; fout[9] = kWidth;
+    fin[10] = kWidth + kGd; fout[10] = kRgbW;
+    fin[11] = kRgbW; fout[11] = 3;
+}
+
+static size_t blob_size() {
+    int fin[12], fout[12];
+    layer_shapes(fin, fout);
+    size_t n = 0;
+    for (int l = 0; l < 12; ++l) n += (size_t)fin[l] * fout[l] + fout[l];
+    return n;
+}
+
+static void free_map(mcl_map* m) {
+    if (!m) return;
+    mlp_tc_free(m);
+    for (auto& mk : m->marks) {
+        cudaEventDestroy(mk.a);
+        cudaEventDestroy(mk.b);
+    }
+    for (auto e : m->pool) cudaEventDestroy(e);
+    void* ptrs[] = {m->w32, m->rays, m->gd, m->zc, m->zf, m->out_c, m->out_f, m->e_ray,
+                    m->logw64, m->cdf, m->status, m->act0, m->act1, m->gxbuf};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    delete m;
+}
+
+}  // namespace mcl
+
+using namespace mcl;
+
+extern "C" const char* mcl_last_error(void) { return g_err; }
+
+extern "C" int mcl_init_map(const float* host_weights, size_t n_floats, const mcl_arch* arch,
+                            const mcl_map_config* cfg, mcl_map** out_map) {
+    g_err[0] = 0;
+    if (!out_map) return fail(MCL_ERR_ARG, "mcl_init_map: out_map is NULL");
+    *out_map = nullptr;
+    if (!host_weights || !arch || !cfg) return fail(MCL_ERR_ARG, "mcl_init_map: NULL argument");
+    if (arch->n_freq_xyz != kLxyz || arch->n_freq_dir != kLdir || arch->trunk_depth != kDepth ||
+        arch->trunk_width != kWidth || arch->skip_layer != kSkip || arch->rgb_width != kRgbW)
+        return fail(MCL_ERR_UNSUPPORTED,
+                    "mcl_init_map: this build serves arch (10,4,8,256,5,128) only");
+    if (n_floats != blob_size())
+        return fail(MCL_ERR_ARG, "mcl_init_map: n_floats %zu, expected %zu", n_floats, blob_size());
+    if (cfg->max_rays < 1 || cfg->max_samples < 2 || cfg->max_samples > kMaxSamples ||
+        cfg->max_particles < 1)
+        return fail(MCL_ERR_ARG, "mcl_init_map: bad workspace config (rays %d samples %d particles %d)",
+                    cfg->max_rays, cfg->max_samples, cfg->max_particles);
+    for (size_t i = 0; i < n_floats; ++i)
+        if (!std::isfinite(host_weights[i]))
+            return fail(MCL_ERR_ARG, "mcl_init_map: weight %zu is not finite", i);
+
+    mcl_map* m = new mcl_map();
+    m->cfg = *cfg;
+    // ---- padded FP32 layers -------------------------------------------
+    int fin[12], fout[12], kpad[12];
+    layer_shapes(fin, fout);
+    for (int l = 0; l < 12; ++l) kpad[l] = fin[l];
+    kpad[0] = kGxPad;               // gamma(x) 63 -> 64
+    kpad[kSkip] = kWidth + kGxPad;  // [h, gamma(x)] 319 -> 320
+    kpad[10] = kWidth + kGdPad;     // [feature, gamma(d)] 283 -> 288
+    std::vector<size_t> offW(12), offB(12);
+    size_t tot = 0;
+    for (int l = 0; l < 12; ++l) {
+        offW[l] = tot; tot += (size_t)fout[l] * kpad[l];
+        tot = (tot + 3) & ~(size_t)3;
+        offB[l] = tot; tot += fout[l];
+        tot = (tot + 3) & ~(size_t)3;
+    }
+    std::vector<float> h(tot, 0.0f);
+    const float* src = host_weights;
+    for (int l = 0; l < 12; ++l) {
+        for (int o = 0; o < fout[l]; ++o)
+            for (int i = 0; i < fin[l]; ++i) h[offW[l] + (size_t)o * kpad[l] + i] = src[(size_t)o * fin[l] + i];
+        src += (size_t)fin[l] * fout[l];
+        for (int o = 0; o < fout[l]; ++o) h[offB[l] + o] = src[o];
+        src += fout[l];
+    }
+    int rc;
+    if ((rc = cuda_check(cudaMalloc(&m->w32, tot * sizeof(float)), "cudaMalloc(weights)"))) {
+        free_map(m);
+        return rc;
+    }
+    if ((rc = cuda_check(cudaMemcpy(m->w32, h.data(), tot * sizeof(float), cudaMemcpyHostToDevice),
+                         "cudaMemcpy(weights)"))) {
+        free_map(m);
+        return rc;
+    }
+    for (int l = 0; l < 12; ++l) {
+        m->L[l].W = m->w32 + offW[l];
+        m->L[l].b = m->w32 + offB[l];
+        m->L[l].n = fout[l];
+        m->L[l].k_pad = kpad[l];
+    }
+    // ---- workspace -------------------------------------------------------
+    const size_t R = (size_t)cfg->max_rays, S = (size_t)cfg->max_samples;
+    m->chunk_rows = 1 << 19;
+    if ((size_t)m->chunk_rows > R * S) m->chunk_rows = (int)(((R * S) + 127) / 128 * 128);
+    struct {
+        void** p;
+        size_t bytes;
+        const char* what;
+    } allocs[] = {
+        {(void**)&m->rays, R * sizeof(Ray), "rays"},
+        {(void**)&m->gd, R * kGdPad * sizeof(float), "gamma(d)"},
+        {(void**)&m->zc, R * S * sizeof(float), "z coarse"},
+        {(void**)&m->zf, R * S * sizeof(float), "z fine"},
+        {(void**)&m->out_c, R * S * sizeof(float4), "coarse outputs"},
+        {(void**)&m->out_f, R * S * sizeof(float4), "fine outputs"},
+        {(void**)&m->e_ray, R * sizeof(float), "per-ray loss"},
+        {(void**)&m->logw64, (size_t)cfg->max_particles * sizeof(double), "log weights"},
+        {(void**)&m->cdf, (size_t)cfg->max_particles * sizeof(unsigned long long), "cdf"},
+        {(void**)&m->status, sizeof(Status), "status"},
+        {(void**)&m->act0, (size_t)m->chunk_rows * kWidth * sizeof(float), "act0"},
+        {(void**)&m->act1, (size_t)m->chunk_rows * kWidth * sizeof(float), "act1"},
+        {(void**)&m->gxbuf, (size_t)m->chunk_rows * kGxPad * sizeof(float), "gamma(x)"},
+    };
+    for (auto& a : allocs) {
+        if ((rc = cuda_check(cudaMalloc(a.p, a.bytes), a.what))) {
+            free_map(m);
+            return rc;
+        }
+    }
+    cudaMemset(m->status, 0, sizeof(Status));
+    if ((rc = mlp_tc_prepare(m, host_weights))) {
+        free_map(m);
+        return rc;
+    }
+    if ((rc = cuda_check(cudaDeviceSynchronize(), "mcl_init_map"))) {
+        free_map(m);
+        return rc;
+    }
+    *out_map = m;
+    return MCL_OK;
+}
+
+extern "C" void mcl_destroy_map(mcl_map* map) {
+    if (!map) return;
+    cudaDeviceSynchronize();
+    free_map(map);
+}
+
+static int check_opts(const mcl_opts* o) {
+    if (!o) return fail(MCL_ERR_ARG, "opts is NULL");
+    if (o->n_coarse < 2 || o->n_coarse > kMaxCoarse || o->n_fine < 0 || o->n_fine > kMaxFine)
+        return fail(MCL_ERR_ARG, "n_coarse %d / n_fine %d out of range", o->n_coarse, o->n_fine);
+    if (o->precision < MCL_PREC_FP32 || o->precision > MCL_PREC_FP8)
+        return fail(MCL_ERR_ARG, "precision %d unknown", o->precision);
+    if (!(o->near_z < o->far_z) || !(o->alpha > 0.f && o->alpha < 0.5f) || !(o->tau > 0.f) ||
+        !(o->rho_reject >= 0.0) || !(o->s_min > 0.0))
+        return fail(MCL_ERR_ARG, "bad near/far/alpha/tau/rho/s_min");
+    return MCL_OK;
+}
+
+// Common front half of mcl_update and mcl_render: rays, both sample passes.
+static int render_passes(mcl_map* m, const float* d_poses, int N, const mcl_intrinsics* K,
+                         int level, const int32_t* d_pixels, int B, const mcl_opts* o,
+                         int* factor_out, cudaStream_t s) {
+    int rc;
+    if ((rc = check_opts(o))) return rc;
+    if (!d_poses || !K || !d_pixels) return fail(MCL_ERR_ARG, "NULL pose / intrinsics / pixel set");
+    if (N < 1 || B < 1 || (long)N * B > m->cfg.max_rays)
+        return fail(MCL_ERR_ARG, "N*B = %ld outside [1, max_rays=%d]", (long)N * B, m->cfg.max_rays);
+    if (o->n_coarse + o->n_fine > m->cfg.max_samples)
+        return fail(MCL_ERR_ARG, "n_coarse + n_fine > max_samples %d", m->cfg.max_samples);
+    if (level < 0 || level > 2) return fail(MCL_ERR_ARG, "level %d not in 0..2", level);
+    const int f = 4 >> level;
+    if (K->width < 1 || K->height < 1 || K->width % f || K->height % f)
+        return fail(MCL_ERR_ARG, "image %dx%d not divisible by level factor %d", K->width, K->height, f);
+    if (!(K->fx > 0.f) || !(K->fy > 0.f)) return fail(MCL_ERR_ARG, "focal length must be > 0");
+    const int nr = N * B;
+    {
+        PhaseScope ph(m, MCL_PHASE_RAYGEN, s);
+        if ((rc = cuda_check(launch_raygen(d_poses, N, d_pixels, B, K->fx / f, K->fy / f,
+                                           K->cx / f, K->cy / f, *o, m->rays, m->gd, m->zc, s),
+                             "raygen")))
+            return rc;
+    }
+    auto mlp = [&](const float* z, int S, float4* out) -> cudaError_t {
+        if (o->precision == MCL_PREC_FP32) return mlp_fp32(m, m->rays, m->gd, z, S, nr, out, s);
+        return mlp_tc(m, o->precision, m->rays, m->gd, z, S, nr, out, s);
+    };
+    {
+        PhaseScope ph(m, MCL_PHASE_MLP_COARSE, s);
+        if ((rc = cuda_check(mlp(m->zc, o->n_coarse, m->out_c), "mlp (coarse)"))) return rc;
+    }
+    if (o->n_fine > 0) {
+        {
+            PhaseScope ph(m, MCL_PHASE_SAMPLE, s);
+            if ((rc = cuda_check(launch_coarse_to_fine(m->rays, nr, m->zc, o->n_coarse, m->out_c,
+                                                       o->n_fine, m->zf, s),
+                                 "importance sampling")))
+                return rc;
+        }
+        PhaseScope ph(m, MCL_PHASE_MLP_FINE, s);
+        if ((rc = cuda_check(mlp(m->zf, o->n_fine, m->out_f), "mlp (fine)"))) return rc;
+    }
+    *factor_out = f;
+    return MCL_OK;
+}
+
+extern "C" int mcl_update(mcl_map* m, const float* d_particles, int N, const float* d_image,
+                          const mcl_intrinsics* K, int level, const int32_t* d_pixels, int B,
+                          const mcl_opts* o, float* d_logw, double* d_w, uint8_t* d_mask,
+                          const mcl_debug* dbg, void* stream) {
+    g_err[0] = 0;
+    if (!m) return fail(MCL_ERR_ARG, "mcl_update: map is NULL");
+    if (!d_image || !d_logw || !d_w || !d_mask) return fail(MCL_ERR_ARG, "mcl_update: NULL output/image");
+    if (N > m->cfg.max_particles) return fail(MCL_ERR_ARG, "N %d > max_particles %d", N, m->cfg.max_particles);
+    cudaStream_t s = (cudaStream_t)stream;
+    int f = 1, rc;
+    if ((rc = render_passes(m, d_particles, N, K, level, d_pixels, B, o, &f, s))) return rc;
+    const int nr = N * B;
+    {
+        PhaseScope ph(m, MCL_PHASE_COMPOSITE, s);
+        if ((rc = cuda_check(launch_final_composite(m->rays, nr, m->zc, m->out_c, o->n_coarse,
+                                                    m->zf, m->out_f, o->n_fine, d_image, K->width,
+                                                    K->height, f, d_pixels, B, *o, m->e_ray, dbg,
+                                                    nullptr, nullptr, s),
+                             "composite")))
+            return rc;
+    }
+    PhaseScope ph(m, MCL_PHASE_WEIGHTS, s);
+    return cuda_check(launch_weights(m->e_ray, N, B, *o, d_logw, m->logw64, d_w, d_mask,
+                                     dbg ? dbg->S : nullptr, m->status, s),
+                      "weights");
+}
+
+extern "C" int mcl_render(mcl_map* m, const float* d_poses, int n_poses, const mcl_intrinsics* K,
+                          int level, const int32_t* d_pixels, int B, const mcl_opts* o,
+                          float* d_rgb, float* d_F, void* stream) {
+    g_err[0] = 0;
+    if (!m || !d_rgb) return fail(MCL_ERR_ARG, "mcl_render: NULL map / output");
+    cudaStream_t s = (cudaStream_t)stream;
+    int f = 1, rc;
+    if ((rc = render_passes(m, d_poses, n_poses, K, level, d_pixels, B, o, &f, s))) return rc;
+    PhaseScope ph(m, MCL_PHASE_COMPOSITE, s);
+    return cuda_check(launch_final_composite(m->rays, n_poses * B, m->zc, m->out_c, o->n_coarse,
+                                             m->zf, m->out_f, o->n_fine, nullptr, K->width,
+                                             K->height, f, d_pixels, B, *o, nullptr, nullptr,
+                                             d_rgb, d_F, s),
+                      "composite");
+}
+
+extern "C" int mcl_resample(mcl_map* m, const double* d_w, int N_in, int N_out, double u0,
+                            int32_t* d_idx, void* stream) {
+    g_err[0] = 0;
+    if (!m || !d_w || !d_idx) return fail(MCL_ERR_ARG, "mcl_resample: NULL argument");
+    if (N_in < 1 || N_in > m->cfg.max_particles)
+        return fail(MCL_ERR_ARG, "mcl_resample: N_in %d outside [1, %d]", N_in, m->cfg.max_particles);
+    if (N_out < 1 || N_out > 65536) return fail(MCL_ERR_ARG, "mcl_resample: N_out %d outside [1, 65536]", N_out);
+    if (!(u0 >= 0.0 && u0 < 1.0)) return fail(MCL_ERR_ARG, "mcl_resample: u0 must be in [0, 1)");
+    PhaseScope ph(m, MCL_PHASE_RESAMPLE, (cudaStream_t)stream);
+    return cuda_check(launch_resample(d_w, N_in, N_out, u0, d_idx, m->cdf, m->status,
+                                      (cudaStream_t)stream),
+                      "resample");
+}
+
+extern "C" int mcl_predict(const float* d_in, int N_in, const int32_t* d_idx, int N_out,
+                           float sigma_t, float sigma_yaw, uint64_t seed, uint64_t counter,
+                           float* d_out, void* stream) {
+    g_err[0] = 0;
+    if (!d_in || !d_out || N_out < 1 || N_in < 1) return fail(MCL_ERR_ARG, "mcl_predict: bad argument");
+    if (!d_idx && N_out > N_in) return fail(MCL_ERR_ARG, "mcl_predict: N_out > N_in without an index");
+    if (!(sigma_t >= 0.f) || !(sigma_yaw >= 0.f)) return fail(MCL_ERR_ARG, "mcl_predict: negative sigma");
+    if (d_in == d_out && d_idx) return fail(MCL_ERR_ARG, "mcl_predict: in-place gather is not allowed");
+    return cuda_check(launch_predict(d_in, N_in, d_idx, N_out, sigma_t, sigma_yaw, seed, counter, d_out,
+                                     (cudaStream_t)stream),
+                      "predict");
+}
+
+extern "C" int mcl_downscale(const float* d_image, int W, int H, int factor, float* d_out,
+                             void* stream) {
+    g_err[0] = 0;
+    if (!d_image || !d_out || W < 1 || H < 1 || factor < 1 || W % factor || H % factor)
+        return fail(MCL_ERR_ARG, "mcl_downscale: bad argument");
+    return cuda_check(launch_downscale(d_image, W, H, factor, d_out, (cudaStream_t)stream), "downscale");
+}
+
+extern "C" int mcl_position_spread(const float* d_poses, int N, double* d_out, void* stream) {
+    g_err[0] = 0;
+    if (!d_poses || !d_out || N < 1) return fail(MCL_ERR_ARG, "mcl_position_spread: bad argument");
+    return cuda_check(launch_position_spread(d_poses, N, d_out, (cudaStream_t)stream), "spread");
+}
+
+extern "C" int mcl_read_status(mcl_map* m, int* n_nonfinite, void* stream) {
+    g_err[0] = 0;
+    if (!m) return fail(MCL_ERR_ARG, "mcl_read_status: map is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    Status st;
+    int rc;
+    if ((rc = cuda_check(cudaMemcpyAsync(&st, m->status, sizeof(Status), cudaMemcpyDeviceToHost, s),
+                         "status read")))
+        return rc;
+    if ((rc = cuda_check(cudaStreamSynchronize(s), "status sync"))) return rc;
+    if ((rc = cuda_check(cudaMemsetAsync(m->status, 0, sizeof(Status), s), "status clear"))) return rc;
+    if (n_nonfinite) *n_nonfinite = st.n_nonfinite;
+    return st.code;
+}
+
+extern "C" int mcl_profile_enable(mcl_map* m, int enable) {
+    g_err[0] = 0;
+    if (!m) return fail(MCL_ERR_ARG, "mcl_profile_enable: map is NULL");
+    m->prof = enable != 0;
+    return MCL_OK;
+}
+
+extern "C" int mcl_profile_read(mcl_map* m, double* ms_out, long long* n_launches, int reset) {
+    g_err[0] = 0;
+    if (!m) return fail(MCL_ERR_ARG, "mcl_profile_read: map is NULL");
+    for (auto& mk : m->marks) {
+        int rc;
+        if ((rc = cuda_check(cudaEventSynchronize(mk.b), "profile sync"))) return rc;
+        float ms = 0.f;
+        if ((rc = cuda_check(cudaEventElapsedTime(&ms, mk.a, mk.b), "profile elapsed"))) return rc;
+        m->phase_ms[mk.phase] += ms;
+        m->pool.push_back(mk.a);
+        m->pool.push_back(mk.b);
+    }
+    m->marks.clear();
+    if (ms_out)
+        for (int i = 0; i < MCL_N_PHASES; ++i) ms_out[i] = m->phase_ms[i];
+    if (n_launches) *n_launches = g_launches.load();
+    if (reset)
+        for (int i = 0; i < MCL_N_PHASES; ++i) m->phase_ms[i] = 0.0;
+    return MCL_OK;
+}

@@ -1,0 +1,129 @@
+// internal.cuh -- private declarations shared by the translation units of the
+// MCL weight-update library (not part of the public ABI in include/mcl.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "../../include/mcl.h"
+
+namespace mcl {
+
+// Fixed architecture served by this build.
+constexpr int kLxyz = 10, kLdir = 4, kDepth = 8, kWidth = 256, kSkip = 5, kRgbW = 128;
+constexpr int kGx = 3 + 6 * kLxyz;   // 63
+constexpr int kGd = 3 + 6 * kLdir;   // 27
+constexpr int kGxPad = 64;           // gamma(x) padded to a multiple of 16
+constexpr int kGdPad = 32;           // gamma(d) padded
+constexpr int kMaxSamples = 512;     // n_coarse + n_fine
+constexpr int kMaxCoarse = 256;
+constexpr int kMaxFine = 256;
+
+// Padded FP32 layer (row-major [n][k_pad], bias [n]).
+struct LayerF32 {
+    const float* W;
+    const float* b;
+    int n, k_pad;
+};
+
+// Device status word (one per map).
+struct Status {
+    int code;         // first MCL_ERR_* seen on the device, 0 if none
+    int n_nonfinite;  // particles masked for a non-finite loss
+};
+
+// Ray record: o (xyz) + |d|; d (xyz), rounded to FP32; the FP32 rounding
+// error of d (d = d_hi + d_lo to about 48 bits), so that paths that need x to
+// better than FP32 can rebuild it.
+struct __align__(16) Ray {
+    float ox, oy, oz, dnorm;
+    float dx, dy, dz, pad;
+    float lx, ly, lz, pad2;
+};
+
+}  // namespace mcl
+
+// The map: weights in the forms each MLP path reads, plus the workspace.
+struct mcl_map {
+    mcl_map_config cfg;
+    // FP32 padded layers: 0..7 trunk, 8 sigma(row vector), 9 feature,
+    // 10 rgb_hidden ([feat | gamma(d) | 0]), 11 rgb_out.
+    float* w32 = nullptr;
+    mcl::LayerF32 L[12];
+    // tensor-core path weights (filled by mlp_tc_prepare)
+    void* tc_blob = nullptr;
+    size_t tc_bytes = 0;
+    void* tc_aux = nullptr;
+    // workspace
+    mcl::Ray* rays = nullptr;     // [max_rays]
+    float* gd = nullptr;          // [max_rays, 32] gamma(d)
+    float* zc = nullptr;          // [max_rays * max_samples] coarse z
+    float* zf = nullptr;          // [max_rays * max_samples] fine z
+    float4* out_c = nullptr;      // [max_rays * max_samples] (sigma_raw, rgb)
+    float4* out_f = nullptr;
+    float* e_ray = nullptr;       // [max_rays] E*F
+    double* logw64 = nullptr;     // [max_particles]
+    unsigned long long* cdf = nullptr;  // [max_particles] resampling CDF
+    mcl::Status* status = nullptr;
+    // FP32-form activations (chunked)
+    float* act0 = nullptr;
+    float* act1 = nullptr;
+    float* gxbuf = nullptr;
+    int chunk_rows = 0;
+    // per-phase timing (host side)
+    struct Mark {
+        int phase;
+        cudaEvent_t a, b;
+    };
+    bool prof = false;
+    std::vector<Mark> marks;
+    std::vector<cudaEvent_t> pool;
+    double phase_ms[MCL_N_PHASES] = {0};
+};
+
+namespace mcl {
+
+// Thread-local error reporting (api.cu).
+int fail(int code, const char* fmt, ...);
+int cuda_check(cudaError_t e, const char* what);
+// Count of kernels launched by the library (api.cu).
+void note_launch(int n = 1);
+
+// render.cu
+cudaError_t launch_raygen(const float* particles, int N, const int32_t* pixels, int B,
+                          float fx, float fy, float cx, float cy, const mcl_opts& o,
+                          Ray* rays, float* gd, float* zc, cudaStream_t s);
+cudaError_t launch_coarse_to_fine(const Ray* rays, int n_rays, const float* zc, int nc,
+                                  const float4* out_c, int nf, float* zf, cudaStream_t s);
+cudaError_t launch_final_composite(const Ray* rays, int n_rays, const float* zc, const float4* out_c,
+                                   int nc, const float* zf, const float4* out_f, int nf,
+                                   const float* image, int W, int H, int factor,
+                                   const int32_t* pixels, int B, const mcl_opts& o,
+                                   float* e_ray, const mcl_debug* dbg, float* rgb_out,
+                                   float* F_out, cudaStream_t s);
+cudaError_t launch_weights(const float* e_ray, int N, int B, const mcl_opts& o, float* logw,
+                           double* logw64, double* w, uint8_t* mask, float* S_dbg,
+                           Status* status, cudaStream_t s);
+
+// mlp_fp32.cu: (sigma_raw, rgb) for rows r = ray*S + k of the pass.
+cudaError_t mlp_fp32(mcl_map* m, const Ray* rays, const float* gd, const float* z, int S,
+                     int n_rays, float4* out, cudaStream_t s);
+
+// mlp_tc.cu
+int mlp_tc_prepare(mcl_map* m, const float* host_blob);
+void mlp_tc_free(mcl_map* m);
+cudaError_t mlp_tc(mcl_map* m, int precision, const Ray* rays, const float* gd, const float* z,
+                   int S, int n_rays, float4* out, cudaStream_t s);
+
+// resample.cu
+cudaError_t launch_resample(const double* w, int n_in, int n_out, double u0, int32_t* idx,
+                            unsigned long long* cdf, Status* status, cudaStream_t s);
+cudaError_t launch_predict(const float* in, int n_in, const int32_t* idx, int n_out, float sigma_t,
+                           float sigma_yaw, uint64_t seed, uint64_t counter, float* out,
+                           cudaStream_t s);
+cudaError_t launch_downscale(const float* img, int W, int H, int f, float* out, cudaStream_t s);
+cudaError_t launch_position_spread(const float* poses, int N, double* out, cudaStream_t s);
+
+}  // namespace mcl

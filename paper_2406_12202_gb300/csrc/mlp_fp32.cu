@@ -1,0 +1,233 @@
+// mlp_fp32.cu -- the plain FP32 form of the NeRF MLP: positional encoding,
+// one SIMT FP32 GEMM launch per layer with bias and ReLU, and two row-wise
+// head kernels.  Activations live in HBM (chunks of rows), so this form is
+// also the unfused comparison point for the tensor-core path.
+#include <math.h>
+
+#include "internal.cuh"
+
+namespace mcl {
+
+// gamma(x) of x = o + z d for rows [r0, r0 + n) of a pass with S samples per
+// ray: [x, sin(2^k x), cos(2^k x)]_{k<10}, padded with a zero to 64.  x and
+// the arguments 2^k x are formed in FP64 and reduced modulo 2 pi there, so the
+// sines carry FP32 error rather than FP32 error of x amplified by 2^9.
+__global__ void k_pe_xyz(const Ray* __restrict__ rays, const float* __restrict__ z, int S, long r0,
+                         int n, float* __restrict__ gx) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const long row = r0 + t;
+    const Ray ray = rays[row / S];
+    const double zz = (double)z[row];
+    const double p[3] = {(double)ray.ox + zz * ((double)ray.dx + (double)ray.lx),
+                         (double)ray.oy + zz * ((double)ray.dy + (double)ray.ly),
+                         (double)ray.oz + zz * ((double)ray.dz + (double)ray.lz)};
+    const double two_pi = 6.283185307179586476925286766559;
+    float* g = gx + (size_t)t * kGxPad;
+    g[0] = (float)p[0]; g[1] = (float)p[1]; g[2] = (float)p[2];
+#pragma unroll
+    for (int k = 0; k < kLxyz; ++k) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const double a = ldexp(p[c], k);
+            const double rr = a - two_pi * rint(a / two_pi);
+            float sn, cs;
+            sincosf((float)rr, &sn, &cs);
+            g[3 + 6 * k + c] = sn;
+            g[6 + 6 * k + c] = cs;
+        }
+    }
+    g[kGx] = 0.f;
+}
+
+// C[M, N] = act([A1 | A2] W^T + b).  A1: [M, K1] (lda1); A2 row for output
+// row r is (r + a2_off) / a2_div (lda2, K2 columns); W: [N, K1 + K2]
+// row-major.  K1, K2 multiples of 16, N a multiple of 128.  128x128 tile,
+// 256 threads, 8x8 outputs per thread, register double-buffered loads.
+template <bool RELU>
+__global__ __launch_bounds__(256, 2) void k_sgemm(const float* __restrict__ A1, int lda1, int K1,
+                                               const float* __restrict__ A2, int lda2, int K2,
+                                               long a2_off, int a2_div,
+                                               const float* __restrict__ W,
+                                               const float* __restrict__ bias,
+                                               float* __restrict__ C, int ldc, int M) {
+    constexpr int BM = 128, BN = 128, BK = 16, PAD = 4;
+    __shared__ __align__(16) float As[BK][BM + PAD];
+    __shared__ __align__(16) float Bs[BK][BN + PAD];
+    const int tid = threadIdx.x;
+    const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+    const int K = K1 + K2;
+    const int lr = tid >> 2, lk = (tid & 3) << 2;
+    const int tx = tid & 15, ty = tid >> 4;
+    float acc[8][8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+    float4 ra[2], rb[2];
+    auto load = [&](int k0) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int row = m0 + lr + h * 64;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (row < M) {
+                if (k0 < K1) {
+                    v = *reinterpret_cast<const float4*>(A1 + (size_t)row * lda1 + k0 + lk);
+                } else {
+                    const long r2 = ((long)row + a2_off) / a2_div;
+                    v = *reinterpret_cast<const float4*>(A2 + (size_t)r2 * lda2 + (k0 - K1) + lk);
+                }
+            }
+            ra[h] = v;
+            const int nr = n0 + lr + h * 64;
+            rb[h] = *reinterpret_cast<const float4*>(W + (size_t)nr * K + k0 + lk);
+        }
+    };
+    auto store = [&]() {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int c = lr + h * 64;
+            As[lk + 0][c] = ra[h].x; As[lk + 1][c] = ra[h].y;
+            As[lk + 2][c] = ra[h].z; As[lk + 3][c] = ra[h].w;
+            Bs[lk + 0][c] = rb[h].x; Bs[lk + 1][c] = rb[h].y;
+            Bs[lk + 2][c] = rb[h].z; Bs[lk + 3][c] = rb[h].w;
+        }
+    };
+    load(0);
+    store();
+    __syncthreads();
+    for (int k0 = 0; k0 < K; k0 += BK) {
+        const bool more = k0 + BK < K;
+        if (more) load(k0 + BK);
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            const float4 a0 = *reinterpret_cast<const float4*>(&As[kk][ty * 4]);
+            const float4 a1 = *reinterpret_cast<const float4*>(&As[kk][64 + ty * 4]);
+            const float4 b0 = *reinterpret_cast<const float4*>(&Bs[kk][tx * 4]);
+            const float4 b1 = *reinterpret_cast<const float4*>(&Bs[kk][64 + tx * 4]);
+            const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+        }
+        __syncthreads();
+        if (more) {
+            store();
+            __syncthreads();
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int row = m0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + (i - 4));
+        if (row >= M) continue;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int col = n0 + h * 64 + tx * 4;
+            float4 v;
+            v.x = acc[i][h * 4 + 0] + bias[col + 0];
+            v.y = acc[i][h * 4 + 1] + bias[col + 1];
+            v.z = acc[i][h * 4 + 2] + bias[col + 2];
+            v.w = acc[i][h * 4 + 3] + bias[col + 3];
+            if (RELU) {
+                v.x = fmaxf(v.x, 0.f); v.y = fmaxf(v.y, 0.f);
+                v.z = fmaxf(v.z, 0.f); v.w = fmaxf(v.w, 0.f);
+            }
+            *reinterpret_cast<float4*>(C + (size_t)row * ldc + col) = v;
+        }
+    }
+}
+
+// sigma_raw = w_sigma . h + b_sigma, one warp per row.
+__global__ void k_sigma_head(const float* __restrict__ h, int ldh, const float* __restrict__ w,
+                             const float* __restrict__ b, int n, float4* __restrict__ out) {
+    const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (row >= n) return;
+    const float* x = h + (size_t)row * ldh;
+    float s = 0.f;
+    for (int k = lane; k < kWidth; k += 32) s = fmaf(w[k], x[k], s);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) reinterpret_cast<float*>(out)[4 * (size_t)row] = s + b[0];
+}
+
+// rgb = sigmoid(W_out h + b_out), one warp per row.
+__global__ void k_rgb_head(const float* __restrict__ h, int ldh, const float* __restrict__ W,
+                           const float* __restrict__ b, int n, float4* __restrict__ out) {
+    const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (row >= n) return;
+    const float* x = h + (size_t)row * ldh;
+    float s[3] = {0.f, 0.f, 0.f};
+    for (int k = lane; k < kRgbW; k += 32) {
+        const float xv = x[k];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) s[c] = fmaf(W[c * kRgbW + k], xv, s[c]);
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+        for (int o = 16; o > 0; o >>= 1) s[c] += __shfl_xor_sync(0xffffffffu, s[c], o);
+    if (lane == 0) {
+        float* dst = reinterpret_cast<float*>(out) + 4 * (size_t)row;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) dst[1 + c] = 1.0f / (1.0f + expf(-(s[c] + b[c])));
+    }
+}
+
+static cudaError_t gemm(const float* A1, int lda1, int K1, const float* A2, int lda2, int K2,
+                        long a2_off, int a2_div, const LayerF32& L, float* C, int ldc, int M,
+                        bool relu, cudaStream_t s) {
+    dim3 grid((M + 127) / 128, L.n / 128);
+    note_launch();
+    if (relu)
+        k_sgemm<true><<<grid, 256, 0, s>>>(A1, lda1, K1, A2, lda2, K2, a2_off, a2_div, L.W, L.b, C,
+                                           ldc, M);
+    else
+        k_sgemm<false><<<grid, 256, 0, s>>>(A1, lda1, K1, A2, lda2, K2, a2_off, a2_div, L.W, L.b, C,
+                                            ldc, M);
+    return cudaGetLastError();
+}
+
+cudaError_t mlp_fp32(mcl_map* m, const Ray* rays, const float* gd, const float* z, int S,
+                     int n_rays, float4* out, cudaStream_t s) {
+    const long rows = (long)n_rays * S;
+    cudaError_t e = cudaSuccess;
+    for (long r0 = 0; r0 < rows; r0 += m->chunk_rows) {
+        const int n = (int)((rows - r0) < m->chunk_rows ? (rows - r0) : m->chunk_rows);
+        note_launch();
+        k_pe_xyz<<<(n + 127) / 128, 128, 0, s>>>(rays, z, S, r0, n, m->gxbuf);
+        float* a = m->act0;
+        float* b = m->act1;
+        // trunk layer 1 reads gamma(x)
+        if ((e = gemm(m->gxbuf, kGxPad, kGxPad, nullptr, 0, 0, 0, 1, m->L[0], a, kWidth, n, true, s)))
+            return e;
+        for (int l = 1; l < kDepth; ++l) {
+            if (l == kSkip) {
+                // layer skip+1 reads [h_skip, gamma(x)]
+                e = gemm(a, kWidth, kWidth, m->gxbuf, kGxPad, kGxPad, 0, 1, m->L[l], b, kWidth, n,
+                         true, s);
+            } else {
+                e = gemm(a, kWidth, kWidth, nullptr, 0, 0, 0, 1, m->L[l], b, kWidth, n, true, s);
+            }
+            if (e) return e;
+            float* t = a; a = b; b = t;
+        }
+        // a = trunk output
+        note_launch();
+        k_sigma_head<<<(n * 32 + 255) / 256, 256, 0, s>>>(a, kWidth, m->L[8].W, m->L[8].b, n,
+                                                          out + r0);
+        if ((e = gemm(a, kWidth, kWidth, nullptr, 0, 0, 0, 1, m->L[9], b, kWidth, n, false, s)))
+            return e;
+        // rgb hidden reads [feature, gamma(d)], gamma(d) row = ray = (r0 + r) / S
+        if ((e = gemm(b, kWidth, kWidth, gd, kGdPad, kGdPad, r0, S, m->L[10], a, kWidth, n, true, s)))
+            return e;
+        note_launch();
+        k_rgb_head<<<(n * 32 + 255) / 256, 256, 0, s>>>(a, kWidth, m->L[11].W, m->L[11].b, n,
+                                                        out + r0);
+        if ((e = cudaGetLastError())) return e;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace mcl

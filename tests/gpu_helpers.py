@@ -1,0 +1,117 @@
+"""Shared set-up of the GPU parity tests: seeded scenes, the oracle's answer
+on the same inputs, and the tolerance checks (each derived in the function
+that applies it)."""
+from __future__ import annotations
+
+import numpy as np
+
+import oracle
+import synth
+
+# A ray is "near-tie" when the oracle's running weight sum W_k passes within
+# this distance of alpha or 1 - alpha: FP32 and FP64 can then take different
+# z_trans / z_opaque decisions (one sample step apart).
+TIE = 1e-4
+# Particles whose oracle loss S_i is below this are excluded from log-weight
+# comparisons (log of a near-zero loss amplifies any rounding).
+S_FLOOR = 1e-6
+
+
+def lib():
+    from paper_2406_12202_gb300 import build as B
+    B.build()
+    import paper_2406_12202_gb300 as M
+    return M
+
+
+def make_scene(map_seed, seed, N, B, W, H, focal, n_coarse, n_fine, level=2, add_gt=True,
+               use_rejection=True, tau=0.1, alpha=0.05):
+    """Particles (FP32-representable), GT pose, pixel set of the level image,
+    and an observed image whose sampled level pixels are oracle renders at
+    the GT pose (the rest is a smooth seeded texture)."""
+    blob = synth.he_init_weights(map_seed)
+    P = synth.random_particles(seed, N)[0]
+    gt = synth.gt_pose(seed)[0]
+    if add_gt:
+        P = np.concatenate([P, gt[None]], 0)
+    P = P.astype(np.float32).astype(np.float64)
+    gt32 = gt.astype(np.float32).astype(np.float64)
+    factor = 4 >> level
+    px = synth.pixel_set(seed, W // factor, H // factor, B)
+    K4 = (np.float32(focal), np.float32(focal), np.float32(W / 2), np.float32(H / 2))
+    K4 = tuple(float(k) for k in K4)
+    opts = oracle.make_opts(n_coarse=n_coarse, n_fine=n_fine, use_rejection=use_rejection,
+                            tau=float(np.float32(tau)), alpha=float(np.float32(alpha)))
+    cols = oracle.render_observation_pixels(blob, gt32, K4, factor, px, opts)
+    img = oracle.paint_pixels(synth.smooth_image(seed, W, H), px, factor, cols)
+    img = img.astype(np.float32).astype(np.float64)
+    return dict(blob=blob, P=P, gt=gt32, px=px, K4=K4, W=W, H=H, level=level, factor=factor,
+                img=img, opts=opts, n_coarse=n_coarse, n_fine=n_fine,
+                use_rejection=use_rejection, tau=tau, alpha=alpha)
+
+
+def gpu_opts(M, sc, precision="fp32", **kw):
+    return M.UpdateOptions(n_coarse=sc["n_coarse"], n_fine=sc["n_fine"], precision=precision,
+                           use_rejection=sc["use_rejection"], tau=sc["tau"], alpha=sc["alpha"],
+                           **kw)
+
+
+def run_gpu_update(M, gmap, sc, precision="fp32", **kw):
+    import torch
+    dev = "cuda"
+    P = torch.tensor(sc["P"], dtype=torch.float32, device=dev)
+    img = torch.tensor(sc["img"], dtype=torch.float32, device=dev)
+    px = torch.tensor(sc["px"], dtype=torch.int32, device=dev)
+    fx, fy, cx, cy = sc["K4"]
+    K = M.intrinsics(fx, fy, cx, cy, sc["W"], sc["H"])
+    out = gmap.update(P, img, K, sc["level"], px, gpu_opts(M, sc, precision, **kw), debug=True)
+    torch.cuda.synchronize()
+    return {k: v.cpu().numpy().astype(np.float64) if v.dtype != torch.uint8 else v.cpu().numpy()
+            for k, v in out.items()}
+
+
+def run_oracle_update(sc, uj=None):
+    return oracle.update(sc["blob"], sc["P"], sc["img"], sc["K4"], sc["factor"], sc["px"],
+                         sc["opts"], uj=uj)
+
+
+def check_fp32_parity(g, r, N, B, rgb_rel=1e-4, rgb_abs=1e-6, logw_rel=1e-4, z_abs=2e-5):
+    """FP32 vs FP64 bars: RGB within rgb_rel relative (abs floor rgb_abs);
+    F, z_trans, z_opaque within z_abs on rays that are not near-tie (z values
+    are FP32 roundings of the same sample positions); log-weights within
+    logw_rel relative for particles without near-tie rays and with
+    S >= S_FLOOR; normalised weights consistent with the log-weights.
+    Returns a dict of the observed maxima (for the report)."""
+    rep = {}
+    err = np.abs(g["rgb"] - r["rgb"])
+    tol = rgb_rel * np.abs(r["rgb"]) + rgb_abs
+    rep["rgb_max_abs"] = float(err.max())
+    rep["rgb_max_rel"] = float((err / np.maximum(np.abs(r["rgb"]), 1e-12)).max())
+    assert np.all(err <= tol), f"RGB off: max err {err.max():.3g}, worst excess {(err - tol).max():.3g}"
+    tie = r["tie"] < TIE
+    rep["near_tie_rays"] = int(tie.sum())
+    ok = ~tie
+    for k in ("F", "z_trans", "z_opaque"):
+        d = np.abs(g[k] - r[k])[ok]
+        rep[f"{k}_max_abs"] = float(d.max()) if d.size else 0.0
+        assert np.all(d <= z_abs), f"{k} off by {d.max():.3g} on a non-tie ray"
+    e_err = np.abs(g["E"] - r["E"])
+    # E = |obs - C|^2: dE = 2 |obs - C| dC + dC^2 with dC <= the RGB bar
+    dC = rgb_rel * np.abs(r["rgb"]).max(1) + rgb_abs
+    e_tol = 2 * np.sqrt(3 * np.maximum(r["E"], 0)) * dC + 3 * dC ** 2 + 1e-7 * r["E"]
+    assert np.all(e_err <= e_tol * 1.0001), f"E off by {e_err.max():.3g}"
+    ptie = tie.reshape(N, B).any(1)
+    okp = (~ptie) & (r["S"] >= S_FLOOR)
+    rep["particles_compared"] = int(okp.sum())
+    lw_err = np.abs(g["logw"] - r["logw"])[okp]
+    rel = lw_err / np.maximum(np.abs(r["logw"][okp]), 1.0)
+    rep["logw_max_rel"] = float(rel.max()) if rel.size else 0.0
+    assert np.all(rel <= logw_rel), f"logw off: {rel.max():.3g}"
+    assert abs(g["w"].sum() - 1.0) < 1e-12
+    # normalised weights follow the GPU's own log-weights (FP64 log-sum-exp)
+    lw = g["logw"]
+    fin = np.isfinite(lw)
+    ref = np.exp(lw[fin] - lw[fin].max())
+    ref /= ref.sum()
+    assert np.allclose(g["w"][fin], ref, rtol=1e-5, atol=1e-12)
+    return rep

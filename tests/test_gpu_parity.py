@@ -1,0 +1,242 @@
+"""GPU parity of the plain FP32 form of the weight update, resampling, motion
+and downscale against the FP64 oracle, element by element on the same seeded
+inputs.  Calls go through the C ABI (ctypes binding)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_helpers import (check_fp32_parity, lib, make_scene, run_gpu_update, run_oracle_update)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def M():
+    return lib()
+
+
+@pytest.fixture(scope="module")
+def gmaps(M):
+    maps = {}
+
+    def get(seed):
+        if seed not in maps:
+            maps[seed] = M.Map(synth.he_init_weights(seed), max_rays=40000, max_samples=192,
+                               max_particles=70000)
+        return maps[seed]
+    yield get
+    for m in maps.values():
+        m.close()
+
+
+def _parity(M, gmaps, sc, **kw):
+    g = run_gpu_update(M, gmaps(sc["map_seed"]), sc, **kw)
+    r = run_oracle_update(sc)
+    N = sc["P"].shape[0]
+    B = sc["px"].shape[0]
+    rep = check_fp32_parity(g, r, N, B)
+    return g, r, rep
+
+
+def scene(map_seed, *a, **k):
+    sc = make_scene(map_seed, *a, **k)
+    sc["map_seed"] = map_seed
+    return sc
+
+
+def test_c1_workload_fp32(M, gmaps):
+    """32 particles x 8 pixels of a 100x100 image, 32 coarse samples, no fine
+    pass, He-init map seed 0."""
+    sc = scene(0, 0, 32, 8, 100, 100, 138.9, 32, 0, add_gt=False)
+    g, r, rep = _parity(M, gmaps, sc)
+    assert rep["near_tie_rays"] <= 0.1 * 32 * 8
+
+
+def test_c1_with_gt_particle(M, gmaps):
+    sc = scene(2, 1, 32, 8, 100, 100, 138.9, 32, 0, add_gt=True)
+    g, r, _ = _parity(M, gmaps, sc)
+    assert np.argmax(r["w"]) == 32 and np.argmax(g["w"]) == 32
+    assert g["w"][32] > 0.999 and g["mask"][32] == 1
+
+
+def test_hierarchical_small_c2_geometry(M, gmaps):
+    """400x400 image, 64 coarse + 128 importance samples, rejection on."""
+    sc = scene(0, 3, 6, 8, 400, 400, 555.6, 64, 128, add_gt=True)
+    g, r, _ = _parity(M, gmaps, sc)
+    assert np.argmax(g["w"]) == 6
+
+
+@pytest.mark.parametrize("level,B", [(0, 16), (1, 32)])
+def test_pyramid_levels(M, gmaps, level, B):
+    sc = scene(2, 4 + level, 5, B, 400, 400, 555.6, 64, 128, level=level, add_gt=True)
+    g, r, _ = _parity(M, gmaps, sc)
+    assert np.argmax(g["w"]) == 5
+
+
+def test_ragged_sizes(M, gmaps):
+    """Odd sample counts and a ray count that fills no tile exactly."""
+    sc = scene(2, 6, 7, 5, 60, 40, 70.0, 17, 33, add_gt=False)
+    _parity(M, gmaps, sc)
+
+
+def test_without_rejection_is_eq4(M, gmaps):
+    sc = scene(0, 7, 8, 8, 100, 100, 138.9, 32, 32, add_gt=False, use_rejection=False)
+    g, r, _ = _parity(M, gmaps, sc)
+    assert np.all(g["F"] == 1.0)
+
+
+def test_jittered_strata(M, gmaps):
+    sc = scene(2, 8, 4, 8, 100, 100, 138.9, 32, 32, add_gt=False)
+    seed, ctr = 1234, 5
+    N, B, nc = 4, 8, 32
+    uj = np.array([[oracle.uniform(seed, ctr, r * nc + k) for k in range(nc)]
+                   for r in range(N * B)])
+    g = run_gpu_update(M, gmaps(2), sc, jitter=True, seed=seed, counter=ctr)
+    r = run_oracle_update(sc, uj=uj)
+    # jittered z are rounded to FP32 before the positional encoding (about
+    # 2.4e-7 at z ~ 4), which the 2^9 frequency turns into ~1e-4 rad: the RGB
+    # bar is widened to 1e-3 relative for this mode
+    check_fp32_parity(g, r, N, B, rgb_rel=1e-3, rgb_abs=1e-5, logw_rel=1e-3, z_abs=2e-5)
+
+
+def test_c2_full_size_sampled(M, gmaps):
+    """The full 600 x 64-pixel, 64 + 128-sample update runs on the GPU; the
+    oracle recomputes three particles' rays one by one."""
+    import torch
+    sc = scene(0, 9, 600, 64, 400, 400, 555.6, 64, 128, add_gt=False)
+    gm = gmaps(0)
+    g = run_gpu_update(M, gm, sc)
+    pick = [0, 299, 599]
+    sub = dict(sc)
+    sub["P"] = sc["P"][pick]
+    r = run_oracle_update(sub)
+    B = 64
+    rays = np.concatenate([np.arange(i * B, (i + 1) * B) for i in pick])
+    gs = {k: g[k][rays] for k in ("rgb", "E", "F", "z_trans", "z_opaque")}
+    gs["S"] = g["S"][pick]
+    gs["logw"] = g["logw"][pick]
+    tie = r["tie"] < 1e-4
+    assert np.all(np.abs(gs["rgb"] - r["rgb"]) <= 1e-4 * np.abs(r["rgb"]) + 1e-6)
+    assert np.all(np.abs(gs["F"] - r["F"])[~tie] <= 2e-5)
+    okp = ~tie.reshape(3, B).any(1)
+    rel = np.abs(gs["logw"] - r["logw"])[okp] / np.maximum(np.abs(r["logw"][okp]), 1)
+    assert np.all(rel <= 1e-4)
+    # properties at full size
+    assert abs(g["w"].sum() - 1.0) < 1e-12
+    assert np.all(g["w"] >= 0) and np.all(np.isfinite(g["logw"]))
+    thr = 1e-3 / 600
+    assert np.array_equal(g["mask"].astype(bool), g["w"] >= thr)
+
+
+@pytest.mark.parametrize("n_in,n_out", [(1, 1), (5, 7), (600, 600), (1500, 750), (1025, 3),
+                                        (4000, 4000), (3000, 65536), (65536, 1000)])
+def test_resample_bit_exact(M, gmaps, n_in, n_out):
+    import torch
+    w = synth.random_weights(n_in + n_out, n_in, zero_frac=0.2)
+    u0 = synth.resample_u0(n_in)
+    ref = oracle.resample(w, n_out, u0)
+    gm = gmaps(0)
+    idx = gm.resample(torch.tensor(w, dtype=torch.float64, device="cuda"), n_out, u0)
+    assert np.array_equal(idx.cpu().numpy(), ref)
+
+
+def test_resample_degenerate_weights(M, gmaps):
+    import torch
+    gm = gmaps(0)
+    gm.read_status()
+    idx = gm.resample(torch.zeros(10, dtype=torch.float64, device="cuda"), 10, 0.5)
+    assert np.all(idx.cpu().numpy() == -1)
+    rc, _ = gm.read_status()
+    assert rc == M.MCL_ERR_DEGENERATE
+    rc, _ = gm.read_status()
+    assert rc == M.MCL_OK
+
+
+def test_predict_matches_oracle(M):
+    import torch
+    P = synth.random_particles(10, 300)[0].astype(np.float32)
+    idx = np.random.default_rng(10).integers(0, 300, size=500).astype(np.int32)
+    seed, ctr, st, sy = 77, 3, 0.05, 0.05
+    out = M.predict(torch.tensor(P, device="cuda"), torch.tensor(idx, device="cuda"), 500,
+                    st, sy, seed, ctr).cpu().numpy()
+    noise = oracle.motion_noise(500, seed, ctr, float(np.float32(st)), float(np.float32(sy)))
+    ref = oracle.predict(P.astype(np.float64)[idx], noise)
+    assert np.allclose(out, ref, rtol=0, atol=3e-6)
+
+
+def test_downscale_and_spread(M):
+    import torch
+    img = synth.smooth_image(11, 400, 400)
+    for f in (1, 2, 4):
+        g = M.downscale(torch.tensor(img, device="cuda"), f).cpu().numpy()
+        assert np.allclose(g, oracle.downscale(img.astype(np.float64), f), atol=2e-7)
+    P = synth.random_particles(12, 1500)[0].astype(np.float32)
+    s = M.position_spread(torch.tensor(P, device="cuda")).cpu().numpy()
+    ref = oracle.position_spread(P.astype(np.float64))
+    assert np.allclose(s[:3], ref["mean"], atol=1e-12)
+    assert abs(s[3] - ref["trace"]) < 1e-12
+
+
+def test_gpu_rendered_observation_gt_wins(M, gmaps):
+    """The GPU renders the observation at the GT pose, then weights a particle
+    set containing that pose: the GT particle takes the largest weight."""
+    import torch
+    gm = gmaps(2)
+    P = synth.random_particles(13, 63)[0]
+    gt = synth.gt_pose(13)[0]
+    P = torch.tensor(np.concatenate([P, gt[None]]), dtype=torch.float32, device="cuda")
+    W = H = 100
+    K = M.intrinsics(138.9, 138.9, 50.0, 50.0, W, H)
+    opts = M.UpdateOptions(n_coarse=32, n_fine=32)
+    allpx = np.stack(np.meshgrid(np.arange(W), np.arange(H), indexing="xy"), -1).reshape(-1, 2)
+    img = torch.zeros(H * W, 3, device="cuda")
+    for c0 in range(0, H * W, 4096):
+        pxc = torch.tensor(allpx[c0:c0 + 4096], dtype=torch.int32, device="cuda")
+        img[c0:c0 + 4096] = gm.render(P[-1:].contiguous(), K, 2, pxc, opts)
+    img = img.reshape(H, W, 3).contiguous()
+    px = torch.tensor(synth.pixel_set(13, W, H, 16), dtype=torch.int32, device="cuda")
+    out = gm.update(P, img, K, 2, px, opts)
+    w = out["w"].cpu().numpy()
+    assert np.argmax(w) == 63 and w[63] > 0.99
+
+
+def test_argument_errors(M, gmaps):
+    import torch
+    gm = gmaps(0)
+    P = torch.zeros(4, 12, device="cuda")
+    img = torch.zeros(100, 100, 3, device="cuda")
+    px = torch.zeros(8, 2, dtype=torch.int32, device="cuda")
+    K = M.intrinsics(100.0, 100.0, 50.0, 50.0, 100, 100)
+    opts = M.UpdateOptions(n_coarse=32, n_fine=0)
+    with pytest.raises(M.MclError) as e:
+        gm.update(P, img, K, 3, px, opts)
+    assert e.value.code == M.MCL_ERR_ARG
+    with pytest.raises(M.MclError):
+        gm.update(P, img, M.intrinsics(100.0, 100.0, 50.0, 50.0, 100, 100), 0, px,
+                  M.UpdateOptions(n_coarse=1, n_fine=0))
+    big = torch.zeros(50000, 12, device="cuda")
+    with pytest.raises(M.MclError):
+        gm.update(big, img, K, 2, px, opts)
+    with pytest.raises(M.MclError):
+        gm.resample(torch.ones(4, dtype=torch.float64, device="cuda"), 4, 1.0)
+
+
+def test_nonfinite_particle_is_masked(M, gmaps):
+    import torch
+    gm = gmaps(2)
+    gm.read_status()
+    P = synth.random_particles(14, 8)[0].astype(np.float32)
+    P[3, 3] = np.nan
+    img = torch.tensor(synth.smooth_image(14, 100, 100), device="cuda")
+    px = torch.tensor(synth.pixel_set(14, 100, 100, 8), dtype=torch.int32, device="cuda")
+    K = M.intrinsics(138.9, 138.9, 50.0, 50.0, 100, 100)
+    out = gm.update(torch.tensor(P, device="cuda"), img, K, 2, px,
+                    M.UpdateOptions(n_coarse=16, n_fine=16))
+    w = out["w"].cpu().numpy()
+    assert w[3] == 0.0 and out["mask"][3].item() == 0 and math.isinf(out["logw"][3].item())
+    assert abs(w.sum() - 1.0) < 1e-12
+    rc, n = gm.read_status()
+    assert rc == M.MCL_ERR_NONFINITE and n == 1
