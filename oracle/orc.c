@@ -445,16 +445,22 @@ int orc_update(const float* blob, const int* arch, const double* particles,
         double s = 0.0;
         for (int j = 0; j < B; ++j) s += ef[(long)i * B + j];
         S[i] = s;
-        double sc = s > op->s_min ? s : op->s_min;
-        logw[i] = 4.0 * (log((double)B) - log(sc));
+        if (isfinite(s)) {
+            double sc = s > op->s_min ? s : op->s_min;
+            logw[i] = 4.0 * (log((double)B) - log(sc));
+        } else {
+            /* a particle whose loss is not a number carries no weight */
+            logw[i] = -INFINITY;
+        }
         if (logw[i] > mx) mx = logw[i];
     }
     double acc = 0.0;
-    for (int i = 0; i < N; ++i) acc += exp(logw[i] - mx);
+    if (mx > -INFINITY)
+        for (int i = 0; i < N; ++i) acc += exp(logw[i] - mx);
     double lse = mx + log(acc);
     for (int i = 0; i < N; ++i) {
-        w[i] = exp(logw[i] - lse);
-        mask[i] = (uint8_t)(w[i] >= op->rho / N);
+        w[i] = mx > -INFINITY ? exp(logw[i] - lse) : 0.0;
+        mask[i] = (uint8_t)(w[i] >= op->rho / N && w[i] > 0.0);
     }
     free(lvl); free(wd); free(ef);
     return err ? -1 : 0;
@@ -495,8 +501,9 @@ int orc_resample(const double* w, int n_in, int n_out, double u0, int32_t* idx) 
     if (T == 0) { free(C); return -1; }
     uint64_t U = (uint64_t)floor(ldexp(u0, 53));
     for (int k = 0; k < n_out; ++k) {
+        /* (k 2^53 + U) needs up to 69 bits: form it in 128 bits */
         unsigned __int128 rhs =
-            ((unsigned __int128)(((uint64_t)k << 53) + U)) * T;
+            ((((unsigned __int128)(uint64_t)k) << 53) + U) * (unsigned __int128)T;
         int found = n_in - 1;
         for (int i = 0; i < n_in; ++i) {
             unsigned __int128 lhs =

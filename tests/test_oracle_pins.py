@@ -318,6 +318,16 @@ def test_update_matches_rendered_rays():
     assert np.allclose((E * rr["F"]).reshape(len(P), -1).sum(1), r["S"], rtol=1e-14)
 
 
+def test_nonfinite_particle_gets_no_weight():
+    blob, P, img, K4, px, opts = _scene(15, 4, 8)
+    P = P[:-1].copy()
+    P[2, 3] = np.nan
+    r = oracle.update(blob, P, img, K4, 1, px, opts)
+    assert not np.isfinite(r["S"][2]) and r["logw"][2] == -np.inf
+    assert r["w"][2] == 0.0 and r["mask"][2] == 0
+    assert abs(r["w"].sum() - 1.0) < 1e-14
+
+
 def test_downscale_closed_forms():
     img = np.full((8, 12, 3), 0.37)
     assert np.allclose(oracle.downscale(img, 4), 0.37)
@@ -354,6 +364,33 @@ def test_resample_bruteforce_dyadic():
         u0 = float(rng.integers(0, 64)) / 64.0
         got = oracle.resample(w, n_out, u0).tolist()
         assert got == _systematic_exact(w, n_out, u0), (w, n_out, u0)
+
+
+def test_resample_large_n_out_exact_integers():
+    """N_out in the thousands (k 2^53 exceeds 64 bits): the definition
+    evaluated in exact integers for dyadic weights and a dyadic u0."""
+    for n_in, n_out, seed in ((5, 3000, 1), (40, 65536, 2), (7, 2049, 3)):
+        w = synth.random_weights(seed, n_in, dyadic_bits=6, zero_frac=0.2)
+        a = seed * 13 % 64                       # u0 = a / 64
+        q = [int(x) for x in w]                  # integer weights (dyadic, scaled)
+        C, run = [], 0
+        for x in q:
+            run += x
+            C.append(run)
+        T = C[-1]
+        # smallest i with C_i / T > (k + a/64) / n_out  <=>  64 C_i n_out > (64 k + a) T
+        exp_idx = [next(i for i, c in enumerate(C) if 64 * c * n_out > (64 * k + a) * T)
+                   for k in range(n_out)]
+        got = oracle.resample(w, n_out, a / 64.0).tolist()
+        assert got == exp_idx
+
+
+def test_resample_copy_counts_large():
+    w = synth.random_weights(17, 300)
+    for n in (4000, 65536):
+        cnt = np.bincount(oracle.resample(w, n, 0.61803), minlength=300)
+        assert cnt.sum() == n
+        assert np.all(cnt >= np.floor(n * w) - 1e-9) and np.all(cnt <= np.ceil(n * w) + 1e-9)
 
 
 def test_resample_copy_counts_and_frequencies():
