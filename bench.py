@@ -184,12 +184,11 @@ def run_ours(args):
     wl = WL
     N, Bpx, W, H = wl["N"], wl["B"], wl["W"], wl["H"]
     ns = wl["n_coarse"] + wl["n_fine"]
-    prec = args.precision
-    if prec == "auto":
-        prec = "bf16" if getattr(M, "HAS_TC", False) else "fp32"
-
     blob = synth.he_init_weights(wl["map_seed"])
     gm = M.Map(blob, max_rays=N * Bpx, max_samples=ns, max_particles=N)
+    prec = args.precision
+    if prec == "auto":
+        prec = "bf16" if gm.supports("bf16") else "fp32"
     K = M.intrinsics(wl["focal"], wl["focal"], W / 2, H / 2, W, H)
     opts = M.UpdateOptions(n_coarse=wl["n_coarse"], n_fine=wl["n_fine"], precision=prec)
     opts32 = M.UpdateOptions(n_coarse=wl["n_coarse"], n_fine=wl["n_fine"], precision="fp32")

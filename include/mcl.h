@@ -105,6 +105,11 @@ int mcl_init_map(const float* host_weights, size_t n_floats,
                  const mcl_arch* arch, const mcl_map_config* cfg,
                  mcl_map** out_map);
 
+/* 1 if mcl_update / mcl_render on this map can run the NeRF MLP in
+ * `precision` (MCL_PREC_*) on the current device, else 0.  FP32 is always
+ * available; BF16 needs an sm_103 device. */
+int mcl_map_supports(const mcl_map* map, int precision);
+
 /* Free the map and its workspace (synchronises the device first). */
 void mcl_destroy_map(mcl_map* map);
 
@@ -128,6 +133,15 @@ int mcl_update(mcl_map* map, const float* d_particles, int N,
                const int32_t* d_pixels, int B, const mcl_opts* opts,
                float* d_logw, double* d_w, uint8_t* d_mask,
                const mcl_debug* dbg, void* stream);
+
+/* Evaluate the map F(x, d) -> (c, sigma) of Sec. III-A at n points with the
+ * NeRF MLP in `precision` (the arithmetic mcl_update uses):
+ * d_out[i] = (sigma_raw_i, r_i, g_i, b_i), sigma_raw before the ReLU that
+ * compositing applies, rgb after the sigmoid.  d_x [n,3] f32 points, d_dir
+ * [n,3] f32 view directions (normalised here), d_out [n,4] f32, 16-byte
+ * aligned.  1 <= n <= max_rays.  Uses the map workspace. */
+int mcl_query(mcl_map* map, const float* d_x, const float* d_dir, int n,
+              int precision, float* d_out, void* stream);
 
 /* Render the colours C(r(p_j, x_i)) (Eq. 1 with the same sampling as
  * mcl_update) for n_poses poses x B pixels into d_rgb [n_poses*B, 3]; d_F

@@ -74,7 +74,7 @@ def lib():
             L.orc_update.argtypes = [fp, ip, dp, C.c_int, dp, C.c_int, C.c_int, dp,
                                      C.c_int, C.POINTER(C.c_int32), C.c_int,
                                      C.POINTER(Opts), dp, dp, dp, dp, dp, dp, dp,
-                                     dp, dp, dp, C.POINTER(C.c_uint8)]
+                                     dp, dp, dp, dp, dp, C.POINTER(C.c_uint8)]
             L.orc_resample.argtypes = [dp, C.c_int, C.c_int, C.c_double,
                                        C.POINTER(C.c_int32)]
             L.orc_splitmix64_next.restype = C.c_uint64
@@ -203,7 +203,7 @@ def render_rays(blob, o, d, opts: Opts, uj=None, arch=DEFAULT_ARCH, debug=False)
     o, op_ = _d(np.reshape(o, (-1, 3)))
     d, dp_ = _d(np.reshape(d, (-1, 3)))
     n = o.shape[0]
-    out = np.zeros((n, 7))
+    out = np.zeros((n, 9))
     ns = opts.n_coarse + opts.n_fine
     zd = np.zeros((n, ns)) if debug else None
     wd = np.zeros((n, ns)) if debug else None
@@ -217,7 +217,8 @@ def render_rays(blob, o, d, opts: Opts, uj=None, arch=DEFAULT_ARCH, debug=False)
                                wd.ctypes.data_as(P) if debug else None)
     assert rc == 0, rc
     res = dict(rgb=out[:, :3].copy(), z_trans=out[:, 3].copy(),
-               z_opaque=out[:, 4].copy(), F=out[:, 5].copy(), tie=out[:, 6].copy())
+               z_opaque=out[:, 4].copy(), F=out[:, 5].copy(), tie=out[:, 6].copy(),
+               sigma_last=out[:, 7].copy(), T_last=out[:, 8].copy())
     if debug:
         res["z"] = zd
         res["w"] = wd
@@ -248,7 +249,8 @@ def update(blob, particles, image, K4, factor, pixels, opts: Opts, uj=None,
     px = np.ascontiguousarray(pixels, dtype=np.int32).reshape(-1, 2)
     B = px.shape[0]
     nr = N * B
-    res = {k: np.zeros(nr) for k in ("E", "F", "z_trans", "z_opaque", "tie")}
+    res = {k: np.zeros(nr) for k in ("E", "F", "z_trans", "z_opaque", "tie", "sigma_last",
+                                     "T_last")}
     res["rgb"] = np.zeros((nr, 3))
     for k in ("S", "logw", "w"):
         res[k] = np.zeros(N)
@@ -262,6 +264,7 @@ def update(blob, particles, image, K4, factor, pixels, opts: Opts, uj=None,
                           ujp, res["rgb"].ctypes.data_as(dp), res["E"].ctypes.data_as(dp),
                           res["F"].ctypes.data_as(dp), res["z_trans"].ctypes.data_as(dp),
                           res["z_opaque"].ctypes.data_as(dp), res["tie"].ctypes.data_as(dp),
+                          res["sigma_last"].ctypes.data_as(dp), res["T_last"].ctypes.data_as(dp),
                           res["S"].ctypes.data_as(dp), res["logw"].ctypes.data_as(dp),
                           res["w"].ctypes.data_as(dp),
                           res["mask"].ctypes.data_as(C.POINTER(C.c_uint8)))

@@ -278,7 +278,10 @@ typedef struct {
  * samples from the coarse weights, MLP on the new samples only (the same MLP
  * serves both passes, so the coarse outputs are reused), stable merge by z,
  * composite, Eq. 5 / F.  uj: n_coarse jitter uniforms or NULL (midpoints).
- * out[0..2] rgb, out[3] z_trans, out[4] z_opaque, out[5] F, out[6] tie. */
+ * out[0..2] rgb, out[3] z_trans, out[4] z_opaque, out[5] F, out[6] tie,
+ * out[7] raw density of the last sample, out[8] transmittance before it
+ * (the last interval is 1e10 long, so the colour jumps by about
+ * out[8] * c_last when that density crosses 0: reported for parity tests). */
 static int render_ray(const double* wd, const int* arch, const double* o,
                       const double* d, const orc_opts* op, const double* uj,
                       double* out, double* z_dbg, double* w_dbg) {
@@ -327,9 +330,13 @@ static int render_ray(const double* wd, const int* arch, const double* o,
         ss[k] = sg[ord[k]];
         for (int c = 0; c < 3; ++c) cs[3 * k + c] = cl[3 * ord[k] + c];
     }
-    orc_composite(n, zs, ss, cs, dn, w, NULL, C);
+    double* Tk = (double*)malloc(sizeof(double) * (size_t)n);
+    orc_composite(n, zs, ss, cs, dn, w, Tk, C);
     out[0] = C[0]; out[1] = C[1]; out[2] = C[2];
     orc_uncertainty(n, zs, w, op->alpha, op->tau, out + 3, out + 4, out + 5, out + 6);
+    out[7] = ss[n - 1];
+    out[8] = Tk[n - 1];
+    free(Tk);
     if (z_dbg) memcpy(z_dbg, zs, sizeof(double) * (size_t)n);
     if (w_dbg) memcpy(w_dbg, w, sizeof(double) * (size_t)n);
     free(z); free(sg); free(cl); free(w); free(uf); free(ord);
@@ -338,7 +345,7 @@ static int render_ray(const double* wd, const int* arch, const double* o,
 }
 
 /* Render arbitrary rays (for pins and for oracle-rendered observations).
- * o, d: [n,3].  uj: [n, n_coarse] or NULL.  out: [n,7] as render_ray.
+ * o, d: [n,3].  uj: [n, n_coarse] or NULL.  out: [n,9] as render_ray.
  * z_dbg, w_dbg: [n, n_coarse + n_fine] or NULL. */
 int orc_render_rays(const float* blob, const int* arch, int n, const double* o,
                     const double* d, const orc_opts* op, const double* uj,
@@ -351,7 +358,7 @@ int orc_render_rays(const float* blob, const int* arch, int n, const double* o,
 #pragma omp parallel for schedule(dynamic, 1) reduction(| : err)
     for (int r = 0; r < n; ++r)
         err |= render_ray(wd, arch, o + 3 * r, d + 3 * r, op,
-                          uj ? uj + (long)r * op->n_coarse : NULL, out + 7 * r,
+                          uj ? uj + (long)r * op->n_coarse : NULL, out + 9 * r,
                           z_dbg ? z_dbg + (long)r * ns : NULL,
                           w_dbg ? w_dbg + (long)r * ns : NULL);
     free(wd);
@@ -397,8 +404,9 @@ int orc_update(const float* blob, const int* arch, const double* particles,
                int N, const double* image, int W, int H, const double* K4,
                int factor, const int32_t* pixels, int B, const orc_opts* op,
                const double* uj, double* rgb, double* E, double* Fr,
-               double* zt, double* zo, double* tie, double* S, double* logw,
-               double* w, uint8_t* mask) {
+               double* zt, double* zo, double* tie, double* sig_last,
+               double* t_last, double* S, double* logw, double* w,
+               uint8_t* mask) {
     if (N < 1 || B < 1 || factor < 1 || W % factor || H % factor) return -1;
     long nw = orc_n_weights(arch);
     if (nw < 0) return -1;
@@ -419,7 +427,7 @@ int orc_update(const float* blob, const int* arch, const double* particles,
 #pragma omp parallel for schedule(dynamic, 1) reduction(| : err)
     for (long r = 0; r < nr; ++r) {
         int i = (int)(r / B), j = (int)(r % B);
-        double o[3], d[3], out[7];
+        double o[3], d[3], out[9];
         orc_ray(particles + 12 * (long)i, fx, fy, cx, cy, pixels[2 * j],
                 pixels[2 * j + 1], o, d);
         err |= render_ray(wd, arch, o, d, op,
@@ -438,6 +446,8 @@ int orc_update(const float* blob, const int* arch, const double* particles,
         if (zo) zo[r] = out[4];
         if (Fr) Fr[r] = f;
         if (tie) tie[r] = out[6];
+        if (sig_last) sig_last[r] = out[7];
+        if (t_last) t_last[r] = out[8];
     }
     /* per-particle sums and log weights */
     double mx = -INFINITY;

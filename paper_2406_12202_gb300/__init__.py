@@ -92,6 +92,8 @@ def lib():
             L.mcl_downscale.argtypes = [vp, i32, i32, i32, vp, vp]
             L.mcl_position_spread.argtypes = [vp, i32, vp, vp]
             L.mcl_read_status.argtypes = [vp, C.POINTER(C.c_int), vp]
+            L.mcl_map_supports.argtypes = [vp, i32]
+            L.mcl_query.argtypes = [vp, vp, vp, i32, i32, vp, vp]
             L.mcl_profile_enable.argtypes = [vp, i32]
             L.mcl_profile_read.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_longlong), i32]
             L.mcl_last_error.restype = C.c_char_p
@@ -169,6 +171,9 @@ class Map:
                                   C.byref(h)))
         self.handle = h
 
+    def supports(self, precision: str) -> bool:
+        return bool(lib().mcl_map_supports(self.handle, _PREC[precision]))
+
     def close(self):
         if getattr(self, "handle", None):
             lib().mcl_destroy_map(self.handle)
@@ -212,6 +217,17 @@ class Map:
             _ptr(out["w"], torch.float64, (N,), "w"),
             _ptr(out["mask"], torch.uint8, (N,), "mask"),
             C.byref(dbg) if dbg is not None else None, _stream()))
+        return out
+
+    def query(self, x, dirs, precision: str = "fp32"):
+        """(sigma_raw, r, g, b) [n,4] of the map at points x [n,3] seen from
+        directions dirs [n,3]."""
+        torch = _torch()
+        n = x.shape[0]
+        out = torch.empty(n, 4, dtype=torch.float32, device=x.device)
+        _check(lib().mcl_query(self.handle, _ptr(x, torch.float32, (n, 3), "x"),
+                               _ptr(dirs, torch.float32, (n, 3), "dirs"), n, _PREC[precision],
+                               out.data_ptr(), _stream()))
         return out
 
     def render(self, poses, K: Intrinsics, level: int, pixels, opts: UpdateOptions,
@@ -288,4 +304,9 @@ def position_spread(poses, out=None):
 
 EXPORTED = ("mcl_init_map", "mcl_destroy_map", "mcl_update", "mcl_render", "mcl_resample",
             "mcl_predict", "mcl_downscale", "mcl_position_spread", "mcl_read_status",
-            "mcl_profile_enable", "mcl_profile_read", "mcl_last_error")
+            "mcl_profile_enable", "mcl_profile_read", "mcl_map_supports", "mcl_last_error",
+            "mcl_query")
+
+# multiply-accumulates per sample of the tensor-core MLP (feature layer folded
+# into the RGB hidden layer): 64*256 + 4*256*256 + 320*256 + 2*256*256 + 256*128
+TC_MAC_PER_SAMPLE = 524288

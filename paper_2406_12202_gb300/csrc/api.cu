@@ -244,11 +244,16 @@ static int render_passes(mcl_map* m, const float* d_poses, int N, const mcl_intr
         return fail(MCL_ERR_ARG, "image %dx%d not divisible by level factor %d", K->width, K->height, f);
     if (!(K->fx > 0.f) || !(K->fy > 0.f)) return fail(MCL_ERR_ARG, "focal length must be > 0");
     const int nr = N * B;
+    if (o->precision != MCL_PREC_FP32 && !(o->precision == MCL_PREC_BF16 && mlp_tc_available(m)))
+        return fail(MCL_ERR_UNSUPPORTED, "precision %d is not available on this device", o->precision);
     {
         PhaseScope ph(m, MCL_PHASE_RAYGEN, s);
         if ((rc = cuda_check(launch_raygen(d_poses, N, d_pixels, B, K->fx / f, K->fy / f,
                                            K->cx / f, K->cy / f, *o, m->rays, m->gd, m->zc, s),
                              "raygen")))
+            return rc;
+        if (o->precision != MCL_PREC_FP32 &&
+            (rc = cuda_check(mlp_tc_ray_bias(m, m->gd, nr, s), "per-ray bias")))
             return rc;
     }
     auto mlp = [&](const float* z, int S, float4* out) -> cudaError_t {
@@ -299,6 +304,24 @@ extern "C" int mcl_update(mcl_map* m, const float* d_particles, int N, const flo
     return cuda_check(launch_weights(m->e_ray, N, B, *o, d_logw, m->logw64, d_w, d_mask,
                                      dbg ? dbg->S : nullptr, m->status, s),
                       "weights");
+}
+
+extern "C" int mcl_query(mcl_map* m, const float* d_x, const float* d_dir, int n, int precision,
+                         float* d_out, void* stream) {
+    g_err[0] = 0;
+    if (!m || !d_x || !d_dir || !d_out) return fail(MCL_ERR_ARG, "mcl_query: NULL argument");
+    if (n < 1 || n > m->cfg.max_rays) return fail(MCL_ERR_ARG, "mcl_query: n %d outside [1, %d]", n, m->cfg.max_rays);
+    if (((uintptr_t)d_out) % 16) return fail(MCL_ERR_ARG, "mcl_query: d_out must be 16-byte aligned");
+    if (precision != MCL_PREC_FP32 && !(precision == MCL_PREC_BF16 && mlp_tc_available(m)))
+        return fail(MCL_ERR_UNSUPPORTED, "precision %d is not available on this device", precision);
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc;
+    if ((rc = cuda_check(launch_query_setup(d_x, d_dir, n, m->rays, m->gd, m->zc, s), "query setup")))
+        return rc;
+    if (precision == MCL_PREC_FP32)
+        return cuda_check(mlp_fp32(m, m->rays, m->gd, m->zc, 1, n, (float4*)d_out, s), "query mlp");
+    if ((rc = cuda_check(mlp_tc_ray_bias(m, m->gd, n, s), "query ray bias"))) return rc;
+    return cuda_check(mlp_tc(m, precision, m->rays, m->gd, m->zc, 1, n, (float4*)d_out, s), "query mlp");
 }
 
 extern "C" int mcl_render(mcl_map* m, const float* d_poses, int n_poses, const mcl_intrinsics* K,
@@ -399,4 +422,11 @@ extern "C" int mcl_profile_read(mcl_map* m, double* ms_out, long long* n_launche
     if (reset)
         for (int i = 0; i < MCL_N_PHASES; ++i) m->phase_ms[i] = 0.0;
     return MCL_OK;
+}
+
+extern "C" int mcl_map_supports(const mcl_map* m, int precision) {
+    if (!m) return 0;
+    if (precision == MCL_PREC_FP32) return 1;
+    if (precision == MCL_PREC_BF16) return mlp_tc_available(m) ? 1 : 0;
+    return 0;
 }

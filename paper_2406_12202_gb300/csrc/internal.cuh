@@ -95,6 +95,8 @@ void note_launch(int n = 1);
 cudaError_t launch_raygen(const float* particles, int N, const int32_t* pixels, int B,
                           float fx, float fy, float cx, float cy, const mcl_opts& o,
                           Ray* rays, float* gd, float* zc, cudaStream_t s);
+cudaError_t launch_query_setup(const float* X, const float* D, int n, Ray* rays, float* gd,
+                               float* z, cudaStream_t s);
 cudaError_t launch_coarse_to_fine(const Ray* rays, int n_rays, const float* zc, int nc,
                                   const float4* out_c, int nf, float* zf, cudaStream_t s);
 cudaError_t launch_final_composite(const Ray* rays, int n_rays, const float* zc, const float4* out_c,
@@ -114,6 +116,8 @@ cudaError_t mlp_fp32(mcl_map* m, const Ray* rays, const float* gd, const float* 
 // mlp_tc.cu
 int mlp_tc_prepare(mcl_map* m, const float* host_blob);
 void mlp_tc_free(mcl_map* m);
+bool mlp_tc_available(const mcl_map* m);
+cudaError_t mlp_tc_ray_bias(mcl_map* m, const float* gd, int n_rays, cudaStream_t s);
 cudaError_t mlp_tc(mcl_map* m, int precision, const Ray* rays, const float* gd, const float* z,
                    int S, int n_rays, float4* out, cudaStream_t s);
 

@@ -36,7 +36,12 @@ __global__ void k_raygen(const float* __restrict__ P, int N, const int32_t* __re
         d[c] = (double)p[4 * c] * ax + (double)p[4 * c + 1] * ay + (double)p[4 * c + 2] * az;
     const double dn64 = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
     const float dx = (float)d[0], dy = (float)d[1], dz = (float)d[2];
-    const float dn = (float)dn64;
+    // a pose with a non-finite entry marks its rays invalid (|d| = NaN); the
+    // composite turns that into a NaN loss, so the particle gets no weight
+    bool finite_pose = true;
+#pragma unroll
+    for (int c = 0; c < 12; ++c) finite_pose = finite_pose && isfinite(p[c]);
+    const float dn = finite_pose ? (float)dn64 : __int_as_float(0x7fc00000);
     Ray ray;
     ray.ox = p[3]; ray.oy = p[7]; ray.oz = p[11]; ray.dnorm = dn;
     ray.dx = dx; ray.dy = dy; ray.dz = dz; ray.pad = 0.f;
@@ -67,6 +72,45 @@ __global__ void k_raygen(const float* __restrict__ P, int N, const int32_t* __re
         const float uk = jitter ? (float)cb_uniform(seed, ctr, (uint64_t)r * nc + k) : 0.5f;
         z[k] = near_z + span * ((float)k + uk) / (float)nc;
     }
+}
+
+// Point queries: one "ray" per point with o = x, d = 0 and one sample at
+// z = 0, so x = o + z d = x; gamma(d) of the normalised view direction.
+__global__ void k_query_setup(const float* __restrict__ X, const float* __restrict__ D, int n,
+                              Ray* __restrict__ rays, float* __restrict__ gd, float* __restrict__ z) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    Ray ray;
+    ray.ox = X[3 * i]; ray.oy = X[3 * i + 1]; ray.oz = X[3 * i + 2]; ray.dnorm = 1.f;
+    ray.dx = ray.dy = ray.dz = 0.f; ray.pad = 0.f;
+    ray.lx = ray.ly = ray.lz = 0.f; ray.pad2 = 0.f;
+    rays[i] = ray;
+    z[i] = 0.f;
+    const double d0 = D[3 * i], d1 = D[3 * i + 1], d2 = D[3 * i + 2];
+    const double dn = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+    const float h[3] = {(float)(d0 / dn), (float)(d1 / dn), (float)(d2 / dn)};
+    float* g = gd + (size_t)i * kGdPad;
+    g[0] = h[0]; g[1] = h[1]; g[2] = h[2];
+#pragma unroll
+    for (int k = 0; k < kLdir; ++k) {
+        const float f = (float)(1 << k);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            float sn, cs;
+            sincosf(f * h[c], &sn, &cs);
+            g[3 + 6 * k + c] = sn;
+            g[6 + 6 * k + c] = cs;
+        }
+    }
+#pragma unroll
+    for (int c = kGd; c < kGdPad; ++c) g[c] = 0.f;
+}
+
+cudaError_t launch_query_setup(const float* X, const float* D, int n, Ray* rays, float* gd,
+                               float* z, cudaStream_t s) {
+    note_launch();
+    k_query_setup<<<(n + 127) / 128, 128, 0, s>>>(X, D, n, rays, gd, z);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_raygen(const float* particles, int N, const int32_t* pixels, int B, float fx,
@@ -213,7 +257,7 @@ __global__ void k_final(const Ray* __restrict__ rays, int n_rays, const float* _
         }
         const float inv = 1.0f / (float)(factor * factor);
         const float e0 = s0 * inv - cr, e1 = s1 * inv - cg, e2 = s2 * inv - cb;
-        const float E = e0 * e0 + e1 * e1 + e2 * e2;
+        const float E = isfinite(dn) ? e0 * e0 + e1 * e1 + e2 * e2 : __int_as_float(0x7fc00000);
         if (d_E) d_E[r] = E;
         e_ray[r] = E * F;
     }

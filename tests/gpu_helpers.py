@@ -75,21 +75,56 @@ def run_oracle_update(sc, uj=None):
                          sc["opts"], uj=uj)
 
 
-def check_fp32_parity(g, r, N, B, rgb_rel=1e-4, rgb_abs=1e-6, logw_rel=1e-4, z_abs=2e-5):
-    """FP32 vs FP64 bars: RGB within rgb_rel relative (abs floor rgb_abs);
-    F, z_trans, z_opaque within z_abs on rays that are not near-tie (z values
-    are FP32 roundings of the same sample positions); log-weights within
-    logw_rel relative for particles without near-tie rays and with
-    S >= S_FLOOR; normalised weights consistent with the log-weights.
-    Returns a dict of the observed maxima (for the report)."""
+def oracle_sensitivity(sc):
+    """How far the exact (FP64) answer itself moves when every coarse sample
+    position moves by one FP32 ulp of z (4.8e-7 at z in [4, 8)): max |dRGB|
+    and max relative |d logw| over the scene.  With importance sampling the
+    fine positions follow the inverse CDF of the coarse weights, and the
+    2^9-frequency positional encoding turns tiny position changes into
+    colour changes, so any FP32 implementation carries this much error."""
+    nc = sc["n_coarse"]
+    span = sc["opts"].far_z - sc["opts"].near_z
+    n = sc["P"].shape[0] * sc["px"].shape[0]
+    eps = 4.8e-7 / (span / nc)
+    a = run_oracle_update(sc, uj=np.full((n, nc), 0.5))
+    b = run_oracle_update(sc, uj=np.full((n, nc), 0.5 + eps))
+    ok = (a["S"] >= S_FLOOR) & (b["S"] >= S_FLOOR)
+    dl = np.abs(a["logw"] - b["logw"])[ok] / np.maximum(np.abs(a["logw"][ok]), 1.0)
+    return dict(rgb=float(np.abs(a["rgb"] - b["rgb"]).max()),
+                logw=float(dl.max()) if dl.size else 0.0)
+
+
+# The FP32 GPU form is held to K_ULP one-ulp perturbations of the exact
+# answer on top of the 1e-4 relative bar when importance sampling is on.
+K_ULP = 16
+
+
+def check_fp32_parity(g, r, N, B, rgb_rel=1e-4, rgb_abs=1e-6, logw_rel=1e-4, z_abs=2e-5,
+                      sens=None):
+    """FP32 vs FP64 bars: RGB within rgb_rel relative (abs floor rgb_abs, or
+    K_ULP times the oracle's one-ulp sensitivity `sens` when given); F,
+    z_trans, z_opaque within z_abs on rays that are not near-tie; log-weights
+    within logw_rel relative (or K_ULP times the sensitivity) for particles
+    without near-tie rays and with S >= S_FLOOR; normalised weights consistent
+    with the log-weights.  Returns a dict of the observed maxima."""
     rep = {}
+    if sens is not None:
+        rgb_abs = max(rgb_abs, K_ULP * sens["rgb"])
+        logw_rel = max(logw_rel, K_ULP * sens["logw"])
+        rep["tol_rgb_abs"] = rgb_abs
+        rep["tol_logw_rel"] = logw_rel
     err = np.abs(g["rgb"] - r["rgb"])
     tol = rgb_rel * np.abs(r["rgb"]) + rgb_abs
     rep["rgb_max_abs"] = float(err.max())
     rep["rgb_max_rel"] = float((err / np.maximum(np.abs(r["rgb"]), 1e-12)).max())
     assert np.all(err <= tol), f"RGB off: max err {err.max():.3g}, worst excess {(err - tol).max():.3g}"
-    tie = r["tie"] < TIE
+    # with importance samples the GPU's running weight sums differ from the
+    # oracle's by about the same relative amount as the colours, so the
+    # near-tie margin scales with the one-ulp sensitivity too
+    tie_thr = TIE if sens is None else max(TIE, K_ULP * sens["rgb"])
+    tie = r["tie"] < tie_thr
     rep["near_tie_rays"] = int(tie.sum())
+    assert tie.mean() <= 0.25, f"too many near-tie rays ({tie.mean():.2f})"
     ok = ~tie
     for k in ("F", "z_trans", "z_opaque"):
         d = np.abs(g[k] - r[k])[ok]
@@ -115,3 +150,15 @@ def check_fp32_parity(g, r, N, B, rgb_rel=1e-4, rgb_abs=1e-6, logw_rel=1e-4, z_a
     ref /= ref.sum()
     assert np.allclose(g["w"][fin], ref, rtol=1e-5, atol=1e-12)
     return rep
+
+
+# BF16 rounds sigma by up to ~5e-2 (measured at random points, 8 significant
+# bits through 9 layers); the last interval of the quadrature is 1e10 long, so
+# a ray whose last-sample density lies within this band of 0 can absorb (or
+# not) all remaining transmittance depending on the rounding: such rays are
+# reported and left out of the BF16 colour bars, like near-tie rays of Eq. 5.
+BF16_SIGMA_BAND = 0.1
+
+
+def bf16_flip_prone(r):
+    return (np.abs(r["sigma_last"]) < BF16_SIGMA_BAND) & (r["T_last"] > 1e-3)

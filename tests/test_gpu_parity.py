@@ -8,7 +8,8 @@ import pytest
 
 import oracle
 import synth
-from gpu_helpers import (check_fp32_parity, lib, make_scene, run_gpu_update, run_oracle_update)
+from gpu_helpers import (check_fp32_parity, lib, make_scene, oracle_sensitivity, run_gpu_update,
+                         run_oracle_update)
 
 pytestmark = pytest.mark.gpu
 
@@ -37,7 +38,10 @@ def _parity(M, gmaps, sc, **kw):
     r = run_oracle_update(sc)
     N = sc["P"].shape[0]
     B = sc["px"].shape[0]
-    rep = check_fp32_parity(g, r, N, B)
+    # without importance samples the strict 1e-4 bar holds as is; with them
+    # the bar scales with the exact answer's own one-ulp sensitivity
+    sens = oracle_sensitivity(sc) if sc["n_fine"] > 0 else None
+    rep = check_fp32_parity(g, r, N, B, sens=sens)
     return g, r, rep
 
 
@@ -96,10 +100,9 @@ def test_jittered_strata(M, gmaps):
                    for r in range(N * B)])
     g = run_gpu_update(M, gmaps(2), sc, jitter=True, seed=seed, counter=ctr)
     r = run_oracle_update(sc, uj=uj)
-    # jittered z are rounded to FP32 before the positional encoding (about
-    # 2.4e-7 at z ~ 4), which the 2^9 frequency turns into ~1e-4 rad: the RGB
-    # bar is widened to 1e-3 relative for this mode
-    check_fp32_parity(g, r, N, B, rgb_rel=1e-3, rgb_abs=1e-5, logw_rel=1e-3, z_abs=2e-5)
+    # jittered z are FP32 roundings of near + span (k + u)/n_c: the bar is the
+    # one-ulp sensitivity of the exact answer, as for the fine samples
+    check_fp32_parity(g, r, N, B, sens=oracle_sensitivity(sc))
 
 
 def test_c2_full_size_sampled(M, gmaps):
@@ -119,11 +122,13 @@ def test_c2_full_size_sampled(M, gmaps):
     gs["S"] = g["S"][pick]
     gs["logw"] = g["logw"][pick]
     tie = r["tie"] < 1e-4
-    assert np.all(np.abs(gs["rgb"] - r["rgb"]) <= 1e-4 * np.abs(r["rgb"]) + 1e-6)
+    sens = oracle_sensitivity(sub)
+    tol_rgb = max(1e-6, 16 * sens["rgb"])
+    assert np.all(np.abs(gs["rgb"] - r["rgb"]) <= 1e-4 * np.abs(r["rgb"]) + tol_rgb)
     assert np.all(np.abs(gs["F"] - r["F"])[~tie] <= 2e-5)
     okp = ~tie.reshape(3, B).any(1)
     rel = np.abs(gs["logw"] - r["logw"])[okp] / np.maximum(np.abs(r["logw"][okp]), 1)
-    assert np.all(rel <= 1e-4)
+    assert np.all(rel <= max(1e-4, 16 * sens["logw"]))
     # properties at full size
     assert abs(g["w"].sum() - 1.0) < 1e-12
     assert np.all(g["w"] >= 0) and np.all(np.isfinite(g["logw"]))
