@@ -245,27 +245,44 @@ void orc_sample_pdf(int n_c, const double* z_c, const double* w_c, int n_f,
 /*   z_trans  = z_k for the smallest k with W_k >= alpha (else z_0);         */
 /*   z_opaque = z_k for the largest  k with W_k <= 1 - alpha (else z_0);     */
 /*   F = max(z_opaque - z_trans, tau).                                       */
-/* tie = min_k min(|W_k - alpha|, |W_k - (1 - alpha)|): how close the ray is */
-/* to flipping one of the two decisions (reported for parity tests).        */
+/* tie: how far the running sum is from flipping either decision, i.e. the   */
+/* distance to alpha of W at the chosen k_trans and at k_trans - 1, and the  */
+/* distance to 1 - alpha of W at k_opaque and k_opaque + 1 (reported for     */
+/* parity tests; not part of the method).                                    */
 /* ------------------------------------------------------------------------ */
 void orc_uncertainty(int n, const double* z, const double* w, double alpha,
                      double tau, double* z_trans, double* z_opaque, double* F,
                      double* tie) {
-    double Wc = 0.0, m = INFINITY;
+    double Wc = 0.0;
     int kt = -1, ko = -1;
+    double* W = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
     for (int k = 0; k < n; ++k) {
         Wc += w[k];
+        W[k] = Wc;
         if (kt < 0 && Wc >= alpha) kt = k;
         if (Wc <= 1.0 - alpha) ko = k;
-        double d1 = fabs(Wc - alpha), d2 = fabs(Wc - (1.0 - alpha));
-        if (d1 < m) m = d1;
-        if (d2 < m) m = d2;
     }
     *z_trans = kt >= 0 ? z[kt] : z[0];
     *z_opaque = ko >= 0 ? z[ko] : z[0];
     double g = *z_opaque - *z_trans;
     *F = g > tau ? g : tau;
-    if (tie) *tie = m;
+    if (tie) {
+        double m = INFINITY, d;
+        if (kt >= 0) {
+            d = W[kt] - alpha; if (d < m) m = d;
+            d = alpha - (kt > 0 ? W[kt - 1] : 0.0); if (d < m) m = d;
+        } else if (n > 0) {
+            d = alpha - W[n - 1]; if (d < m) m = d;
+        }
+        if (ko >= 0) {
+            d = (1.0 - alpha) - W[ko]; if (d < m) m = d;
+            if (ko + 1 < n) { d = W[ko + 1] - (1.0 - alpha); if (d < m) m = d; }
+        } else if (n > 0) {
+            d = W[0] - (1.0 - alpha); if (d < m) m = d;
+        }
+        *tie = m;
+    }
+    free(W);
 }
 
 /* Options of one update (mirrored by a ctypes Structure in oracle/__init__). */

@@ -94,6 +94,7 @@ def lib():
             L.mcl_read_status.argtypes = [vp, C.POINTER(C.c_int), vp]
             L.mcl_map_supports.argtypes = [vp, i32]
             L.mcl_query.argtypes = [vp, vp, vp, i32, i32, vp, vp]
+            L.mcl_resample_noalloc.argtypes = [vp, i32, i32, f64, vp, vp]
             L.mcl_profile_enable.argtypes = [vp, i32]
             L.mcl_profile_read.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_longlong), i32]
             L.mcl_last_error.restype = C.c_char_p
@@ -270,6 +271,24 @@ class Map:
         return rc, n.value
 
 
+RESAMPLE_NOALLOC_MAX_IN = 65536
+
+
+def resample_noalloc(w, n_out: int, u0: float, idx=None):
+    """Systematic resampling without a map and without any device allocation
+    in the library (mcl_resample_noalloc).  Same indices as Map.resample for
+    the same weights and u0.  Calls that overlap on the GPU race on the
+    library's fixed scratch, so issue them from one stream."""
+    torch = _torch()
+    n_in = w.shape[0]
+    if idx is None:
+        idx = torch.empty(n_out, dtype=torch.int32, device=w.device)
+    _check(lib().mcl_resample_noalloc(_ptr(w, torch.float64, (n_in,), "w"), n_in, int(n_out),
+                                      float(u0), _ptr(idx, torch.int32, (n_out,), "idx"),
+                                      _stream()))
+    return idx
+
+
 def predict(poses, idx, n_out: int, sigma_t: float, sigma_yaw: float, seed: int, counter: int,
             out=None):
     torch = _torch()
@@ -305,8 +324,11 @@ def position_spread(poses, out=None):
 EXPORTED = ("mcl_init_map", "mcl_destroy_map", "mcl_update", "mcl_render", "mcl_resample",
             "mcl_predict", "mcl_downscale", "mcl_position_spread", "mcl_read_status",
             "mcl_profile_enable", "mcl_profile_read", "mcl_map_supports", "mcl_last_error",
-            "mcl_query")
+            "mcl_resample_noalloc", "mcl_query")
 
-# multiply-accumulates per sample of the tensor-core MLP (feature layer folded
-# into the RGB hidden layer): 64*256 + 4*256*256 + 320*256 + 2*256*256 + 256*128
-TC_MAC_PER_SAMPLE = 524288
+# Algorithmic multiply-accumulates per sample of the network the tensor-core
+# form evaluates (the linear feature layer folded into the RGB hidden layer):
+# trunk 63*256 + 4*256^2 + 319*256 + 2*256^2, RGB hidden 256*128, density
+# head 256, RGB output 128*3 (the per-ray gamma(d) term is per ray, not per
+# sample).  Padding (63 -> 64, 319 -> 320, N 129 -> 144) is not counted.
+TC_MAC_PER_SAMPLE = 63 * 256 + 4 * 256 * 256 + 319 * 256 + 2 * 256 * 256 + 256 * 128 + 256 + 384

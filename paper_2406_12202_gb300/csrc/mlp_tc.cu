@@ -17,7 +17,8 @@
 // TMA through a 4-stage ring; warp 1 allocates TMEM and issues the MMAs for
 // both tiles from the same weight block (M = 128, N = 256, K = 16 per
 // instruction); warps 2-5 and 6-9 run prologue and epilogues of tile 0 and
-// tile 1.  Every wait is bounded (see tc_ptx.cuh).
+// tile 1 (one warp per TMEM lane quadrant, one thread per row).  Every wait
+// is bounded (see tc_ptx.cuh).
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <math.h>
@@ -28,22 +29,47 @@
 #include "internal.cuh"
 #include "tc_ptx.cuh"
 
+#ifdef MCL_TC_TRACE
+// Timeline instrumentation of CTA 0 (compiled only with -DMCL_TC_TRACE):
+// globaltimer stamps of the MMA issuer, the first row of each tile's
+// epilogue and the TMA producer for the first two tile pairs.
+constexpr int kTraceSlots = 16, kTraceLen = 128;
+__device__ unsigned long long g_tc_trace[kTraceSlots * kTraceLen];
+#define TC_TRACE(slot, idx)                                                           \
+    do {                                                                              \
+        if (blockIdx.x == 0 && (slot) < kTraceSlots && (idx) < kTraceLen)             \
+            g_tc_trace[(slot) * kTraceLen + (idx)] = mcl::tc::globaltimer();          \
+    } while (0)
+extern "C" int mcl_tc_trace_read(unsigned long long* out, int n) {
+    const int m = n < kTraceSlots * kTraceLen ? n : kTraceSlots * kTraceLen;
+    return (int)cudaMemcpyFromSymbol(out, g_tc_trace, sizeof(unsigned long long) * m);
+}
+#else
+#define TC_TRACE(slot, idx) \
+    do {                    \
+    } while (0)
+#endif
+
 namespace mcl {
 
 using namespace tc;
 
 namespace {
 
-constexpr int kThreads = 320;
+constexpr int kEpiThreads = 128;                // 4 warps per 128-row tile
+constexpr int kThreads = 64 + 2 * kEpiThreads;   // + TMA warp + MMA warp
 constexpr int kStages = 4;
 constexpr uint32_t kStageBytes = 256 * 32 * 2;  // one weight block [256 rows x 32 k] bf16
 constexpr uint32_t kActBytes = 128 * 256 * 2;   // one tile's activations (4 K-blocks of 64)
 constexpr uint32_t kGxBytes = 128 * 64 * 2;     // one tile's gamma(x)
 constexpr int kLayers = 9;
-constexpr int kBlocksPerPair = 64;              // weight blocks streamed per tile pair
+constexpr int kBlocksPerPair = 68;              // weight blocks streamed per tile pair
 constexpr uint32_t kSmemBytes = 1024 + 2 * kActBytes + 2 * kGxBytes + kStages * kStageBytes;
-// 32-wide K chunks per layer: trunk1 reads gamma(x) (64), trunk6 reads
-// [h (256), gamma(x) (64)], the others h (256).
+// 32-wide K chunks (one weight block each) per layer: trunk1 reads gamma(x)
+// (64), trunk6 reads [h (256), gamma(x) (64)], the others h (256).  The last
+// layer has N = 144: rows 0..127 are the RGB hidden layer (feature layer
+// folded in), row 128 the density head, so sigma_raw arrives as accumulator
+// column 128 of the last MMA.
 __constant__ int c_chunks[kLayers] = {2, 8, 8, 8, 8, 10, 8, 8, 8};
 
 struct Params {
@@ -52,8 +78,7 @@ struct Params {
     int S;
     long long M;            // rows of the pass
     long long n_pairs;
-    const float* bias;      // [8][256] trunk biases
-    const float* w_sigma;   // [256]
+    const uint32_t* bias2;  // [8][128] trunk biases as BF16 pairs
     float b_sigma;
     const float* ray_bias;  // [n_rays][128]
     const float* w_out;     // [3][128]
@@ -100,6 +125,31 @@ __device__ __forceinline__ void pe_row_bf16(const float x[3], uint32_t (&pk)[32]
     for (int i = 0; i < 32; ++i) pk[i] = pack_bf16x2(v[2 * i], v[2 * i + 1]);
 }
 
+// 32 accumulator columns of one row -> relu(acc + bias) as BF16 -> four
+// 16-byte chunks (j0 .. j0+3) of the row in a 128-byte-swizzled K-block.
+__device__ __forceinline__ void epi_chunk_store(const uint32_t (&v)[32], const uint4* b4,
+                                                uint32_t blk, uint32_t r, uint32_t j0) {
+    const uint32_t one2 = 0x3F803F80u;  // (1.0, 1.0) in BF16
+    uint32_t pk[16];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const uint4 b = __ldg(b4 + q);
+        const uint32_t bb[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int i = 4 * q + e;
+            const uint32_t a = pack_bf16x2(__uint_as_float(v[2 * i]), __uint_as_float(v[2 * i + 1]));
+            uint32_t h;
+            asm("fma.rn.relu.bf16x2 %0, %1, %2, %3;" : "=r"(h) : "r"(a), "r"(one2), "r"(bb[e]));
+            pk[i] = h;
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        st_shared_v4(blk + sw128_offset(r, j0 + q), pk[4 * q], pk[4 * q + 1], pk[4 * q + 2],
+                     pk[4 * q + 3]);
+}
+
 __global__ void __launch_bounds__(kThreads, 1)
     k_mlp_tc(const __grid_constant__ CUtensorMap tmap, const Params p) {
     extern __shared__ uint8_t smem_raw[];
@@ -118,7 +168,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         for (int s = 0; s < 2; ++s) {
             mbar_init(smem_u32(&bars.acc_full[s]), 1);
-            mbar_init(smem_u32(&bars.a_ready[s]), 128);
+            mbar_init(smem_u32(&bars.a_ready[s]), kEpiThreads);
         }
         mbar_init(smem_u32(&bars.drain), 1);
         fence_mbar_init();
@@ -142,10 +192,12 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (long long pr = blockIdx.x; pr < p.n_pairs && ok; pr += gridDim.x) {
                 for (int b = 0; b < kBlocksPerPair; ++b, ++g) {
                     const uint32_t st = g % kStages, ph = (g / kStages) & 1u;
+                    TC_TRACE(0, g);
                     if (!mbar_wait(smem_u32(&bars.empty[st]), ph ^ 1u, abort_flag)) {
                         ok = false;
                         break;
                     }
+                    TC_TRACE(1, g);
                     mbar_arrive_expect_tx(smem_u32(&bars.full[st]), kStageBytes);
                     tma_load_2d(s_ring + st * kStageBytes, &tmap, 0, b * 256,
                                 smem_u32(&bars.full[st]));
@@ -164,28 +216,27 @@ __global__ void __launch_bounds__(kThreads, 1)
             uint32_t g = 0;
             uint32_t rdy_ph[2] = {0, 0};
             bool ok = true;
-            const uint32_t id256 = idesc_bf16(128, 256), id128 = idesc_bf16(128, 128);
+            const uint32_t id256 = idesc_bf16(128, 256), id144 = idesc_bf16(128, 144);
+            int tl = 0;
             for (long long pr = blockIdx.x; pr < p.n_pairs && ok; pr += gridDim.x) {
-                for (int l = 0; l < kLayers && ok; ++l) {
+                for (int l = 0; l < kLayers && ok; ++l, ++tl) {
                     const int nch = c_chunks[l];
-                    const uint32_t idesc = (l == 8) ? id128 : id256;
+                    const uint32_t idesc = (l == 8) ? id144 : id256;
+                    TC_TRACE(2, tl);
                     for (int c = 0; c < nch && ok; ++c) {
                         const uint32_t st = g % kStages, ph = (g / kStages) & 1u;
-                        const bool new_block = (l < 8) || ((c & 1) == 0);
-                        if (new_block) {
-                            if (!mbar_wait(smem_u32(&bars.full[st]), ph, abort_flag)) {
-                                ok = false;
-                                break;
-                            }
-                            tc_fence_after();
+                        if (!mbar_wait(smem_u32(&bars.full[st]), ph, abort_flag)) {
+                            ok = false;
+                            break;
                         }
-                        const uint32_t boff = (l == 8 && (c & 1)) ? 8192u : 0u;
+                        tc_fence_after();
                         for (int s = 0; s < 2; ++s) {
                             if (c == 0) {
                                 if (!mbar_wait(smem_u32(&bars.a_ready[s]), rdy_ph[s], abort_flag)) {
                                     ok = false;
                                     break;
                                 }
+                                TC_TRACE(3 + s, tl);
                                 rdy_ph[s] ^= 1u;
                                 tc_fence_after();
                             }
@@ -202,18 +253,16 @@ __global__ void __launch_bounds__(kThreads, 1)
                                 }
                                 const uint64_t ad = smem_desc(a_addr, 1024, kLayoutSw128);
                                 const uint64_t bd =
-                                    smem_desc(s_ring + st * kStageBytes + boff + kk * 32, 512, kLayoutSw64);
+                                    smem_desc(s_ring + st * kStageBytes + kk * 32, 512, kLayoutSw64);
                                 mma_bf16(tmem + s * 256, ad, bd, idesc, (c | kk) ? 1u : 0u);
                             }
                             if (c == nch - 1) mma_commit(smem_u32(&bars.acc_full[s]));
                         }
                         if (!ok) break;
-                        const bool block_done = (l < 8) || ((c & 1) == 1);
-                        if (block_done) {
-                            mma_commit(smem_u32(&bars.empty[st]));
-                            ++g;
-                        }
+                        mma_commit(smem_u32(&bars.empty[st]));
+                        ++g;
                     }
+                    TC_TRACE(5, tl);
                 }
             }
             if (!ok) record_abort(p);
@@ -223,8 +272,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
     } else {
         // ------------------------------------------------ prologue / epilogues
-        const int slot = (warp - 2) >> 2;                 // warps 2-5 -> 0, 6-9 -> 1
-        const int quad = warp & 3;                        // TMEM lane quadrant of this warp
+        // 4 warps per tile: warp w covers TMEM lane quadrant (w % 4), i.e. rows
+        // 32 (w % 4) .. +31, all columns; one thread owns one row.
+        const int slot = (warp - 2) >> 2;
+        const int quad = warp & 3;
         const uint32_t r = quad * 32 + lane;              // row within the tile
         const uint32_t t_acc = tmem + ((uint32_t)(quad * 32) << 16) + slot * 256;
         const uint32_t a_base = s_act + slot * kActBytes;
@@ -233,11 +284,13 @@ __global__ void __launch_bounds__(kThreads, 1)
         const uint32_t bar_acc = smem_u32(&bars.acc_full[slot]);
         uint32_t acc_ph = 0;
         bool ok = true;
+        const bool tracer = (r == 0);
+        int tl = 0;
         for (long long pr = blockIdx.x; pr < p.n_pairs && ok; pr += gridDim.x) {
             const long long grow = pr * 256 + slot * 128 + r;
             const bool valid = grow < p.M;
             const long long ray = valid ? grow / p.S : 0;
-            // ---- prologue: gamma(x) of this row
+            // ---- prologue: gamma(x) of this row into the tile's gamma(x) buffer
             {
                 uint32_t pk[32];
                 if (valid) {
@@ -259,58 +312,83 @@ __global__ void __launch_bounds__(kThreads, 1)
                 mbar_arrive(bar_ready);
             }
             float sigma = 0.0f;
-            for (int l = 0; l < kLayers && ok; ++l) {
+            for (int l = 0; l < kLayers && ok; ++l, ++tl) {
                 if (!mbar_wait(bar_acc, acc_ph, abort_flag)) {
                     ok = false;
                     break;
                 }
+                if (tracer) TC_TRACE(6 + 2 * slot, tl);
                 acc_ph ^= 1u;
                 tc_fence_after();
                 if (l < 8) {
-                    const float* bias = p.bias + l * 256;
+                    // h = relu(acc + b): accumulators rounded to BF16 pairs,
+                    // bias added and ReLU applied in packed BF16 arithmetic
+                    const uint4* b4 = reinterpret_cast<const uint4*>(p.bias2 + l * 128);
+                    uint32_t va[32], vb[32];
+                    tmem_ld32(t_acc, va);
 #pragma unroll 1
-                    for (int c32 = 0; c32 < 8; ++c32) {
-                        uint32_t v[32];
-                        tmem_ld32(t_acc + c32 * 32, v);
+                    for (int c32 = 0; c32 < 8; c32 += 2) {
                         tmem_ld_wait();
-                        float h[32];
-#pragma unroll
-                        for (int i = 0; i < 32; ++i)
-                            h[i] = fmaxf(__uint_as_float(v[i]) + __ldg(bias + c32 * 32 + i), 0.0f);
-                        if (l == 7) {
-#pragma unroll
-                            for (int i = 0; i < 32; ++i)
-                                sigma = fmaf(h[i], __ldg(p.w_sigma + c32 * 32 + i), sigma);
-                        }
-                        uint32_t pk[16];
-#pragma unroll
-                        for (int i = 0; i < 16; ++i) pk[i] = pack_bf16x2(h[2 * i], h[2 * i + 1]);
+                        if (tracer && slot == 0 && tl < 16) TC_TRACE(10 + (c32 >> 1), tl);
+                        tmem_ld32(t_acc + (c32 + 1) * 32, vb);
                         const uint32_t blk = a_base + (c32 >> 1) * 16384;
-                        const uint32_t j0 = (c32 & 1) * 4;
-#pragma unroll
-                        for (int q = 0; q < 4; ++q)
-                            st_shared_v4(blk + sw128_offset(r, j0 + q), pk[4 * q], pk[4 * q + 1],
-                                         pk[4 * q + 2], pk[4 * q + 3]);
+                        epi_chunk_store(va, b4 + c32 * 4, blk, r, 0);
+                        tmem_ld_wait();
+                        if (c32 + 2 < 8) tmem_ld32(t_acc + (c32 + 2) * 32, va);
+                        epi_chunk_store(vb, b4 + (c32 + 1) * 4, blk, r, 4);
                     }
+                    if (tracer && slot == 0 && tl < 16) TC_TRACE(14, tl);
                     fence_proxy_async_smem();
                     tc_fence_before();
+                    if (tracer) TC_TRACE(7 + 2 * slot, tl);
                     mbar_arrive(bar_ready);
                 } else {
-                    const float* rb = p.ray_bias + ray * 128;
+                    const float4* rb4 = reinterpret_cast<const float4*>(p.ray_bias + ray * 128);
+                    const float4* wo4 = reinterpret_cast<const float4*>(p.w_out);
                     float o0 = 0.f, o1 = 0.f, o2 = 0.f;
+                    uint32_t va[32], vb[32];
+                    tmem_ld32(t_acc, va);
 #pragma unroll 1
-                    for (int c32 = 0; c32 < 4; ++c32) {
-                        uint32_t v[32];
-                        tmem_ld32(t_acc + c32 * 32, v);
+                    for (int c32 = 0; c32 < 4; c32 += 2) {
                         tmem_ld_wait();
+                        tmem_ld32(t_acc + (c32 + 1) * 32, vb);
 #pragma unroll
-                        for (int i = 0; i < 32; ++i) {
-                            const int col = c32 * 32 + i;
-                            const float hr = fmaxf(__uint_as_float(v[i]) + __ldg(rb + col), 0.0f);
-                            o0 = fmaf(hr, __ldg(p.w_out + col), o0);
-                            o1 = fmaf(hr, __ldg(p.w_out + 128 + col), o1);
-                            o2 = fmaf(hr, __ldg(p.w_out + 256 + col), o2);
+                        for (int q = 0; q < 8; ++q) {
+                            const float4 b = __ldg(rb4 + c32 * 8 + q);
+                            const float4 w0 = __ldg(wo4 + c32 * 8 + q);
+                            const float4 w1 = __ldg(wo4 + 32 + c32 * 8 + q);
+                            const float4 w2 = __ldg(wo4 + 64 + c32 * 8 + q);
+                            const float h0 = fmaxf(__uint_as_float(va[4 * q + 0]) + b.x, 0.0f);
+                            const float h1 = fmaxf(__uint_as_float(va[4 * q + 1]) + b.y, 0.0f);
+                            const float h2 = fmaxf(__uint_as_float(va[4 * q + 2]) + b.z, 0.0f);
+                            const float h3 = fmaxf(__uint_as_float(va[4 * q + 3]) + b.w, 0.0f);
+                            o0 = fmaf(h0, w0.x, fmaf(h1, w0.y, fmaf(h2, w0.z, fmaf(h3, w0.w, o0))));
+                            o1 = fmaf(h0, w1.x, fmaf(h1, w1.y, fmaf(h2, w1.z, fmaf(h3, w1.w, o1))));
+                            o2 = fmaf(h0, w2.x, fmaf(h1, w2.y, fmaf(h2, w2.z, fmaf(h3, w2.w, o2))));
                         }
+                        tmem_ld_wait();
+                        if (c32 + 2 < 4) tmem_ld32(t_acc + (c32 + 2) * 32, va);
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) {
+                            const float4 b = __ldg(rb4 + (c32 + 1) * 8 + q);
+                            const float4 w0 = __ldg(wo4 + (c32 + 1) * 8 + q);
+                            const float4 w1 = __ldg(wo4 + 32 + (c32 + 1) * 8 + q);
+                            const float4 w2 = __ldg(wo4 + 64 + (c32 + 1) * 8 + q);
+                            const float h0 = fmaxf(__uint_as_float(vb[4 * q + 0]) + b.x, 0.0f);
+                            const float h1 = fmaxf(__uint_as_float(vb[4 * q + 1]) + b.y, 0.0f);
+                            const float h2 = fmaxf(__uint_as_float(vb[4 * q + 2]) + b.z, 0.0f);
+                            const float h3 = fmaxf(__uint_as_float(vb[4 * q + 3]) + b.w, 0.0f);
+                            o0 = fmaf(h0, w0.x, fmaf(h1, w0.y, fmaf(h2, w0.z, fmaf(h3, w0.w, o0))));
+                            o1 = fmaf(h0, w1.x, fmaf(h1, w1.y, fmaf(h2, w1.z, fmaf(h3, w1.w, o1))));
+                            o2 = fmaf(h0, w2.x, fmaf(h1, w2.y, fmaf(h2, w2.z, fmaf(h3, w2.w, o2))));
+                        }
+                    }
+                    {
+                        // density head: accumulator column 128 of the last MMA
+                        uint32_t vs[32];
+                        tmem_ld32(t_acc + 128, vs);
+                        tmem_ld_wait();
+                        sigma = __uint_as_float(vs[0]);
                     }
                     tc_fence_before();
                     if (valid) {
@@ -354,8 +432,7 @@ struct TcState {
     float* aux = nullptr;      // fp32 biases and small heads
     float* ray_bias = nullptr; // [max_rays][128]
     int* abort_flag = nullptr;
-    const float* bias = nullptr;
-    const float* w_sigma = nullptr;
+    const uint32_t* bias2 = nullptr;
     const float* w_out = nullptr;
     const float* Wd = nullptr;
     const float* bprime = nullptr;
@@ -431,20 +508,25 @@ int mlp_tc_prepare(mcl_map* m, const float* blob) {
             put_chunk(b, 0, 256, get, k0);
         }
     }
-    // RGB hidden (folded), N = 128: two K chunks per block (rows 0..127, 128..255)
-    for (int k0 = 0; k0 < kWidth; k0 += 64, ++b) {
+    // last layer, N = 144: rows 0..127 RGB hidden (folded), row 128 density head
+    for (int k0 = 0; k0 < kWidth; k0 += 32, ++b) {
         auto get = [&](int n, int k) -> double { return Wfold[(size_t)n * kWidth + k]; };
         put_chunk(b, 0, 128, get, k0);
-        put_chunk(b, 128, 128, get, k0 + 32);
+        auto gets = [&](int n, int k) -> double { (void)n; return (double)Wp[8][k]; };
+        put_chunk(b, 128, 1, gets, k0);
     }
     if (b != kBlocksPerPair) return fail(MCL_ERR_UNSUPPORTED, "internal: weight block count %d", b);
-    // ---- fp32 aux: trunk biases [8][256], w_sigma [256], w_out [3][128],
-    //      W_d [128][27], b' [128]
+    // ---- aux: trunk biases as BF16 pairs [8][128] (bit patterns stored in
+    //      floats), w_out [3][128], W_d [128][27], b' [128]
     std::vector<float> aux;
     const size_t o_bias = aux.size();
-    for (int l = 0; l < kDepth; ++l) aux.insert(aux.end(), bp[l], bp[l] + kWidth);
-    const size_t o_wsig = aux.size();
-    aux.insert(aux.end(), Wp[8], Wp[8] + kWidth);
+    for (int l = 0; l < kDepth; ++l)
+        for (int j = 0; j < kWidth / 2; ++j) {
+            const uint32_t pr = (uint32_t)f2bf(bp[l][2 * j]) | ((uint32_t)f2bf(bp[l][2 * j + 1]) << 16);
+            float f;
+            memcpy(&f, &pr, 4);
+            aux.push_back(f);
+        }
     const size_t o_wout = aux.size();
     aux.insert(aux.end(), Wp[11], Wp[11] + 3 * kRgbW);
     const size_t o_wd = aux.size();
@@ -467,8 +549,7 @@ int mlp_tc_prepare(mcl_map* m, const float* blob) {
     if ((rc = cuda_check(cudaMalloc(&st->ray_bias, (size_t)m->cfg.max_rays * 128 * 4), "ray bias")))
         return rc;
     if ((rc = cuda_check(cudaMalloc(&st->abort_flag, sizeof(int)), "abort flag"))) return rc;
-    st->bias = st->aux + o_bias;
-    st->w_sigma = st->aux + o_wsig;
+    st->bias2 = reinterpret_cast<const uint32_t*>(st->aux + o_bias);
     st->w_out = st->aux + o_wout;
     st->Wd = st->aux + o_wd;
     st->bprime = st->aux + o_bp;
@@ -542,8 +623,7 @@ cudaError_t mlp_tc(mcl_map* m, int precision, const Ray* rays, const float* gd, 
     p.S = S;
     p.M = (long long)n_rays * S;
     p.n_pairs = (p.M + 255) / 256;
-    p.bias = st->bias;
-    p.w_sigma = st->w_sigma;
+    p.bias2 = st->bias2;
     p.b_sigma = st->b_sigma;
     p.ray_bias = st->ray_bias;
     p.w_out = st->w_out;

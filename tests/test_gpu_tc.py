@@ -53,6 +53,21 @@ def topk_overlap(a, b, k=10):
     return len(set(np.argsort(-a)[:k]) & set(np.argsort(-b)[:k]))
 
 
+_SPREAD = {}
+
+
+def sigma_spread(seed):
+    """Standard deviation of the map's raw density over the sample volume
+    (oracle, 2048 seeded points): the scale the density error is judged on."""
+    if seed not in _SPREAD:
+        rng = np.random.default_rng(12345)
+        x = rng.uniform(-6, 6, size=(2048, 3))
+        d = rng.normal(size=(2048, 3))
+        d /= np.linalg.norm(d, axis=1, keepdims=True)
+        _SPREAD[seed] = float(np.std(oracle.mlp(synth.he_init_weights(seed), x, d)[0]))
+    return _SPREAD[seed]
+
+
 @pytest.mark.parametrize("n", [1, 127, 128, 129, 256, 4097])
 def test_mlp_points_bf16_vs_oracle(M, gmaps, n):
     """Ragged row counts around the 128-row tile and 256-row pair."""
@@ -67,7 +82,7 @@ def test_mlp_points_bf16_vs_oracle(M, gmaps, n):
                                 d.astype(np.float64) / np.linalg.norm(d.astype(np.float64), axis=1, keepdims=True))
     assert np.all(np.isfinite(out))
     e_rgb = np.abs(out[:, 1:] - rgb_ref)
-    e_sig = np.abs(out[:, 0] - s_ref) / max(np.std(s_ref), 0.1)
+    e_sig = np.abs(out[:, 0] - s_ref) / sigma_spread(2)
     print(f"n={n} rgb max {e_rgb.max():.3g} mean {e_rgb.mean():.3g} sigma rel max {e_sig.max():.3g}")
     assert e_rgb.max() <= 2.5e-2 and e_rgb.mean() <= 5e-3
     assert e_sig.max() <= 0.1 and e_sig.mean() <= 0.02
