@@ -165,6 +165,29 @@ int mcl_render(mcl_map* map, const float* d_poses, int n_poses,
 int mcl_resample(mcl_map* map, const double* d_w, int N_in, int N_out,
                  double u0, int32_t* d_idx, void* stream);
 
+/* Largest N_in that mcl_resample_noalloc accepts. */
+#define MCL_RESAMPLE_NOALLOC_MAX_IN 65536
+
+/* Systematic resampling exactly as mcl_resample (same integer rule, same
+ * indices for the same weights and u0), for callers that cannot allocate
+ * device memory: a control loop that forbids allocation once it runs, code
+ * executing while a stream is captured into a CUDA graph, or a filter that
+ * has no map.  The paper has no counterpart; this entry point only changes
+ * where the scratch lives.  It needs no map and allocates nothing: its
+ * scratch (the integer CDF of up to MCL_RESAMPLE_NOALLOC_MAX_IN weights and a
+ * status word, about 512 KB) is a fixed array in the library image, present
+ * on every device that loads the library until the process exits.  The first
+ * call on a device looks up that array's device address (with that device
+ * current); make that first call before any stream capture.  Every call
+ * shares the array: calls that overlap on the GPU (different streams, or
+ * different host threads on one device) race and must be serialised by the
+ * caller.  N_in > MCL_RESAMPLE_NOALLOC_MAX_IN is rejected with MCL_ERR_ARG.
+ * Negative, non-finite or all-zero weights give d_idx[k] = -1 for every k.
+ * d_w: [N_in] f64, d_idx: [N_out] int32, 1 <= N_out <= 65536,
+ * 0 <= u0 < 1. */
+int mcl_resample_noalloc(const double* d_w, int N_in, int N_out, double u0,
+                         int32_t* d_idx, void* stream);
+
 /* Prediction step (Sec. III-A): d_out[k] = d_in[idx[k]] * Exp(delta_k) with
  * O_t = I, delta_k = (rho, (0, yaw, 0)) in se(3), rho ~ N(0, sigma_t^2 I3),
  * yaw ~ N(0, sigma_yaw^2) in the body frame.  The normals are Box-Muller
