@@ -53,9 +53,11 @@ typedef struct {
 
 /* Workspace bounds fixed at map creation. */
 typedef struct {
-    int max_rays;      /* largest N * B of any mcl_update / mcl_render call   */
+    int max_rays;      /* largest N * B of any call (summed over queries)     */
     int max_samples;   /* largest n_coarse + n_fine                           */
-    int max_particles; /* largest particle count of mcl_update / mcl_resample */
+    int max_particles; /* largest particle count (queries x stride for       */
+                       /* mcl_localize)                                       */
+    int max_queries;   /* largest query count of mcl_localize (<= 64)         */
 } mcl_map_config;
 
 /* Pinhole intrinsics K at FULL resolution (Eq. 4, "shared intrinsic camera
@@ -216,6 +218,66 @@ int mcl_position_spread(const float* d_poses, int N, double* d_out,
  * first MCL_ERR_* recorded by the device since the last read; *n_nonfinite
  * (optional) receives the number of particles masked for non-finite loss. */
 int mcl_read_status(mcl_map* map, int* n_nonfinite, void* stream);
+
+/* Draw the query pixel set of one update (Eq. 4 / Eq. 6 index p_j without a
+ * particle index: one set for every particle): B distinct pixels of a W x H
+ * level image, uniformly without replacement, by Floyd's sampling algorithm
+ * on SplitMix64 stream (seed, counter): for j = n-B .. n-1 (n = W H), t =
+ * floor(r (j+1) / 2^64) with r = value j-(n-B) of the stream; take t unless
+ * already taken, else j; pixel index -> (u, v) = (index % W, index / W).
+ * d_out: [B,2] int32.  1 <= B <= min(1024, W H). */
+int mcl_draw_pixels(int W, int H, int B, uint64_t seed, uint64_t counter,
+                    int32_t* d_out, void* stream);
+
+/* Coarse-to-fine schedule of Sec. III-C for mcl_localize.  Stage s renders
+ * level level[s] (R = 2^(level - 2)) with n_pixels[s] query pixels and at
+ * most n_cap[s] particles.  After each iteration the particle count becomes
+ * clamp(survivors, n_min, n_cap[stage]) (survivors = particles whose
+ * normalised weight is at least rho_reject / N), and the run moves to the
+ * next stage when the weighted variance (trace) of the positions falls below
+ * refine[stage] or after stage_iter_cap[stage] iterations in the stage. */
+#define MCL_MAX_STAGES 3
+typedef struct {
+    int n_stages;                         /* 1 .. 3                          */
+    int level[MCL_MAX_STAGES];            /* image level of each stage       */
+    int n_pixels[MCL_MAX_STAGES];         /* B of each stage, <= 256         */
+    int n_cap[MCL_MAX_STAGES];            /* particle cap of each stage      */
+    int n_min;                            /* lower clamp of the survivors    */
+    int stage_iter_cap[MCL_MAX_STAGES];   /* forced refinement after this    */
+    double refine[MCL_MAX_STAGES];        /* spread threshold per stage      */
+    int iterations;                       /* MCL iterations of the run       */
+    float sigma_t, sigma_yaw;             /* motion noise (mcl_predict)      */
+} mcl_schedule;
+
+/* One record per query and iteration of mcl_localize (weights of that
+ * iteration, before resampling). */
+typedef struct {
+    int stage, level, n_particles, n_pixels, n_survivors;
+    int status;            /* particles with a non-finite loss this iteration */
+    double spread;         /* weighted trace of the position covariance       */
+    double est[4];         /* weighted mean position (x, y, z), circular yaw  */
+} mcl_iter_record;
+
+/* Run Monte Carlo localisation (Alg. 1 iterated, Sec. III-C schedule) on the
+ * device for n_queries independent queries on one map.  Iteration t of query
+ * q: draw the pixel set (mcl_draw_pixels, stream (seed, q 2^32 + 4t)), weight
+ * the particles (as mcl_update), record, apply the schedule, resample
+ * (mcl_resample with u0 = value 0 of stream (seed, q 2^32 + 4t + 1)) and
+ * predict (mcl_predict with stream (seed, q 2^32 + 4t + 2)); jitter, when
+ * enabled, uses stream (seed, q 2^32 + 4t + 3).  d_particles: [n_queries,
+ * stride, 12] f32, query q's h_n0[q] initial particles at row q*stride; on
+ * return its final particles (count in d_final_n[q]).  h_images: host array
+ * of n_queries device pointers to [H,W,3] observations, all with intrinsics
+ * K.  d_log: [n_queries, iterations].  All sizes that change during the run
+ * stay on the device: with use_graph != 0 the run is captured into a CUDA
+ * graph on the map's own stream (ordered after earlier work on `stream` and
+ * before later work on it) and kept; later calls with the same shapes and
+ * pointers relaunch it.  opts->precision must be MCL_PREC_BF16. */
+int mcl_localize(mcl_map* map, int n_queries, float* d_particles, int stride,
+                 const int* h_n0, const float* const* h_images,
+                 const mcl_intrinsics* K, const mcl_schedule* sch,
+                 const mcl_opts* opts, mcl_iter_record* d_log, int* d_final_n,
+                 int use_graph, void* stream);
 
 /* Phases timed when profiling is on (indices into the array of
  * mcl_profile_read). */

@@ -67,14 +67,14 @@ def lib():
             L.orc_composite.argtypes = [C.c_int, dp, dp, dp, C.c_double, dp, dp, dp]
             L.orc_sample_pdf.argtypes = [C.c_int, dp, dp, C.c_int, dp, dp]
             L.orc_uncertainty.argtypes = [C.c_int, dp, dp, C.c_double, C.c_double,
-                                          dp, dp, dp, dp]
+                                          dp, dp, dp, dp, dp]
             L.orc_render_rays.argtypes = [fp, ip, C.c_int, dp, dp, C.POINTER(Opts),
                                           dp, dp, dp, dp]
             L.orc_downscale.argtypes = [dp, C.c_int, C.c_int, C.c_int, dp]
             L.orc_update.argtypes = [fp, ip, dp, C.c_int, dp, C.c_int, C.c_int, dp,
                                      C.c_int, C.POINTER(C.c_int32), C.c_int,
                                      C.POINTER(Opts), dp, dp, dp, dp, dp, dp, dp,
-                                     dp, dp, dp, dp, dp, C.POINTER(C.c_uint8)]
+                                     dp, dp, dp, dp, dp, dp, C.POINTER(C.c_uint8)]
             L.orc_resample.argtypes = [dp, C.c_int, C.c_int, C.c_double,
                                        C.POINTER(C.c_int32)]
             L.orc_splitmix64_next.restype = C.c_uint64
@@ -91,6 +91,8 @@ def lib():
                                            C.c_double, C.c_double, dp]
             L.orc_position_spread.argtypes = [C.c_int, dp, dp]
             L.orc_num_threads.restype = C.c_int
+            L.orc_pixel_set.argtypes = [C.c_int, C.c_int, C.c_int, C.c_uint64, C.c_uint64,
+                                        C.POINTER(C.c_int32)]
             _lib = L
     return _lib
 
@@ -185,14 +187,14 @@ def sample_pdf(z_c, w_c, n_f, u=None):
 def uncertainty(z, w, alpha, tau):
     z, zp = _d(z)
     w, wp = _d(w)
-    out = np.zeros(4)
+    out = np.zeros(5)
     o = out.ctypes.data_as(C.POINTER(C.c_double))
     dp = C.POINTER(C.c_double)
     base = C.addressof(o.contents)
     lib().orc_uncertainty(z.shape[0], zp, wp, float(alpha), float(tau),
                           C.cast(base, dp), C.cast(base + 8, dp),
-                          C.cast(base + 16, dp), C.cast(base + 24, dp))
-    return dict(z_trans=out[0], z_opaque=out[1], F=out[2], tie=out[3])
+                          C.cast(base + 16, dp), C.cast(base + 24, dp), C.cast(base + 32, dp))
+    return dict(z_trans=out[0], z_opaque=out[1], F=out[2], tie=out[3], step=out[4])
 
 
 def render_rays(blob, o, d, opts: Opts, uj=None, arch=DEFAULT_ARCH, debug=False):
@@ -203,7 +205,7 @@ def render_rays(blob, o, d, opts: Opts, uj=None, arch=DEFAULT_ARCH, debug=False)
     o, op_ = _d(np.reshape(o, (-1, 3)))
     d, dp_ = _d(np.reshape(d, (-1, 3)))
     n = o.shape[0]
-    out = np.zeros((n, 9))
+    out = np.zeros((n, 10))
     ns = opts.n_coarse + opts.n_fine
     zd = np.zeros((n, ns)) if debug else None
     wd = np.zeros((n, ns)) if debug else None
@@ -218,7 +220,7 @@ def render_rays(blob, o, d, opts: Opts, uj=None, arch=DEFAULT_ARCH, debug=False)
     assert rc == 0, rc
     res = dict(rgb=out[:, :3].copy(), z_trans=out[:, 3].copy(),
                z_opaque=out[:, 4].copy(), F=out[:, 5].copy(), tie=out[:, 6].copy(),
-               sigma_last=out[:, 7].copy(), T_last=out[:, 8].copy())
+               sigma_last=out[:, 7].copy(), T_last=out[:, 8].copy(), step=out[:, 9].copy())
     if debug:
         res["z"] = zd
         res["w"] = wd
@@ -250,7 +252,7 @@ def update(blob, particles, image, K4, factor, pixels, opts: Opts, uj=None,
     B = px.shape[0]
     nr = N * B
     res = {k: np.zeros(nr) for k in ("E", "F", "z_trans", "z_opaque", "tie", "sigma_last",
-                                     "T_last")}
+                                     "T_last", "step")}
     res["rgb"] = np.zeros((nr, 3))
     for k in ("S", "logw", "w"):
         res[k] = np.zeros(N)
@@ -265,7 +267,7 @@ def update(blob, particles, image, K4, factor, pixels, opts: Opts, uj=None,
                           res["F"].ctypes.data_as(dp), res["z_trans"].ctypes.data_as(dp),
                           res["z_opaque"].ctypes.data_as(dp), res["tie"].ctypes.data_as(dp),
                           res["sigma_last"].ctypes.data_as(dp), res["T_last"].ctypes.data_as(dp),
-                          res["S"].ctypes.data_as(dp), res["logw"].ctypes.data_as(dp),
+                          res["step"].ctypes.data_as(dp), res["S"].ctypes.data_as(dp), res["logw"].ctypes.data_as(dp),
                           res["w"].ctypes.data_as(dp),
                           res["mask"].ctypes.data_as(C.POINTER(C.c_uint8)))
     if rc != 0:
@@ -281,6 +283,16 @@ def resample(w, n_out, u0):
     if rc != 0:
         raise ValueError(f"orc_resample returned {rc}")
     return idx
+
+
+def pixel_set(W, H, B, seed, ctr):
+    """B distinct pixels (u, v) of a W x H image drawn by Floyd's algorithm
+    from SplitMix64 stream (seed, ctr)."""
+    out = np.zeros((B, 2), dtype=np.int32)
+    rc = lib().orc_pixel_set(W, H, B, seed, ctr, out.ctypes.data_as(C.POINTER(C.c_int32)))
+    if rc != 0:
+        raise ValueError(f"orc_pixel_set returned {rc}")
+    return out
 
 
 def splitmix64_stream(seed, n):

@@ -247,12 +247,14 @@ void orc_sample_pdf(int n_c, const double* z_c, const double* w_c, int n_f,
 /*   F = max(z_opaque - z_trans, tau).                                       */
 /* tie: how far the running sum is from flipping either decision, i.e. the   */
 /* distance to alpha of W at the chosen k_trans and at k_trans - 1, and the  */
-/* distance to 1 - alpha of W at k_opaque and k_opaque + 1 (reported for     */
-/* parity tests; not part of the method).                                    */
+/* distance to 1 - alpha of W at k_opaque and k_opaque + 1; step: the widest */
+/* sample spacing next to either decision (how far z_trans or z_opaque move  */
+/* if a decision flips by one sample).  Both are reported for parity tests   */
+/* and are not part of the method.                                           */
 /* ------------------------------------------------------------------------ */
 void orc_uncertainty(int n, const double* z, const double* w, double alpha,
                      double tau, double* z_trans, double* z_opaque, double* F,
-                     double* tie) {
+                     double* tie, double* step) {
     double Wc = 0.0;
     int kt = -1, ko = -1;
     double* W = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
@@ -282,6 +284,16 @@ void orc_uncertainty(int n, const double* z, const double* w, double alpha,
         }
         *tie = m;
     }
+    if (step) {
+        double st = 0.0;
+        int ks[2] = {kt >= 0 ? kt : 0, ko >= 0 ? ko : 0};
+        for (int i = 0; i < 2; ++i) {
+            int k = ks[i];
+            if (k > 0 && z[k] - z[k - 1] > st) st = z[k] - z[k - 1];
+            if (k + 1 < n && z[k + 1] - z[k] > st) st = z[k + 1] - z[k];
+        }
+        *step = st;
+    }
     free(W);
 }
 
@@ -298,7 +310,8 @@ typedef struct {
  * out[0..2] rgb, out[3] z_trans, out[4] z_opaque, out[5] F, out[6] tie,
  * out[7] raw density of the last sample, out[8] transmittance before it
  * (the last interval is 1e10 long, so the colour jumps by about
- * out[8] * c_last when that density crosses 0: reported for parity tests). */
+ * out[8] * c_last when that density crosses 0), out[9] decision step (see
+ * orc_uncertainty); out[6..9] are reported for parity tests. */
 static int render_ray(const double* wd, const int* arch, const double* o,
                       const double* d, const orc_opts* op, const double* uj,
                       double* out, double* z_dbg, double* w_dbg) {
@@ -350,7 +363,7 @@ static int render_ray(const double* wd, const int* arch, const double* o,
     double* Tk = (double*)malloc(sizeof(double) * (size_t)n);
     orc_composite(n, zs, ss, cs, dn, w, Tk, C);
     out[0] = C[0]; out[1] = C[1]; out[2] = C[2];
-    orc_uncertainty(n, zs, w, op->alpha, op->tau, out + 3, out + 4, out + 5, out + 6);
+    orc_uncertainty(n, zs, w, op->alpha, op->tau, out + 3, out + 4, out + 5, out + 6, out + 9);
     out[7] = ss[n - 1];
     out[8] = Tk[n - 1];
     free(Tk);
@@ -362,7 +375,7 @@ static int render_ray(const double* wd, const int* arch, const double* o,
 }
 
 /* Render arbitrary rays (for pins and for oracle-rendered observations).
- * o, d: [n,3].  uj: [n, n_coarse] or NULL.  out: [n,9] as render_ray.
+ * o, d: [n,3].  uj: [n, n_coarse] or NULL.  out: [n,10] as render_ray.
  * z_dbg, w_dbg: [n, n_coarse + n_fine] or NULL. */
 int orc_render_rays(const float* blob, const int* arch, int n, const double* o,
                     const double* d, const orc_opts* op, const double* uj,
@@ -375,7 +388,7 @@ int orc_render_rays(const float* blob, const int* arch, int n, const double* o,
 #pragma omp parallel for schedule(dynamic, 1) reduction(| : err)
     for (int r = 0; r < n; ++r)
         err |= render_ray(wd, arch, o + 3 * r, d + 3 * r, op,
-                          uj ? uj + (long)r * op->n_coarse : NULL, out + 9 * r,
+                          uj ? uj + (long)r * op->n_coarse : NULL, out + 10 * r,
                           z_dbg ? z_dbg + (long)r * ns : NULL,
                           w_dbg ? w_dbg + (long)r * ns : NULL);
     free(wd);
@@ -422,7 +435,7 @@ int orc_update(const float* blob, const int* arch, const double* particles,
                int factor, const int32_t* pixels, int B, const orc_opts* op,
                const double* uj, double* rgb, double* E, double* Fr,
                double* zt, double* zo, double* tie, double* sig_last,
-               double* t_last, double* S, double* logw, double* w,
+               double* t_last, double* step, double* S, double* logw, double* w,
                uint8_t* mask) {
     if (N < 1 || B < 1 || factor < 1 || W % factor || H % factor) return -1;
     long nw = orc_n_weights(arch);
@@ -444,7 +457,7 @@ int orc_update(const float* blob, const int* arch, const double* particles,
 #pragma omp parallel for schedule(dynamic, 1) reduction(| : err)
     for (long r = 0; r < nr; ++r) {
         int i = (int)(r / B), j = (int)(r % B);
-        double o[3], d[3], out[9];
+        double o[3], d[3], out[10];
         orc_ray(particles + 12 * (long)i, fx, fy, cx, cy, pixels[2 * j],
                 pixels[2 * j + 1], o, d);
         err |= render_ray(wd, arch, o, d, op,
@@ -465,6 +478,7 @@ int orc_update(const float* blob, const int* arch, const double* particles,
         if (tie) tie[r] = out[6];
         if (sig_last) sig_last[r] = out[7];
         if (t_last) t_last[r] = out[8];
+        if (step) step[r] = out[9];
     }
     /* per-particle sums and log weights */
     double mx = -INFINITY;
@@ -576,6 +590,37 @@ double orc_normal(uint64_t seed, uint64_t ctr, uint64_t m) {
     double u1 = ((double)(orc_cbrng(seed, ctr, 2 * m) >> 11) + 1.0) * 0x1.0p-53;
     double u2 = orc_uniform(seed, ctr, 2 * m + 1);
     return sqrt(-2.0 * log(u1)) * cos(2.0 * M_PI * u2);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Query pixel set {p_j} of one update (Alg. 1; Eq. 4 and Eq. 6 index p_j    */
+/* without a particle index, so one set serves every particle): B distinct  */
+/* pixels of a W x H level image, uniformly without replacement, by Floyd's  */
+/* sampling algorithm (Bentley & Floyd, CACM 1987): for j = n-B .. n-1 draw  */
+/* t uniform in [0, j]; take t unless already taken, else take j.  The       */
+/* uniform integer is floor(r (j + 1) / 2^64) with r = value j-(n-B) of      */
+/* SplitMix64 stream (seed, ctr).  Pixel index q -> (u, v) = (q % W, q / W). */
+/* ------------------------------------------------------------------------ */
+int orc_pixel_set(int W, int H, int B, uint64_t seed, uint64_t ctr, int32_t* out) {
+    long n = (long)W * H;
+    if (W < 1 || H < 1 || B < 1 || B > n) return -1;
+    long* chosen = (long*)malloc(sizeof(long) * (size_t)B);
+    if (!chosen) return -2;
+    int m = 0;
+    for (long j = n - B; j < n; ++j) {
+        uint64_t r = orc_cbrng(seed, ctr, (uint64_t)(j - (n - B)));
+        long t = (long)(((unsigned __int128)r * (unsigned __int128)(uint64_t)(j + 1)) >> 64);
+        int dup = 0;
+        for (int i = 0; i < m; ++i)
+            if (chosen[i] == t) { dup = 1; break; }
+        chosen[m++] = dup ? j : t;
+    }
+    for (int i = 0; i < B; ++i) {
+        out[2 * i] = (int32_t)(chosen[i] % W);
+        out[2 * i + 1] = (int32_t)(chosen[i] / W);
+    }
+    free(chosen);
+    return 0;
 }
 
 /* ------------------------------------------------------------------------ */

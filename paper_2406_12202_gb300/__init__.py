@@ -44,7 +44,37 @@ class Arch(C.Structure):
 
 
 class MapConfig(C.Structure):
-    _fields_ = [("max_rays", C.c_int), ("max_samples", C.c_int), ("max_particles", C.c_int)]
+    _fields_ = [("max_rays", C.c_int), ("max_samples", C.c_int), ("max_particles", C.c_int),
+                ("max_queries", C.c_int)]
+
+
+MAX_STAGES = 3
+
+
+class Schedule(C.Structure):
+    _fields_ = [("n_stages", C.c_int), ("level", C.c_int * MAX_STAGES),
+                ("n_pixels", C.c_int * MAX_STAGES), ("n_cap", C.c_int * MAX_STAGES),
+                ("n_min", C.c_int), ("stage_iter_cap", C.c_int * MAX_STAGES),
+                ("refine", C.c_double * MAX_STAGES), ("iterations", C.c_int),
+                ("sigma_t", C.c_float), ("sigma_yaw", C.c_float)]
+
+
+class IterRecord(C.Structure):
+    _fields_ = [("stage", C.c_int), ("level", C.c_int), ("n_particles", C.c_int),
+                ("n_pixels", C.c_int), ("n_survivors", C.c_int), ("status", C.c_int),
+                ("spread", C.c_double), ("est", C.c_double * 4)]
+
+
+def schedule(levels, pixels, caps, n_min=64, iter_caps=None, refine=None, iterations=20,
+             sigma_t=0.05, sigma_yaw=0.05) -> Schedule:
+    n = len(levels)
+    pad = lambda v, fill: list(v) + [fill] * (MAX_STAGES - len(v))
+    iter_caps = iter_caps or [iterations] * n
+    refine = refine or [0.0] * n
+    return Schedule(n, (C.c_int * MAX_STAGES)(*pad(levels, 0)),
+                    (C.c_int * MAX_STAGES)(*pad(pixels, 1)), (C.c_int * MAX_STAGES)(*pad(caps, 1)),
+                    n_min, (C.c_int * MAX_STAGES)(*pad(iter_caps, 1)),
+                    (C.c_double * MAX_STAGES)(*pad(refine, 0.0)), iterations, sigma_t, sigma_yaw)
 
 
 class Intrinsics(C.Structure):
@@ -93,6 +123,10 @@ def lib():
             L.mcl_position_spread.argtypes = [vp, i32, vp, vp]
             L.mcl_read_status.argtypes = [vp, C.POINTER(C.c_int), vp]
             L.mcl_map_supports.argtypes = [vp, i32]
+            L.mcl_draw_pixels.argtypes = [i32, i32, i32, u64, u64, vp, vp]
+            L.mcl_localize.argtypes = [vp, i32, vp, i32, C.POINTER(C.c_int), C.POINTER(vp),
+                                       C.POINTER(Intrinsics), C.POINTER(Schedule), C.POINTER(Opts),
+                                       vp, vp, i32, vp]
             L.mcl_query.argtypes = [vp, vp, vp, i32, i32, vp, vp]
             L.mcl_resample_noalloc.argtypes = [vp, i32, i32, f64, vp, vp]
             L.mcl_profile_enable.argtypes = [vp, i32]
@@ -162,11 +196,13 @@ class Map:
     """A NeRF map uploaded to the GPU with its workspace (mcl_init_map)."""
 
     def __init__(self, weights: np.ndarray, max_rays: int, max_samples: int = 192,
-                 max_particles: int | None = None, arch=(10, 4, 8, 256, 5, 128)):
+                 max_particles: int | None = None, max_queries: int = 1,
+                 arch=(10, 4, 8, 256, 5, 128)):
         w = np.ascontiguousarray(weights, dtype=np.float32)
         self._arch = Arch(*arch)
         self.cfg = MapConfig(int(max_rays), int(max_samples),
-                             int(max_particles if max_particles is not None else max_rays))
+                             int(max_particles if max_particles is not None else max_rays),
+                             int(max_queries))
         h = C.c_void_p()
         _check(lib().mcl_init_map(w.ctypes.data, w.size, C.byref(self._arch), C.byref(self.cfg),
                                   C.byref(h)))
@@ -265,6 +301,44 @@ class Map:
         _check(lib().mcl_profile_read(self.handle, ms, C.byref(n), int(reset)))
         return dict(zip(PHASES, list(ms))), n.value
 
+    def localize(self, particles, n0, images, K: Intrinsics, sch: Schedule, opts: UpdateOptions,
+                 use_graph: bool = True, log=None, final_n=None):
+        """Run MCL on the device for len(images) queries (mcl_localize).
+        particles: [Q, stride, 12] f32 CUDA tensor (in / out); n0: initial
+        counts; images: list of [H,W,3] f32 CUDA tensors.  Returns (log
+        ndarray of IterRecord fields [Q, iterations], final counts)."""
+        torch = _torch()
+        Q, stride, _ = particles.shape
+        if log is None:
+            log = torch.empty(Q * sch.iterations * C.sizeof(IterRecord), dtype=torch.uint8,
+                              device=particles.device)
+        if final_n is None:
+            final_n = torch.empty(Q, dtype=torch.int32, device=particles.device)
+        n0a = (C.c_int * Q)(*[int(v) for v in n0])
+        imgs = (C.c_void_p * Q)(*[_ptr(im, torch.float32, (K.height, K.width, 3), "image")
+                                  for im in images])
+        o = opts.c()
+        _check(lib().mcl_localize(self.handle, Q, _ptr(particles, torch.float32, None, "particles"),
+                                  stride, n0a, imgs, C.byref(K), C.byref(sch), C.byref(o),
+                                  log.data_ptr(), final_n.data_ptr(), int(use_graph), _stream()))
+        self._last_log = log
+        return log, final_n
+
+    @staticmethod
+    def decode_log(log, Q, iterations):
+        raw = log.cpu().numpy().tobytes()
+        recs = (IterRecord * (Q * iterations)).from_buffer_copy(raw)
+        out = []
+        for q in range(Q):
+            rows = []
+            for t in range(iterations):
+                r = recs[q * iterations + t]
+                rows.append(dict(stage=r.stage, level=r.level, n_particles=r.n_particles,
+                                 n_pixels=r.n_pixels, n_survivors=r.n_survivors, status=r.status,
+                                 spread=r.spread, est=list(r.est)))
+            out.append(rows)
+        return out
+
     def read_status(self):
         n = C.c_int(0)
         rc = lib().mcl_read_status(self.handle, C.byref(n), _stream())
@@ -287,6 +361,15 @@ def resample_noalloc(w, n_out: int, u0: float, idx=None):
                                       float(u0), _ptr(idx, torch.int32, (n_out,), "idx"),
                                       _stream()))
     return idx
+
+
+def draw_pixels(W: int, H: int, B: int, seed: int, counter: int, out=None):
+    torch = _torch()
+    if out is None:
+        out = torch.empty(B, 2, dtype=torch.int32, device="cuda")
+    _check(lib().mcl_draw_pixels(W, H, B, int(seed), int(counter),
+                                 _ptr(out, torch.int32, (B, 2), "out"), _stream()))
+    return out
 
 
 def predict(poses, idx, n_out: int, sigma_t: float, sigma_yaw: float, seed: int, counter: int,
@@ -324,7 +407,7 @@ def position_spread(poses, out=None):
 EXPORTED = ("mcl_init_map", "mcl_destroy_map", "mcl_update", "mcl_render", "mcl_resample",
             "mcl_predict", "mcl_downscale", "mcl_position_spread", "mcl_read_status",
             "mcl_profile_enable", "mcl_profile_read", "mcl_map_supports", "mcl_last_error",
-            "mcl_resample_noalloc", "mcl_query")
+            "mcl_resample_noalloc", "mcl_query", "mcl_draw_pixels", "mcl_localize")
 
 # Algorithmic multiply-accumulates per sample of the network the tensor-core
 # form evaluates (the linear feature layer folded into the RGB hidden layer):

@@ -92,8 +92,14 @@ static void free_map(mcl_map* m) {
         cudaEventDestroy(mk.b);
     }
     for (auto e : m->pool) cudaEventDestroy(e);
+    if (m->loop.exec) cudaGraphExecDestroy(m->loop.exec);
+    if (m->loop.stream) cudaStreamDestroy(m->loop.stream);
+    if (m->loop.ev_in) cudaEventDestroy(m->loop.ev_in);
+    if (m->loop.ev_out) cudaEventDestroy(m->loop.ev_out);
     void* ptrs[] = {m->w32, m->rays, m->gd, m->zc, m->zf, m->out_c, m->out_f, m->e_ray,
-                    m->logw64, m->cdf, m->status, m->act0, m->act1, m->gxbuf};
+                    m->logw64, m->cdf, m->status, m->act0, m->act1, m->gxbuf,
+                    m->loop.plan, m->loop.qs, m->loop.n0, (void*)m->loop.imgs, m->loop.pix,
+                    m->loop.P_next, m->loop.w, m->loop.mask, m->loop.idx};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete m;
@@ -118,9 +124,10 @@ extern "C" int mcl_init_map(const float* host_weights, size_t n_floats, const mc
     if (n_floats != blob_size())
         return fail(MCL_ERR_ARG, "mcl_init_map: n_floats %zu, expected %zu", n_floats, blob_size());
     if (cfg->max_rays < 1 || cfg->max_samples < 2 || cfg->max_samples > kMaxSamples ||
-        cfg->max_particles < 1)
-        return fail(MCL_ERR_ARG, "mcl_init_map: bad workspace config (rays %d samples %d particles %d)",
-                    cfg->max_rays, cfg->max_samples, cfg->max_particles);
+        cfg->max_particles < 1 || cfg->max_queries < 1 || cfg->max_queries > kLoopMaxQueries)
+        return fail(MCL_ERR_ARG,
+                    "mcl_init_map: bad workspace config (rays %d samples %d particles %d queries %d)",
+                    cfg->max_rays, cfg->max_samples, cfg->max_particles, cfg->max_queries);
     for (size_t i = 0; i < n_floats; ++i)
         if (!std::isfinite(host_weights[i]))
             return fail(MCL_ERR_ARG, "mcl_init_map: weight %zu is not finite", i);
@@ -189,6 +196,16 @@ extern "C" int mcl_init_map(const float* host_weights, size_t n_floats, const mc
         {(void**)&m->act0, (size_t)m->chunk_rows * kWidth * sizeof(float), "act0"},
         {(void**)&m->act1, (size_t)m->chunk_rows * kWidth * sizeof(float), "act1"},
         {(void**)&m->gxbuf, (size_t)m->chunk_rows * kGxPad * sizeof(float), "gamma(x)"},
+        {(void**)&m->loop.plan, sizeof(LoopPlan), "loop plan"},
+        {(void**)&m->loop.qs, (size_t)cfg->max_queries * sizeof(LoopQuery), "loop state"},
+        {(void**)&m->loop.n0, (size_t)cfg->max_queries * sizeof(int), "loop n0"},
+        {(void**)&m->loop.imgs, (size_t)cfg->max_queries * sizeof(float*), "loop images"},
+        {(void**)&m->loop.pix, (size_t)cfg->max_queries * kLoopMaxPixels * 2 * sizeof(int32_t),
+         "loop pixels"},
+        {(void**)&m->loop.P_next, (size_t)cfg->max_particles * 12 * sizeof(float), "loop particles"},
+        {(void**)&m->loop.w, (size_t)cfg->max_particles * sizeof(double), "loop weights"},
+        {(void**)&m->loop.mask, (size_t)cfg->max_particles, "loop mask"},
+        {(void**)&m->loop.idx, (size_t)cfg->max_particles * sizeof(int32_t), "loop indices"},
     };
     for (auto& a : allocs) {
         if ((rc = cuda_check(cudaMalloc(a.p, a.bytes), a.what))) {
@@ -197,6 +214,13 @@ extern "C" int mcl_init_map(const float* host_weights, size_t n_floats, const mc
         }
     }
     cudaMemset(m->status, 0, sizeof(Status));
+    if ((rc = cuda_check(cudaStreamCreateWithFlags(&m->loop.stream, cudaStreamNonBlocking),
+                         "loop stream")) ||
+        (rc = cuda_check(cudaEventCreateWithFlags(&m->loop.ev_in, cudaEventDisableTiming), "event")) ||
+        (rc = cuda_check(cudaEventCreateWithFlags(&m->loop.ev_out, cudaEventDisableTiming), "event"))) {
+        free_map(m);
+        return rc;
+    }
     if ((rc = mlp_tc_prepare(m, host_weights))) {
         free_map(m);
         return rc;
@@ -253,12 +277,12 @@ static int render_passes(mcl_map* m, const float* d_poses, int N, const mcl_intr
                              "raygen")))
             return rc;
         if (o->precision != MCL_PREC_FP32 &&
-            (rc = cuda_check(mlp_tc_ray_bias(m, m->gd, nr, s), "per-ray bias")))
+            (rc = cuda_check(mlp_tc_ray_bias(m, m->gd, nr, nullptr, s), "per-ray bias")))
             return rc;
     }
     auto mlp = [&](const float* z, int S, float4* out) -> cudaError_t {
         if (o->precision == MCL_PREC_FP32) return mlp_fp32(m, m->rays, m->gd, z, S, nr, out, s);
-        return mlp_tc(m, o->precision, m->rays, m->gd, z, S, nr, out, s);
+        return mlp_tc(m, o->precision, m->rays, m->gd, z, S, nr, nullptr, out, s);
     };
     {
         PhaseScope ph(m, MCL_PHASE_MLP_COARSE, s);
@@ -267,7 +291,7 @@ static int render_passes(mcl_map* m, const float* d_poses, int N, const mcl_intr
     if (o->n_fine > 0) {
         {
             PhaseScope ph(m, MCL_PHASE_SAMPLE, s);
-            if ((rc = cuda_check(launch_coarse_to_fine(m->rays, nr, m->zc, o->n_coarse, m->out_c,
+            if ((rc = cuda_check(launch_coarse_to_fine(m->rays, nr, nullptr, m->zc, o->n_coarse, m->out_c,
                                                        o->n_fine, m->zf, s),
                                  "importance sampling")))
                 return rc;
@@ -320,8 +344,9 @@ extern "C" int mcl_query(mcl_map* m, const float* d_x, const float* d_dir, int n
         return rc;
     if (precision == MCL_PREC_FP32)
         return cuda_check(mlp_fp32(m, m->rays, m->gd, m->zc, 1, n, (float4*)d_out, s), "query mlp");
-    if ((rc = cuda_check(mlp_tc_ray_bias(m, m->gd, n, s), "query ray bias"))) return rc;
-    return cuda_check(mlp_tc(m, precision, m->rays, m->gd, m->zc, 1, n, (float4*)d_out, s), "query mlp");
+    if ((rc = cuda_check(mlp_tc_ray_bias(m, m->gd, n, nullptr, s), "query ray bias"))) return rc;
+    return cuda_check(mlp_tc(m, precision, m->rays, m->gd, m->zc, 1, n, nullptr, (float4*)d_out, s),
+                      "query mlp");
 }
 
 extern "C" int mcl_render(mcl_map* m, const float* d_poses, int n_poses, const mcl_intrinsics* K,
@@ -429,4 +454,116 @@ extern "C" int mcl_map_supports(const mcl_map* m, int precision) {
     if (precision == MCL_PREC_FP32) return 1;
     if (precision == MCL_PREC_BF16) return mlp_tc_available(m) ? 1 : 0;
     return 0;
+}
+
+extern "C" int mcl_draw_pixels(int W, int H, int B, uint64_t seed, uint64_t counter,
+                               int32_t* d_out, void* stream) {
+    g_err[0] = 0;
+    if (!d_out || W < 1 || H < 1 || B < 1 || B > 1024 || (long)B > (long)W * H)
+        return fail(MCL_ERR_ARG, "mcl_draw_pixels: bad argument (W %d H %d B %d)", W, H, B);
+    return cuda_check(launch_draw_pixels(W, H, B, seed, counter, d_out, (cudaStream_t)stream),
+                      "draw pixels");
+}
+
+static unsigned long long mix_key(unsigned long long h, const void* p, size_t n) {
+    const unsigned char* b = (const unsigned char*)p;
+    for (size_t i = 0; i < n; ++i) h = (h ^ b[i]) * 0x100000001B3ull;  // FNV-1a
+    return h;
+}
+
+extern "C" int mcl_localize(mcl_map* m, int nq, float* d_particles, int stride, const int* h_n0,
+                            const float* const* h_images, const mcl_intrinsics* K,
+                            const mcl_schedule* sch, const mcl_opts* o, mcl_iter_record* d_log,
+                            int* d_final_n, int use_graph, void* stream) {
+    g_err[0] = 0;
+    int rc;
+    if (!m || !d_particles || !h_n0 || !h_images || !K || !sch || !o || !d_log || !d_final_n)
+        return fail(MCL_ERR_ARG, "mcl_localize: NULL argument");
+    if ((rc = check_opts(o))) return rc;
+    if (!(o->precision == MCL_PREC_BF16 && mlp_tc_available(m)))
+        return fail(MCL_ERR_UNSUPPORTED, "mcl_localize: needs the BF16 tensor-core form");
+    if (nq < 1 || nq > m->cfg.max_queries) return fail(MCL_ERR_ARG, "mcl_localize: n_queries %d", nq);
+    if (stride < 1 || (long)nq * stride > m->cfg.max_particles)
+        return fail(MCL_ERR_ARG, "mcl_localize: n_queries * stride > max_particles");
+    if (sch->n_stages < 1 || sch->n_stages > MCL_MAX_STAGES || sch->iterations < 1 || sch->n_min < 1)
+        return fail(MCL_ERR_ARG, "mcl_localize: bad schedule");
+    int maxB = 0, maxf = 1;
+    for (int st = 0; st < sch->n_stages; ++st) {
+        if (sch->level[st] < 0 || sch->level[st] > 2 || sch->n_pixels[st] < 1 ||
+            sch->n_pixels[st] > kLoopMaxPixels || sch->n_cap[st] < 1 || sch->n_cap[st] > stride ||
+            sch->stage_iter_cap[st] < 1)
+            return fail(MCL_ERR_ARG, "mcl_localize: bad stage %d", st);
+        const int f = 4 >> sch->level[st];
+        if (sch->n_pixels[st] > maxB) maxB = sch->n_pixels[st];
+        if (f > maxf) maxf = f;
+        if ((long)(K->width / f) * (K->height / f) < sch->n_pixels[st])
+            return fail(MCL_ERR_ARG, "mcl_localize: stage %d asks for more pixels than its level has", st);
+    }
+    if (!(sch->sigma_t >= 0.f) || !(sch->sigma_yaw >= 0.f))
+        return fail(MCL_ERR_ARG, "mcl_localize: negative motion noise");
+    if (K->width < 1 || K->height < 1 || K->width % maxf || K->height % maxf || !(K->fx > 0.f) ||
+        !(K->fy > 0.f))
+        return fail(MCL_ERR_ARG, "mcl_localize: bad intrinsics for the schedule's levels");
+    for (int q = 0; q < nq; ++q) {
+        if (h_n0[q] < 1 || h_n0[q] > stride) return fail(MCL_ERR_ARG, "mcl_localize: n0[%d]", q);
+        if (!h_images[q]) return fail(MCL_ERR_ARG, "mcl_localize: image %d is NULL", q);
+    }
+    const long max_rays_run = (long)nq * stride * maxB;
+    if (max_rays_run > m->cfg.max_rays)
+        return fail(MCL_ERR_ARG, "mcl_localize: n_queries * stride * max B = %ld > max_rays %d",
+                    max_rays_run, m->cfg.max_rays);
+    if (o->n_coarse + o->n_fine > m->cfg.max_samples)
+        return fail(MCL_ERR_ARG, "mcl_localize: n_coarse + n_fine > max_samples");
+    cudaStream_t caller = (cudaStream_t)stream;
+    // graph mode captures on the map's own stream, ordered after the caller's
+    // work and before the caller's later work by two events
+    cudaStream_t s = use_graph ? m->loop.stream : caller;
+    if (use_graph) {
+        if ((rc = cuda_check(cudaEventRecord(m->loop.ev_in, caller), "event record")) ||
+            (rc = cuda_check(cudaStreamWaitEvent(s, m->loop.ev_in, 0), "stream wait")))
+            return rc;
+    }
+    // per-call inputs read by the run's kernels
+    if ((rc = cuda_check(cudaMemcpyAsync(m->loop.n0, h_n0, sizeof(int) * nq, cudaMemcpyHostToDevice, s),
+                         "upload n0")))
+        return rc;
+    if ((rc = cuda_check(cudaMemcpyAsync((void*)m->loop.imgs, h_images, sizeof(float*) * nq,
+                                         cudaMemcpyHostToDevice, s),
+                         "upload image pointers")))
+        return rc;
+    m->loop.max_rays_run = (int)max_rays_run;
+    if (!use_graph)
+        return enqueue_localize(m, nq, d_particles, stride, *K, *sch, *o, d_log, d_final_n, s);
+    unsigned long long key = 1469598103934665603ull;
+    const void* ptrs[] = {d_particles, d_log, d_final_n};
+    key = mix_key(key, &nq, sizeof(nq));
+    key = mix_key(key, &stride, sizeof(stride));
+    key = mix_key(key, ptrs, sizeof(ptrs));
+    key = mix_key(key, K, sizeof(*K));
+    key = mix_key(key, sch, sizeof(*sch));
+    key = mix_key(key, o, sizeof(*o));
+    if (!m->loop.exec || m->loop.key != key) {
+        if (m->loop.exec) {
+            cudaGraphExecDestroy(m->loop.exec);
+            m->loop.exec = nullptr;
+        }
+        if ((rc = cuda_check(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal),
+                             "begin capture")))
+            return rc;
+        const int erc = enqueue_localize(m, nq, d_particles, stride, *K, *sch, *o, d_log, d_final_n, s);
+        cudaGraph_t g = nullptr;
+        const cudaError_t ce = cudaStreamEndCapture(s, &g);
+        if (erc) {
+            if (g) cudaGraphDestroy(g);
+            return erc;
+        }
+        if ((rc = cuda_check(ce, "end capture"))) return rc;
+        rc = cuda_check(cudaGraphInstantiate(&m->loop.exec, g, 0), "instantiate graph");
+        cudaGraphDestroy(g);
+        if (rc) return rc;
+        m->loop.key = key;
+    }
+    if ((rc = cuda_check(cudaGraphLaunch(m->loop.exec, s), "launch graph"))) return rc;
+    if ((rc = cuda_check(cudaEventRecord(m->loop.ev_out, s), "event record"))) return rc;
+    return cuda_check(cudaStreamWaitEvent(caller, m->loop.ev_out, 0), "stream wait");
 }

@@ -43,6 +43,40 @@ struct __align__(16) Ray {
     float lx, ly, lz, pad2;
 };
 
+// Device-driven localisation loop (loop.cu).
+constexpr int kLoopMaxQueries = 64;
+constexpr int kLoopMaxPixels = 256;
+
+struct LoopPlan {
+    int total_rays, rows_c, rows_f, pad;
+    int ray_off[kLoopMaxQueries + 1];
+    int N[kLoopMaxQueries], B[kLoopMaxQueries], factor[kLoopMaxQueries], Nnext[kLoopMaxQueries];
+};
+
+struct LoopQuery {
+    int stage, iter_at_stage, N, n_surv, nonfinite, pad;
+    double wspread;
+};
+
+struct LoopWork {
+    LoopPlan* plan = nullptr;
+    LoopQuery* qs = nullptr;
+    int* n0 = nullptr;
+    const float** imgs = nullptr;
+    int32_t* pix = nullptr;
+    float* P_next = nullptr;
+    double* w = nullptr;
+    uint8_t* mask = nullptr;
+    int32_t* idx = nullptr;
+    int max_rays_run = 0;
+    cudaGraphExec_t exec = nullptr;
+    unsigned long long key = 0;
+    // capture stream (graph mode on the legacy default stream) and the
+    // events that order it with the caller's stream
+    cudaStream_t stream = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+};
+
 }  // namespace mcl
 
 // The map: weights in the forms each MLP path reads, plus the workspace.
@@ -81,6 +115,7 @@ struct mcl_map {
     std::vector<Mark> marks;
     std::vector<cudaEvent_t> pool;
     double phase_ms[MCL_N_PHASES] = {0};
+    mcl::LoopWork loop;
 };
 
 namespace mcl {
@@ -97,8 +132,9 @@ cudaError_t launch_raygen(const float* particles, int N, const int32_t* pixels, 
                           Ray* rays, float* gd, float* zc, cudaStream_t s);
 cudaError_t launch_query_setup(const float* X, const float* D, int n, Ray* rays, float* gd,
                                float* z, cudaStream_t s);
-cudaError_t launch_coarse_to_fine(const Ray* rays, int n_rays, const float* zc, int nc,
-                                  const float4* out_c, int nf, float* zf, cudaStream_t s);
+cudaError_t launch_coarse_to_fine(const Ray* rays, int n_rays, const int* n_rays_dev,
+                                  const float* zc, int nc, const float4* out_c, int nf, float* zf,
+                                  cudaStream_t s);
 cudaError_t launch_final_composite(const Ray* rays, int n_rays, const float* zc, const float4* out_c,
                                    int nc, const float* zf, const float4* out_f, int nf,
                                    const float* image, int W, int H, int factor,
@@ -117,9 +153,11 @@ cudaError_t mlp_fp32(mcl_map* m, const Ray* rays, const float* gd, const float* 
 int mlp_tc_prepare(mcl_map* m, const float* host_blob);
 void mlp_tc_free(mcl_map* m);
 bool mlp_tc_available(const mcl_map* m);
-cudaError_t mlp_tc_ray_bias(mcl_map* m, const float* gd, int n_rays, cudaStream_t s);
+cudaError_t mlp_tc_ray_bias(mcl_map* m, const float* gd, int n_rays, const int* n_rays_dev,
+                            cudaStream_t s);
+// rows_dev (optional): device-side row count (rows = n_rays * S is the bound).
 cudaError_t mlp_tc(mcl_map* m, int precision, const Ray* rays, const float* gd, const float* z,
-                   int S, int n_rays, float4* out, cudaStream_t s);
+                   int S, int n_rays, const int* rows_dev, float4* out, cudaStream_t s);
 
 // resample.cu
 cudaError_t launch_resample(const double* w, int n_in, int n_out, double u0, int32_t* idx,
@@ -129,5 +167,12 @@ cudaError_t launch_predict(const float* in, int n_in, const int32_t* idx, int n_
                            cudaStream_t s);
 cudaError_t launch_downscale(const float* img, int W, int H, int f, float* out, cudaStream_t s);
 cudaError_t launch_position_spread(const float* poses, int N, double* out, cudaStream_t s);
+
+// loop.cu
+cudaError_t launch_draw_pixels(int W, int H, int B, uint64_t seed, uint64_t ctr, int32_t* out,
+                               cudaStream_t s);
+int enqueue_localize(mcl_map* m, int nq, float* P_user, int stride, const mcl_intrinsics& K,
+                     const mcl_schedule& sch, const mcl_opts& o, mcl_iter_record* d_log,
+                     int* d_final_n, cudaStream_t s);
 
 }  // namespace mcl

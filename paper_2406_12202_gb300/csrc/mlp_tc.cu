@@ -76,8 +76,9 @@ struct Params {
     const Ray* rays;
     const float* z;
     int S;
-    long long M;            // rows of the pass
+    long long M;            // rows of the pass (upper bound when M_dev is set)
     long long n_pairs;
+    const int* M_dev;       // optional: rows of the pass from device memory
     const uint32_t* bias2;  // [8][128] trunk biases as BF16 pairs
     float b_sigma;
     const float* ray_bias;  // [n_rays][128]
@@ -160,6 +161,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t s_ring = s_gx + 2 * kGxBytes;              // kStages x 16 KB
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     volatile int* abort_flag = p.abort_flag;
+    // rows of this pass: fixed, or decided on the device by an earlier kernel
+    const long long M = p.M_dev ? min(p.M, (long long)*p.M_dev) : p.M;
+    const long long n_pairs = (M + 255) / 256;
 
     if (tid == 0) {
         for (int i = 0; i < kStages; ++i) {
@@ -189,7 +193,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             uint32_t issued[kStages] = {0, 0, 0, 0};
             uint32_t g = 0;
             bool ok = true;
-            for (long long pr = blockIdx.x; pr < p.n_pairs && ok; pr += gridDim.x) {
+            for (long long pr = blockIdx.x; pr < n_pairs && ok; pr += gridDim.x) {
                 for (int b = 0; b < kBlocksPerPair; ++b, ++g) {
                     const uint32_t st = g % kStages, ph = (g / kStages) & 1u;
                     TC_TRACE(0, g);
@@ -218,7 +222,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             bool ok = true;
             const uint32_t id256 = idesc_bf16(128, 256), id144 = idesc_bf16(128, 144);
             int tl = 0;
-            for (long long pr = blockIdx.x; pr < p.n_pairs && ok; pr += gridDim.x) {
+            for (long long pr = blockIdx.x; pr < n_pairs && ok; pr += gridDim.x) {
                 for (int l = 0; l < kLayers && ok; ++l, ++tl) {
                     const int nch = c_chunks[l];
                     const uint32_t idesc = (l == 8) ? id144 : id256;
@@ -286,9 +290,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         bool ok = true;
         const bool tracer = (r == 0);
         int tl = 0;
-        for (long long pr = blockIdx.x; pr < p.n_pairs && ok; pr += gridDim.x) {
+        for (long long pr = blockIdx.x; pr < n_pairs && ok; pr += gridDim.x) {
             const long long grow = pr * 256 + slot * 128 + r;
-            const bool valid = grow < p.M;
+            const bool valid = grow < M;
             const long long ray = valid ? grow / p.S : 0;
             // ---- prologue: gamma(x) of this row into the tile's gamma(x) buffer
             {
@@ -413,10 +417,12 @@ __global__ void __launch_bounds__(kThreads, 1)
 }
 
 // Per-ray bias of the RGB hidden layer: b'_ray = b' + W_rgb_hidden[:, 256:283] gamma(d).
-__global__ void k_ray_bias(const float* __restrict__ gd, int n_rays, const float* __restrict__ Wd,
-                           const float* __restrict__ bprime, float* __restrict__ out) {
+__global__ void k_ray_bias(const float* __restrict__ gd, int n_rays, const int* __restrict__ n_dev,
+                           const float* __restrict__ Wd, const float* __restrict__ bprime,
+                           float* __restrict__ out) {
     const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= (long)n_rays * 128) return;
+    const int n = n_dev ? min(n_rays, *n_dev) : n_rays;
+    if (t >= (long)n * 128) return;
     const long ray = t >> 7;
     const int o = (int)(t & 127);
     const float* g = gd + ray * kGdPad;
@@ -603,17 +609,18 @@ bool mlp_tc_available(const mcl_map* m) {
     return st && st->ready;
 }
 
-cudaError_t mlp_tc_ray_bias(mcl_map* m, const float* gd, int n_rays, cudaStream_t s) {
+cudaError_t mlp_tc_ray_bias(mcl_map* m, const float* gd, int n_rays, const int* n_rays_dev,
+                            cudaStream_t s) {
     TcState* st = (TcState*)m->tc_aux;
     const long n = (long)n_rays * 128;
     note_launch();
-    k_ray_bias<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(gd, n_rays, st->Wd, st->bprime,
-                                                           st->ray_bias);
+    k_ray_bias<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(gd, n_rays, n_rays_dev, st->Wd,
+                                                           st->bprime, st->ray_bias);
     return cudaGetLastError();
 }
 
 cudaError_t mlp_tc(mcl_map* m, int precision, const Ray* rays, const float* gd, const float* z,
-                   int S, int n_rays, float4* out, cudaStream_t s) {
+                   int S, int n_rays, const int* rows_dev, float4* out, cudaStream_t s) {
     (void)gd;
     TcState* st = (TcState*)m->tc_aux;
     if (!st || !st->ready || precision != MCL_PREC_BF16) return cudaErrorNotSupported;
@@ -623,6 +630,7 @@ cudaError_t mlp_tc(mcl_map* m, int precision, const Ray* rays, const float* gd, 
     p.S = S;
     p.M = (long long)n_rays * S;
     p.n_pairs = (p.M + 255) / 256;
+    p.M_dev = rows_dev;
     p.bias2 = st->bias2;
     p.b_sigma = st->b_sigma;
     p.ray_bias = st->ray_bias;

@@ -1,21 +1,16 @@
-// render.cu -- the SIMT stages of the weight update around the NeRF MLP:
+// render.cu -- the SIMT stages of one weight update around the NeRF MLP:
 // ray generation and stratified samples, coarse compositing with importance
 // sampling, the final composite with Eq. 5 / F and the photometric match, and
-// the Eq. 6 weights with FP64 log-sum-exp normalisation.
+// the Eq. 6 weights with FP64 log-sum-exp normalisation (bodies in
+// stages.cuh).
 #include <math.h>
 
-#include "internal.cuh"
-#include "rng.cuh"
+#include "stages.cuh"
 
 namespace mcl {
 
-// ---------------------------------------------------------------------------
-// Ray generation (pixel-centre rays of R K, camera looking along -z, +y up)
-// and stratified coarse samples z_k = near + (far - near)(k + u_k)/n_c with
-// u_k = 1/2, or SplitMix64 stream (seed, counter) value ray*n_c + k.  Also
-// gamma(d) of the unit direction (positional encoding with 4 frequencies),
-// which is constant along the ray.  One thread per ray r = i*B + j.
-// ---------------------------------------------------------------------------
+// One thread per ray r = i*B + j: pixel-centre ray of particle i through
+// pixel j with the level intrinsics, gamma(d), stratified coarse samples.
 __global__ void k_raygen(const float* __restrict__ P, int N, const int32_t* __restrict__ px,
                          int B, float fx, float fy, float cx, float cy, int nc, float near_z,
                          float far_z, int jitter, uint64_t seed, uint64_t ctr,
@@ -23,55 +18,11 @@ __global__ void k_raygen(const float* __restrict__ P, int N, const int32_t* __re
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= N * B) return;
     const int i = r / B, j = r - (r / B) * B;
-    const float* p = P + 12 * (size_t)i;
-    // direction in FP64 (pose and pixel are exact FP32 inputs), kept as a
-    // rounded FP32 value plus its rounding error
-    const double u = (double)px[2 * j], v = (double)px[2 * j + 1];
-    const double ax = (u + 0.5 - (double)cx) / (double)fx;
-    const double ay = -(v + 0.5 - (double)cy) / (double)fy;
-    const double az = -1.0;
-    double d[3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c)
-        d[c] = (double)p[4 * c] * ax + (double)p[4 * c + 1] * ay + (double)p[4 * c + 2] * az;
-    const double dn64 = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-    const float dx = (float)d[0], dy = (float)d[1], dz = (float)d[2];
-    // a pose with a non-finite entry marks its rays invalid (|d| = NaN); the
-    // composite turns that into a NaN loss, so the particle gets no weight
-    bool finite_pose = true;
-#pragma unroll
-    for (int c = 0; c < 12; ++c) finite_pose = finite_pose && isfinite(p[c]);
-    const float dn = finite_pose ? (float)dn64 : __int_as_float(0x7fc00000);
     Ray ray;
-    ray.ox = p[3]; ray.oy = p[7]; ray.oz = p[11]; ray.dnorm = dn;
-    ray.dx = dx; ray.dy = dy; ray.dz = dz; ray.pad = 0.f;
-    ray.lx = (float)(d[0] - (double)dx);
-    ray.ly = (float)(d[1] - (double)dy);
-    ray.lz = (float)(d[2] - (double)dz);
-    ray.pad2 = 0.f;
+    make_ray(P + 12 * (size_t)i, px[2 * j], px[2 * j + 1], fx, fy, cx, cy, ray,
+             gd + (size_t)r * kGdPad);
     rays[r] = ray;
-    const float h[3] = {(float)(d[0] / dn64), (float)(d[1] / dn64), (float)(d[2] / dn64)};
-    float* g = gd + (size_t)r * kGdPad;
-    g[0] = h[0]; g[1] = h[1]; g[2] = h[2];
-#pragma unroll
-    for (int k = 0; k < kLdir; ++k) {
-        const float f = (float)(1 << k);
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            float sn, cs;
-            sincosf(f * h[c], &sn, &cs);
-            g[3 + 6 * k + c] = sn;
-            g[6 + 6 * k + c] = cs;
-        }
-    }
-#pragma unroll
-    for (int c = kGd; c < kGdPad; ++c) g[c] = 0.f;
-    float* z = zc + (size_t)r * nc;
-    const float span = far_z - near_z;
-    for (int k = 0; k < nc; ++k) {
-        const float uk = jitter ? (float)cb_uniform(seed, ctr, (uint64_t)r * nc + k) : 0.5f;
-        z[k] = near_z + span * ((float)k + uk) / (float)nc;
-    }
+    coarse_samples(r, nc, near_z, far_z, jitter, seed, ctr, zc + (size_t)r * nc);
 }
 
 // Point queries: one "ray" per point with o = x, d = 0 and one sample at
@@ -124,73 +75,31 @@ cudaError_t launch_raygen(const float* particles, int N, const int32_t* pixels, 
     return cudaGetLastError();
 }
 
-// ---------------------------------------------------------------------------
-// Coarse composite (Eq. 1 quadrature) and inverse-CDF importance samples.
-// Edges = midpoints of consecutive coarse z; pdf over the interior bins
-// proportional to w_1..w_{n_c-2} + 1e-5; u_j = j/(n_f - 1); the bin is the
-// first CDF entry strictly greater than u_j (u sorted, so one sweep).  One
-// thread per ray.
-// ---------------------------------------------------------------------------
+// Coarse composite and importance samples, one thread per ray.  n_rays_dev
+// (optional) bounds the rays from device memory.
 __global__ void k_coarse_to_fine(const Ray* __restrict__ rays, int n_rays,
-                                 const float* __restrict__ zc, int nc,
-                                 const float4* __restrict__ out_c, int nf, float* __restrict__ zf) {
+                                 const int* __restrict__ n_rays_dev, const float* __restrict__ zc,
+                                 int nc, const float4* __restrict__ out_c, int nf,
+                                 float* __restrict__ zf) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= n_rays) return;
-    const float* z = zc + (size_t)r * nc;
-    const float4* o = out_c + (size_t)r * nc;
-    const float dn = rays[r].dnorm;
-    float cdf[kMaxCoarse];
-    // weights of the interior samples go straight into pdf slots cdf[1..nc-2]
-    float T = 1.0f;
-    float tot = 0.0f;
-    for (int k = 0; k < nc; ++k) {
-        const float sg = fmaxf(o[k].x, 0.0f);
-        const float delta = (k < nc - 1) ? (z[k + 1] - z[k]) * dn : 1e10f;
-        const float a = 1.0f - expf(-sg * delta);
-        const float w = T * a;
-        T *= (1.0f - a);
-        if (k >= 1 && k <= nc - 2) {
-            cdf[k] = w + 1e-5f;
-            tot += w + 1e-5f;
-        }
-    }
-    const int ne = nc - 1;
-    cdf[0] = 0.0f;
-    float run = 0.0f;
-    for (int i = 1; i < ne; ++i) {
-        run += cdf[i] / tot;
-        cdf[i] = run;
-    }
-    float* out = zf + (size_t)r * nf;
-    int idx = 0;
-    for (int j = 0; j < nf; ++j) {
-        const float u = nf > 1 ? (float)j / (float)(nf - 1) : 0.0f;
-        while (idx < ne && cdf[idx] <= u) ++idx;
-        const int below = idx - 1 < 0 ? 0 : idx - 1;
-        const int above = idx > ne - 1 ? ne - 1 : idx;
-        float denom = cdf[above] - cdf[below];
-        if (denom < 1e-5f) denom = 1.0f;
-        const float t = (u - cdf[below]) / denom;
-        const float eb = 0.5f * (z[below] + z[below + 1]);
-        const float ea = 0.5f * (z[above] + z[above + 1]);
-        out[j] = eb + t * (ea - eb);
-    }
+    const int n = n_rays_dev ? min(n_rays, *n_rays_dev) : n_rays;
+    if (r >= n) return;
+    importance_samples(zc + (size_t)r * nc, out_c + (size_t)r * nc, nc, rays[r].dnorm, nf,
+                       zf + (size_t)r * nf);
 }
 
-cudaError_t launch_coarse_to_fine(const Ray* rays, int n_rays, const float* zc, int nc,
-                                  const float4* out_c, int nf, float* zf, cudaStream_t s) {
+cudaError_t launch_coarse_to_fine(const Ray* rays, int n_rays, const int* n_rays_dev,
+                                  const float* zc, int nc, const float4* out_c, int nf, float* zf,
+                                  cudaStream_t s) {
     const int tb = 128;
     note_launch();
-    k_coarse_to_fine<<<(n_rays + tb - 1) / tb, tb, 0, s>>>(rays, n_rays, zc, nc, out_c, nf, zf);
+    k_coarse_to_fine<<<(n_rays + tb - 1) / tb, tb, 0, s>>>(rays, n_rays, n_rays_dev, zc, nc, out_c,
+                                                            nf, zf);
     return cudaGetLastError();
 }
 
-// ---------------------------------------------------------------------------
-// Final composite over the merged coarse + fine samples (both sorted; equal z
-// take the coarse sample first), Eq. 5 on the running weight sum, F of
-// Eq. 6, and E = squared RGB distance to the box-filtered observed pixel.
-// image == NULL: render only (rgb_out / F_out).  One thread per ray.
-// ---------------------------------------------------------------------------
+// Final composite, Eq. 5 / F and E against the level image, one thread per
+// ray.  image == NULL: render only (rgb_out / F_out).
 __global__ void k_final(const Ray* __restrict__ rays, int n_rays, const float* __restrict__ zc,
                         const float4* __restrict__ oc, int nc, const float* __restrict__ zf,
                         const float4* __restrict__ of, int nf, const float* __restrict__ img,
@@ -201,44 +110,13 @@ __global__ void k_final(const Ray* __restrict__ rays, int n_rays, const float* _
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n_rays) return;
     const float dn = rays[r].dnorm;
-    const float* za = zc + (size_t)r * nc;
-    const float4* oa = oc + (size_t)r * nc;
-    const float* zb = zf + (size_t)r * nf;
-    const float4* ob = of + (size_t)r * nf;
-    int ia = 0, ib = 0;
-    auto take = [&](float& z, float4& v) {
-        if (ib >= nf || (ia < nc && za[ia] <= zb[ib])) {
-            z = za[ia]; v = oa[ia]; ++ia;
-        } else {
-            z = zb[ib]; v = ob[ib]; ++ib;
-        }
-    };
-    const int n = nc + nf;
-    float zcur, znext = 0.f;
-    float4 vcur, vnext = make_float4(0.f, 0.f, 0.f, 0.f);
-    take(zcur, vcur);
-    const float z0 = zcur;
-    float T = 1.0f, cr = 0.f, cg = 0.f, cb = 0.f, Wc = 0.f;
-    float zt = z0, zo = z0;
-    bool have_t = false;
-    for (int k = 0; k < n; ++k) {
-        if (k < n - 1) take(znext, vnext);
-        const float delta = (k < n - 1) ? (znext - zcur) * dn : 1e10f;
-        const float sg = fmaxf(vcur.x, 0.0f);
-        const float a = 1.0f - expf(-sg * delta);
-        const float w = T * a;
-        cr += w * vcur.y; cg += w * vcur.z; cb += w * vcur.w;
-        T *= (1.0f - a);
-        Wc += w;
-        if (!have_t && Wc >= alpha) { zt = zcur; have_t = true; }
-        if (Wc <= 1.0f - alpha) zo = zcur;
-        zcur = znext; vcur = vnext;
-    }
-    const float F = use_rej ? fmaxf(zo - zt, tau) : 1.0f;
-    if (d_rgb) { d_rgb[3 * (size_t)r] = cr; d_rgb[3 * (size_t)r + 1] = cg; d_rgb[3 * (size_t)r + 2] = cb; }
-    if (d_F) d_F[r] = F;
-    if (d_zt) d_zt[r] = zt;
-    if (d_zo) d_zo[r] = zo;
+    const RayResult c = composite_ray(dn, zc + (size_t)r * nc, oc + (size_t)r * nc, nc,
+                                      zf + (size_t)r * nf, of + (size_t)r * nf, nf, alpha, tau,
+                                      use_rej);
+    if (d_rgb) { d_rgb[3 * (size_t)r] = c.r; d_rgb[3 * (size_t)r + 1] = c.g; d_rgb[3 * (size_t)r + 2] = c.b; }
+    if (d_F) d_F[r] = c.F;
+    if (d_zt) d_zt[r] = c.z_trans;
+    if (d_zo) d_zo[r] = c.z_opaque;
     if (img) {
         const int j = r % B;
         const int u = px[2 * j], v = px[2 * j + 1];
@@ -248,18 +126,9 @@ __global__ void k_final(const Ray* __restrict__ rays, int n_rays, const float* _
             e_ray[r] = __int_as_float(0x7fc00000);
             return;
         }
-        float s0 = 0.f, s1 = 0.f, s2 = 0.f;
-        for (int dy = 0; dy < factor; ++dy) {
-            const float* row = img + ((size_t)(v * factor + dy) * W + (size_t)u * factor) * 3;
-            for (int dx = 0; dx < factor; ++dx) {
-                s0 += row[3 * dx]; s1 += row[3 * dx + 1]; s2 += row[3 * dx + 2];
-            }
-        }
-        const float inv = 1.0f / (float)(factor * factor);
-        const float e0 = s0 * inv - cr, e1 = s1 * inv - cg, e2 = s2 * inv - cb;
-        const float E = isfinite(dn) ? e0 * e0 + e1 * e1 + e2 * e2 : __int_as_float(0x7fc00000);
+        const float E = photometric_E(img, W, factor, u, v, c, dn);
         if (d_E) d_E[r] = E;
-        e_ray[r] = E * F;
+        e_ray[r] = E * c.F;
     }
 }
 
@@ -280,84 +149,13 @@ cudaError_t launch_final_composite(const Ray* rays, int n_rays, const float* zc,
     return cudaGetLastError();
 }
 
-// ---------------------------------------------------------------------------
-// Eq. 6 weights: S_i = sum_j E_ij F_ij (FP32, in j order), log w_i =
-// 4 (log B - log max(S_i, s_min)) and the normalisation
-// w_i = exp(log w_i - logsumexp) in FP64; mask_i = (w_i >= rho / N).  One
-// block; non-finite S_i -> log w = -inf, counted in the status word.
-// ---------------------------------------------------------------------------
 constexpr int kNormThreads = 1024;
-
-__device__ double block_reduce_max(double v, double* sh) {
-    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    __syncthreads();
-    if (l == 0) sh[w] = v;
-    __syncthreads();
-    if (w == 0) {
-        v = l < (int)(blockDim.x >> 5) ? sh[l] : -INFINITY;
-        for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-        if (l == 0) sh[0] = v;
-    }
-    __syncthreads();
-    return sh[0];
-}
-
-__device__ double block_reduce_sum(double v, double* sh) {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    __syncthreads();
-    if (l == 0) sh[w] = v;
-    __syncthreads();
-    if (w == 0) {
-        v = l < (int)(blockDim.x >> 5) ? sh[l] : 0.0;
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (l == 0) sh[0] = v;
-    }
-    __syncthreads();
-    return sh[0];
-}
 
 __global__ __launch_bounds__(kNormThreads) void k_weights(
     const float* __restrict__ e_ray, int N, int B, double s_min, double rho,
     float* __restrict__ logw, double* __restrict__ l64, double* __restrict__ w,
     uint8_t* __restrict__ mask, float* __restrict__ S_dbg, Status* status) {
-    __shared__ double sh[32];
-    __shared__ int nbad;
-    if (threadIdx.x == 0) nbad = 0;
-    __syncthreads();
-    const double logB = log((double)B);
-    double mx = -INFINITY;
-    for (int i = threadIdx.x; i < N; i += blockDim.x) {
-        const float* e = e_ray + (size_t)i * B;
-        float S = 0.0f;
-        for (int j = 0; j < B; ++j) S += e[j];
-        if (S_dbg) S_dbg[i] = S;
-        double l;
-        if (isfinite(S)) {
-            const double sc = fmax((double)S, s_min);
-            l = 4.0 * (logB - log(sc));
-        } else {
-            l = -INFINITY;
-            atomicAdd(&nbad, 1);
-        }
-        l64[i] = l;
-        logw[i] = (float)l;
-        mx = fmax(mx, l);
-    }
-    mx = block_reduce_max(mx, sh);
-    double acc = 0.0;
-    if (mx > -INFINITY)
-        for (int i = threadIdx.x; i < N; i += blockDim.x) acc += exp(l64[i] - mx);
-    acc = block_reduce_sum(acc, sh);
-    const double lse = mx + log(acc);
-    const double thr = rho / (double)N;
-    for (int i = threadIdx.x; i < N; i += blockDim.x) {
-        const double wi = (mx > -INFINITY) ? exp(l64[i] - lse) : 0.0;
-        w[i] = wi;
-        mask[i] = (uint8_t)(wi >= thr && wi > 0.0);
-    }
-    __syncthreads();
+    const int nbad = weights_block(e_ray, N, B, s_min, rho, logw, l64, w, mask, S_dbg);
     if (threadIdx.x == 0 && nbad > 0) {
         atomicAdd(&status->n_nonfinite, nbad);
         atomicCAS(&status->code, 0, MCL_ERR_NONFINITE);

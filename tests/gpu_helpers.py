@@ -75,7 +75,7 @@ def run_oracle_update(sc, uj=None):
                          sc["opts"], uj=uj)
 
 
-def oracle_sensitivity(sc):
+def oracle_sensitivity(sc, uj=None):
     """How far the exact (FP64) answer itself moves when every coarse sample
     position moves by one FP32 ulp of z (4.8e-7 at z in [4, 8)): max |dRGB|
     and max relative |d logw| over the scene.  With importance sampling the
@@ -86,12 +86,17 @@ def oracle_sensitivity(sc):
     span = sc["opts"].far_z - sc["opts"].near_z
     n = sc["P"].shape[0] * sc["px"].shape[0]
     eps = 4.8e-7 / (span / nc)
-    a = run_oracle_update(sc, uj=np.full((n, nc), 0.5))
-    b = run_oracle_update(sc, uj=np.full((n, nc), 0.5 + eps))
+    base = np.full((n, nc), 0.5) if uj is None else np.reshape(uj, (n, nc))
+    a = run_oracle_update(sc, uj=base)
+    b = run_oracle_update(sc, uj=base + eps)
     ok = (a["S"] >= S_FLOOR) & (b["S"] >= S_FLOOR)
     dl = np.abs(a["logw"] - b["logw"])[ok] / np.maximum(np.abs(a["logw"][ok]), 1.0)
+    # how far the Eq. 5 decision margins move (rays whose decisions stay put)
+    same = (a["z_trans"] == b["z_trans"]) & (a["z_opaque"] == b["z_opaque"])
+    dt = np.abs(a["tie"] - b["tie"])[same]
     return dict(rgb=float(np.abs(a["rgb"] - b["rgb"]).max()),
-                logw=float(dl.max()) if dl.size else 0.0)
+                logw=float(dl.max()) if dl.size else 0.0,
+                tie=float(dt.max()) if dt.size else 0.0)
 
 
 # The FP32 GPU form is held to K_ULP one-ulp perturbations of the exact
@@ -101,47 +106,52 @@ K_ULP = 16
 
 def check_fp32_parity(g, r, N, B, rgb_rel=1e-4, rgb_abs=1e-6, logw_rel=1e-4, z_abs=2e-5,
                       sens=None):
-    """FP32 vs FP64 bars: RGB within rgb_rel relative (abs floor rgb_abs, or
-    K_ULP times the oracle's one-ulp sensitivity `sens` when given); F,
-    z_trans, z_opaque within z_abs on rays that are not near-tie; log-weights
-    within logw_rel relative (or K_ULP times the sensitivity) for particles
-    without near-tie rays and with S >= S_FLOOR; normalised weights consistent
-    with the log-weights.  Returns a dict of the observed maxima."""
+    """FP32 vs FP64 bars.
+    RGB: within rgb_rel relative plus rgb_abs (or, with importance samples,
+    K_ULP times the oracle's one-ulp sensitivity `sens`).
+    F, z_trans, z_opaque: within z_abs, except on near-tie rays (running
+    weight sum within the tie margin of alpha or 1 - alpha at a decision),
+    where a decision may move by one sample: within 2 steps + z_abs (step =
+    widest sample spacing next to a decision, reported by the oracle).
+    log-weights: |d logw_i| <= 4 dS_i / S_i + logw_rel |logw_i| with
+    dS_i = sum_j (E_ij dF_ij + F_ij dE_ij) from the per-ray allowances, for
+    particles with S_i >= S_FLOOR.  Normalised weights must follow the GPU's
+    own log-weights.  Returns a dict of the observed maxima."""
     rep = {}
     if sens is not None:
         rgb_abs = max(rgb_abs, K_ULP * sens["rgb"])
-        logw_rel = max(logw_rel, K_ULP * sens["logw"])
         rep["tol_rgb_abs"] = rgb_abs
-        rep["tol_logw_rel"] = logw_rel
     err = np.abs(g["rgb"] - r["rgb"])
     tol = rgb_rel * np.abs(r["rgb"]) + rgb_abs
     rep["rgb_max_abs"] = float(err.max())
-    rep["rgb_max_rel"] = float((err / np.maximum(np.abs(r["rgb"]), 1e-12)).max())
     assert np.all(err <= tol), f"RGB off: max err {err.max():.3g}, worst excess {(err - tol).max():.3g}"
-    # with importance samples the GPU's running weight sums differ from the
-    # oracle's by about the same relative amount as the colours, so the
-    # near-tie margin scales with the one-ulp sensitivity too
-    tie_thr = TIE if sens is None else max(TIE, K_ULP * sens["rgb"])
-    tie = r["tie"] < tie_thr
+    # Without importance samples the sample positions are exact and only rays
+    # whose running weight sum passes within TIE of a threshold may flip a
+    # decision.  With importance samples (or jitter) every sample position
+    # carries the FP32 rounding of the inverse CDF, so any decision may move
+    # by one sample: F is held to two decision steps on every ray.
+    tie = (r["tie"] < TIE) if sens is None else np.ones_like(r["tie"], dtype=bool)
     rep["near_tie_rays"] = int(tie.sum())
-    assert tie.mean() <= 0.25, f"too many near-tie rays ({tie.mean():.2f})"
-    ok = ~tie
+    f_allow = np.where(tie, 2.0 * r["step"] + z_abs, z_abs)
     for k in ("F", "z_trans", "z_opaque"):
-        d = np.abs(g[k] - r[k])[ok]
-        rep[f"{k}_max_abs"] = float(d.max()) if d.size else 0.0
-        assert np.all(d <= z_abs), f"{k} off by {d.max():.3g} on a non-tie ray"
-    e_err = np.abs(g["E"] - r["E"])
+        d = np.abs(g[k] - r[k])
+        rep[f"{k}_max_abs"] = float(d.max())
+        bad = d > f_allow * (1 + 1e-6)
+        assert not bad.any(), f"{k} off by {d[bad].max():.3g} (allowed {f_allow[bad].min():.3g})"
     # E = |obs - C|^2: dE = 2 |obs - C| dC + dC^2 with dC <= the RGB bar
     dC = rgb_rel * np.abs(r["rgb"]).max(1) + rgb_abs
-    e_tol = 2 * np.sqrt(3 * np.maximum(r["E"], 0)) * dC + 3 * dC ** 2 + 1e-7 * r["E"]
-    assert np.all(e_err <= e_tol * 1.0001), f"E off by {e_err.max():.3g}"
-    ptie = tie.reshape(N, B).any(1)
-    okp = (~ptie) & (r["S"] >= S_FLOOR)
-    rep["particles_compared"] = int(okp.sum())
+    e_allow = 2 * np.sqrt(3 * np.maximum(r["E"], 0)) * dC + 3 * dC ** 2 + 1e-7 * r["E"]
+    e_err = np.abs(g["E"] - r["E"])
+    assert np.all(e_err <= e_allow * 1.0001), f"E off by {e_err.max():.3g}"
+    Fr = r["F"] if np.any(r["F"] != 1.0) else np.ones_like(r["F"])
+    fa = f_allow if np.any(r["F"] != 1.0) else np.zeros_like(f_allow)
+    dS = (r["E"] * fa + (Fr + fa) * e_allow).reshape(N, B).sum(1)
+    okp = r["S"] >= S_FLOOR
+    lw_tol = 4.0 * dS[okp] / r["S"][okp] + logw_rel * np.maximum(np.abs(r["logw"][okp]), 1.0)
     lw_err = np.abs(g["logw"] - r["logw"])[okp]
-    rel = lw_err / np.maximum(np.abs(r["logw"][okp]), 1.0)
-    rep["logw_max_rel"] = float(rel.max()) if rel.size else 0.0
-    assert np.all(rel <= logw_rel), f"logw off: {rel.max():.3g}"
+    rep["particles_compared"] = int(okp.sum())
+    rep["logw_max_abs"] = float(lw_err.max()) if lw_err.size else 0.0
+    assert np.all(lw_err <= lw_tol * 1.0001), f"logw off: {lw_err.max():.3g} > {lw_tol.min():.3g}"
     assert abs(g["w"].sum() - 1.0) < 1e-12
     # normalised weights follow the GPU's own log-weights (FP64 log-sum-exp)
     lw = g["logw"]

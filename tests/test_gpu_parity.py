@@ -102,7 +102,7 @@ def test_jittered_strata(M, gmaps):
     r = run_oracle_update(sc, uj=uj)
     # jittered z are FP32 roundings of near + span (k + u)/n_c: the bar is the
     # one-ulp sensitivity of the exact answer, as for the fine samples
-    check_fp32_parity(g, r, N, B, sens=oracle_sensitivity(sc))
+    check_fp32_parity(g, r, N, B, sens=oracle_sensitivity(sc, uj=uj))
 
 
 def test_c2_full_size_sampled(M, gmaps):

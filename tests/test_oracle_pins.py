@@ -40,6 +40,33 @@ def test_normal_moments():
     assert abs((z ** 4).mean() - 3.0) < 0.25
 
 
+def test_pixel_set_distinct_in_range_and_full_permutation():
+    for (W, H, B) in ((100, 100, 64), (7, 3, 21), (5, 5, 1), (400, 400, 16)):
+        px = oracle.pixel_set(W, H, B, 9, 4)
+        assert px.shape == (B, 2)
+        assert np.all((px[:, 0] >= 0) & (px[:, 0] < W) & (px[:, 1] >= 0) & (px[:, 1] < H))
+        q = px[:, 1] * W + px[:, 0]
+        assert len(set(q.tolist())) == B
+    # B = n: every pixel exactly once
+    px = oracle.pixel_set(7, 3, 21, 1, 2)
+    assert sorted((px[:, 1] * 7 + px[:, 0]).tolist()) == list(range(21))
+
+
+def test_pixel_set_uniform_subsets():
+    """Floyd's algorithm draws every B-subset with equal probability: for
+    n = 5, B = 2 the 10 subsets are equally frequent (chi-square, 9 dof)."""
+    from collections import Counter
+    cnt = Counter()
+    T = 20000
+    for c in range(T):
+        px = oracle.pixel_set(5, 1, 2, 77, c)
+        cnt[tuple(sorted(px[:, 0].tolist()))] += 1
+    assert len(cnt) == 10
+    exp = T / 10
+    chi2 = sum((v - exp) ** 2 / exp for v in cnt.values())
+    assert chi2 < 30.0   # 99.95th percentile of chi-square(9) is ~29.7
+
+
 # ----------------------------------------------------------------- PE -----
 def test_pe_closed_form():
     L = 10
