@@ -17,7 +17,9 @@
  *   launched; problems only the device can see (non-finite inputs, degenerate
  *   weights) are recorded in a per-map status word (mcl_read_status).
  * - The library allocates device memory only in mcl_init_map (weights and a
- *   workspace sized by mcl_map_config) and frees it in mcl_destroy_map.
+ *   workspace sized by mcl_map_config) and frees it in mcl_destroy_map; the
+ *   two proposal-training entry points also allocate (and free before they
+ *   return) their own training scratch.
  * - Every floating-point array is row-major and tightly packed.
  * - A map may be used by one stream at a time (the workspace is shared).
  */
@@ -84,6 +86,13 @@ typedef struct {
     double rho_reject;  /* mask_i = (w_i >= rho_reject / N)                   */
     double s_min;       /* floor of S_i before the logarithm (> 0)            */
     uint64_t seed, counter;
+    int use_proposal;   /* 1: sample with the learned proposal (the project's
+                           extension; see mcl_proposal_train): n_proposal
+                           stratified proposal samples -> n_guided inverse-CDF
+                           samples for the NeRF MLP -> n_fine importance
+                           samples from those; n_coarse is then unused      */
+    int n_proposal;     /* 2..256                                            */
+    int n_guided;       /* 2..256                                            */
 } mcl_opts;
 
 /* Optional per-ray / per-particle outputs of mcl_update (any may be NULL). */
@@ -278,6 +287,61 @@ int mcl_localize(mcl_map* map, int n_queries, float* d_particles, int stride,
                  const mcl_intrinsics* K, const mcl_schedule* sch,
                  const mcl_opts* opts, mcl_iter_record* d_log, int* d_final_n,
                  int use_graph, void* stream);
+
+/* ---- learned proposal sampler (a project extension; the paper has none) --
+ * Network: gamma(x) with 6 frequencies (39 inputs) -> four ReLU layers of 64
+ * units -> raw density s (linear head); density max(s, 0) composited over
+ * n_proposal stratified midpoints as Eq. 1.  Weight blob (15105 floats):
+ * P1 W[64][39] b[64], P2..P4 W[64][64] b[64], head w[64] b[1]. */
+#define MCL_PROPOSAL_N_WEIGHTS 15105
+
+typedef struct {
+    int epochs;         /* passes over the training rays                     */
+    int batch_rays;     /* rays per Adam step                                */
+    int n_bins;         /* proposal samples = target histogram bins (<= 256) */
+    float lr, beta1, beta2, eps;   /* Adam                                   */
+    uint64_t seed;      /* shuffling of the rays                             */
+    float lr_end;       /* learning rate of the last step; the rate decays
+                           geometrically from lr (lr_end <= 0: constant lr)   */
+} mcl_train_cfg;
+
+/* Copy proposal weights in / out (host buffers of MCL_PROPOSAL_N_WEIGHTS). */
+int mcl_proposal_set(mcl_map* map, const float* host_weights, size_t n);
+int mcl_proposal_get(mcl_map* map, float* host_out, size_t n);
+
+/* Targets of the distillation: for n_poses poses x B pixels, render with the
+ * full sampler of `opts` (n_coarse + n_fine, use_proposal ignored) and
+ * re-bin the final weights onto n_bins equal intervals of [near_z, far_z]
+ * (interval floor((z - near)/(far - near) n_bins), clamped), normalised
+ * (uniform when a ray carries no weight).  d_hist: [n_poses*B, n_bins]. */
+int mcl_render_histogram(mcl_map* map, const float* d_poses, int n_poses,
+                         const mcl_intrinsics* K, int level,
+                         const int32_t* d_pixels, int B, const mcl_opts* opts,
+                         int n_bins, float* d_hist, void* stream);
+
+/* Mean cross-entropy -sum_b h_b log(w_b / sum_k w_k + 1e-8) of the proposal
+ * weights of n rays (origins d_o, directions d_d [n,3]; n_bins stratified
+ * midpoints of [near_z, far_z]) against d_hist [n, n_bins] into *d_loss
+ * (device double), and its gradient with respect to the proposal weights
+ * into d_grad [MCL_PROPOSAL_N_WEIGHTS] (FP32).  Synchronous; allocates and
+ * frees its scratch. */
+int mcl_proposal_loss_grad(mcl_map* map, const float* d_o, const float* d_d,
+                           int n, int n_bins, float near_z, float far_z,
+                           const float* d_hist, double* d_loss, float* d_grad,
+                           void* stream);
+
+/* Distil the proposal from the full sampler: targets of n_poses x B rays
+ * (mcl_render_histogram with sampler_opts), then cfg->epochs epochs of Adam
+ * on shuffled batches of the mean cross-entropy, starting from the current
+ * proposal weights (set them first).  d_loss_log (optional, [epochs])
+ * receives the mean loss of every epoch.  Gradients are reduced in a fixed
+ * order, so the same inputs give the same weights.  Synchronous; allocates
+ * and frees its training scratch (targets, one batch of activations). */
+int mcl_proposal_train(mcl_map* map, const float* d_poses, int n_poses,
+                       const int32_t* d_pixels, int B, const mcl_intrinsics* K,
+                       int level, const mcl_opts* sampler_opts,
+                       const mcl_train_cfg* cfg, float* d_loss_log,
+                       void* stream);
 
 /* Phases timed when profiling is on (indices into the array of
  * mcl_profile_read). */

@@ -93,6 +93,14 @@ def lib():
             L.orc_num_threads.restype = C.c_int
             L.orc_pixel_set.argtypes = [C.c_int, C.c_int, C.c_int, C.c_uint64, C.c_uint64,
                                         C.POINTER(C.c_int32)]
+            L.orc_prop_n_weights.restype = C.c_long
+            L.orc_prop_forward.argtypes = [fp, C.c_int, dp, dp]
+            L.orc_histogram.argtypes = [C.c_int, dp, dp, C.c_int, C.c_double, C.c_double, dp]
+            L.orc_prop_loss_grad.argtypes = [fp, C.c_int, dp, dp, C.c_int, C.c_double, C.c_double,
+                                             dp, dp, dp]
+            L.orc_prop_weights.argtypes = [fp, C.c_int, dp, dp, C.c_int, C.c_double, C.c_double, dp]
+            L.orc_render_rays_proposal.argtypes = [fp, ip, fp, C.c_int, dp, dp, C.POINTER(Opts),
+                                                   C.c_int, C.c_int, dp]
             _lib = L
     return _lib
 
@@ -283,6 +291,71 @@ def resample(w, n_out, u0):
     if rc != 0:
         raise ValueError(f"orc_resample returned {rc}")
     return idx
+
+
+# ---------------------------------------------------------------- proposal
+def prop_n_weights() -> int:
+    return int(lib().orc_prop_n_weights())
+
+
+def prop_forward(pblob, x):
+    b, bp = _blob(pblob)
+    x, xp = _d(np.reshape(x, (-1, 3)))
+    out = np.zeros(x.shape[0])
+    lib().orc_prop_forward(bp, x.shape[0], xp, out.ctypes.data_as(C.POINTER(C.c_double)))
+    return out
+
+
+def histogram(z, w, nb, near, far):
+    z, zp = _d(z)
+    w, wp = _d(w)
+    out = np.zeros(nb)
+    lib().orc_histogram(z.shape[0], zp, wp, nb, float(near), float(far),
+                        out.ctypes.data_as(C.POINTER(C.c_double)))
+    return out
+
+
+def prop_loss_grad(pblob, o, d, hist, near=2.0, far=6.0, with_grad=True):
+    b, bp = _blob(pblob)
+    o, op_ = _d(np.reshape(o, (-1, 3)))
+    d, dp_ = _d(np.reshape(d, (-1, 3)))
+    n = o.shape[0]
+    h, hp = _d(np.reshape(hist, (n, -1)))
+    nb = h.shape[1]
+    loss = np.zeros(1)
+    grad = np.zeros(prop_n_weights()) if with_grad else None
+    P = C.POINTER(C.c_double)
+    lib().orc_prop_loss_grad(bp, n, op_, dp_, nb, float(near), float(far), hp,
+                             loss.ctypes.data_as(P), grad.ctypes.data_as(P) if with_grad else None)
+    return float(loss[0]), grad
+
+
+def prop_weights(pblob, o, d, nb, near=2.0, far=6.0):
+    b, bp = _blob(pblob)
+    o, op_ = _d(np.reshape(o, (-1, 3)))
+    d, dp_ = _d(np.reshape(d, (-1, 3)))
+    out = np.zeros((o.shape[0], nb))
+    lib().orc_prop_weights(bp, o.shape[0], op_, dp_, nb, float(near), float(far),
+                           out.ctypes.data_as(C.POINTER(C.c_double)))
+    return out
+
+
+def render_rays_proposal(blob, pblob, o, d, opts: Opts, n_p=64, n_g=32, arch=DEFAULT_ARCH):
+    """Render with the proposal sampler (n_p proposal samples, n_g guided
+    samples, opts.n_fine importance samples from those)."""
+    b, bp = _blob(blob)
+    pb, pbp = _blob(pblob)
+    a, ap = _arch(arch)
+    o, op_ = _d(np.reshape(o, (-1, 3)))
+    d, dp_ = _d(np.reshape(d, (-1, 3)))
+    n = o.shape[0]
+    out = np.zeros((n, 10))
+    rc = lib().orc_render_rays_proposal(bp, ap, pbp, n, op_, dp_, C.byref(opts), n_p, n_g,
+                                        out.ctypes.data_as(C.POINTER(C.c_double)))
+    assert rc == 0, rc
+    return dict(rgb=out[:, :3].copy(), z_trans=out[:, 3].copy(), z_opaque=out[:, 4].copy(),
+                F=out[:, 5].copy(), tie=out[:, 6].copy(), sigma_last=out[:, 7].copy(),
+                T_last=out[:, 8].copy(), step=out[:, 9].copy())
 
 
 def pixel_set(W, H, B, seed, ctr):

@@ -710,6 +710,290 @@ void orc_position_spread(int n, const double* pose, double* out) {
     out[3] = tr / n;
 }
 
+/* ======================================================================== */
+/* Learned proposal sampler (not in the paper; a project extension that     */
+/* replaces the coarse pass).  Network: gamma(x) with 6 frequencies (39     */
+/* inputs) -> 4 ReLU layers of 64 units -> raw density s (linear head);     */
+/* density = max(s, 0), composited over n_b stratified midpoints exactly as  */
+/* Eq. 1 (delta_last = 1e10).  Blob: P1 W[64][39] b[64], P2..P4 W[64][64]    */
+/* b[64], head w[64] b[1] (15105 floats).  Target: the full sampler's final  */
+/* weights re-binned onto the same n_b equal intervals of [near, far] and    */
+/* normalised (uniform when the ray carries no weight).  Loss of a ray:      */
+/*   L = -sum_b h_b log(w_b / sum_k w_k + 1e-8).                             */
+/* ======================================================================== */
+#define PROP_L 6
+#define PROP_IN (3 + 6 * PROP_L)
+#define PROP_W 64
+#define PROP_DEPTH 4
+
+long orc_prop_n_weights(void) {
+    return (long)PROP_W * PROP_IN + PROP_W + (PROP_DEPTH - 1) * ((long)PROP_W * PROP_W + PROP_W) +
+           PROP_W + 1;
+}
+
+/* Forward of one point; a[l][j] pre-activations, h[l][j] = max(a, 0). */
+static double prop_forward(const double* wd, const double* x, double* g,
+                           double a[PROP_DEPTH][PROP_W], double h[PROP_DEPTH][PROP_W]) {
+    orc_pe(x, PROP_L, g);
+    const double* p = wd;
+    const double* in = g;
+    int fin = PROP_IN;
+    for (int l = 0; l < PROP_DEPTH; ++l) {
+        const double* W = p;
+        const double* b = p + (long)PROP_W * fin;
+        for (int o = 0; o < PROP_W; ++o) {
+            double s = b[o];
+            for (int i = 0; i < fin; ++i) s += W[(long)o * fin + i] * in[i];
+            a[l][o] = s;
+            h[l][o] = s > 0.0 ? s : 0.0;
+        }
+        p = b + PROP_W;
+        in = h[l];
+        fin = PROP_W;
+    }
+    double s = p[PROP_W];
+    for (int i = 0; i < PROP_W; ++i) s += p[i] * h[PROP_DEPTH - 1][i];
+    return s;
+}
+
+int orc_prop_forward(const float* blob, int n, const double* x, double* s_out) {
+    long nw = orc_prop_n_weights();
+    double* wd = widen(blob, nw);
+    if (!wd) return -2;
+#pragma omp parallel for schedule(static)
+    for (int i = 0; i < n; ++i) {
+        double g[PROP_IN], a[PROP_DEPTH][PROP_W], h[PROP_DEPTH][PROP_W];
+        s_out[i] = prop_forward(wd, x + 3 * i, g, a, h);
+    }
+    free(wd);
+    return 0;
+}
+
+/* Re-bin weights w of sorted samples z onto nb equal intervals of
+ * [near, far] (interval floor((z - near) / (far - near) nb), clamped) and
+ * normalise; a ray without weight gets the uniform histogram. */
+void orc_histogram(int n, const double* z, const double* w, int nb, double near_z,
+                   double far_z, double* hist) {
+    for (int b = 0; b < nb; ++b) hist[b] = 0.0;
+    for (int k = 0; k < n; ++k) {
+        int b = (int)floor((z[k] - near_z) / (far_z - near_z) * nb);
+        if (b < 0) b = 0;
+        if (b > nb - 1) b = nb - 1;
+        hist[b] += w[k];
+    }
+    double t = 0.0;
+    for (int b = 0; b < nb; ++b) t += hist[b];
+    for (int b = 0; b < nb; ++b) hist[b] = t > 0.0 ? hist[b] / t : 1.0 / nb;
+}
+
+/* Loss of one ray and (if grad != NULL) its gradient added to grad (blob
+ * layout), by the chain rule: with g_k = dL/dw_k and w_k = T_k alpha_k,
+ *   dL/dsigma_j = delta_j (g_j T_j (1 - alpha_j) - sum_{k>j} g_k w_k),
+ * masked by s_j > 0, then back through the ReLU layers. */
+static double prop_ray(const double* wd, const double* o, const double* d, int nb,
+                       double near_z, double far_z, const double* hist, double* grad) {
+    double dn = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    double* z = (double*)malloc(sizeof(double) * nb);
+    double* sr = (double*)malloc(sizeof(double) * nb);
+    double* al = (double*)malloc(sizeof(double) * nb);
+    double* T = (double*)malloc(sizeof(double) * nb);
+    double* w = (double*)malloc(sizeof(double) * nb);
+    double* gw = (double*)malloc(sizeof(double) * nb);
+    double* ds = (double*)malloc(sizeof(double) * nb);
+    double (*A)[PROP_DEPTH][PROP_W] = malloc(sizeof(double) * nb * PROP_DEPTH * PROP_W);
+    double (*Hh)[PROP_DEPTH][PROP_W] = malloc(sizeof(double) * nb * PROP_DEPTH * PROP_W);
+    double (*G)[PROP_IN] = malloc(sizeof(double) * nb * PROP_IN);
+    for (int k = 0; k < nb; ++k) {
+        z[k] = near_z + (far_z - near_z) * (k + 0.5) / nb;
+        double x[3] = {o[0] + z[k] * d[0], o[1] + z[k] * d[1], o[2] + z[k] * d[2]};
+        sr[k] = prop_forward(wd, x, G[k], A[k], Hh[k]);
+    }
+    double trans = 1.0, W = 0.0;
+    for (int k = 0; k < nb; ++k) {
+        double delta = (k < nb - 1) ? (z[k + 1] - z[k]) * dn : 1e10;
+        double sg = sr[k] > 0.0 ? sr[k] : 0.0;
+        al[k] = 1.0 - exp(-sg * delta);
+        T[k] = trans;
+        w[k] = trans * al[k];
+        trans *= (1.0 - al[k]);
+        W += w[k];
+    }
+    double L = 0.0;
+    if (!(W > 0.0)) {
+        /* no density anywhere on the ray: every p_b = 1e-8, no gradient */
+        for (int b = 0; b < nb; ++b) L -= hist[b] * log(1e-8);
+    } else {
+        for (int b = 0; b < nb; ++b) L -= hist[b] * log(w[b] / W + 1e-8);
+    }
+    if (grad && W > 0.0) {
+        /* g_j = -h_j / (p_j W) + sum_b h_b w_b / (p_b W^2) */
+        double c = 0.0;
+        for (int b = 0; b < nb; ++b) c += hist[b] * w[b] / ((w[b] / W + 1e-8) * W * W);
+        for (int j = 0; j < nb; ++j) gw[j] = -hist[j] / ((w[j] / W + 1e-8) * W) + c;
+        double tail = 0.0; /* sum_{k>j} g_k w_k */
+        for (int j = nb - 1; j >= 0; --j) {
+            double delta = (j < nb - 1) ? (z[j + 1] - z[j]) * dn : 1e10;
+            double dsig = delta * (gw[j] * T[j] * (1.0 - al[j]) - tail);
+            ds[j] = sr[j] > 0.0 ? dsig : 0.0;
+            tail += gw[j] * w[j];
+        }
+        /* back through the network, parameters in blob order */
+        long off[PROP_DEPTH + 1];
+        off[0] = 0;
+        for (int l = 0; l < PROP_DEPTH; ++l)
+            off[l + 1] = off[l] + (long)PROP_W * (l == 0 ? PROP_IN : PROP_W) + PROP_W;
+        const double* head = wd + off[PROP_DEPTH];
+        for (int k = 0; k < nb; ++k) {
+            double dh[PROP_W], da[PROP_W];
+            for (int i = 0; i < PROP_W; ++i) {
+                grad[off[PROP_DEPTH] + i] += ds[k] * Hh[k][PROP_DEPTH - 1][i];
+                dh[i] = ds[k] * head[i];
+            }
+            grad[off[PROP_DEPTH] + PROP_W] += ds[k];
+            for (int l = PROP_DEPTH - 1; l >= 0; --l) {
+                int fin = (l == 0) ? PROP_IN : PROP_W;
+                const double* in = (l == 0) ? G[k] : Hh[k][l - 1];
+                const double* Wl = wd + off[l];
+                for (int o2 = 0; o2 < PROP_W; ++o2) da[o2] = A[k][l][o2] > 0.0 ? dh[o2] : 0.0;
+                for (int o2 = 0; o2 < PROP_W; ++o2) {
+                    for (int i = 0; i < fin; ++i) grad[off[l] + (long)o2 * fin + i] += da[o2] * in[i];
+                    grad[off[l] + (long)PROP_W * fin + o2] += da[o2];
+                }
+                if (l > 0)
+                    for (int i = 0; i < PROP_W; ++i) {
+                        double s = 0.0;
+                        for (int o2 = 0; o2 < PROP_W; ++o2) s += Wl[(long)o2 * fin + i] * da[o2];
+                        dh[i] = s;
+                    }
+            }
+        }
+    }
+    free(z); free(sr); free(al); free(T); free(w); free(gw); free(ds);
+    free(A); free(Hh); free(G);
+    return L;
+}
+
+/* Mean loss and mean gradient over n rays (o, d [n,3], hist [n, nb]). */
+int orc_prop_loss_grad(const float* blob, int n, const double* o, const double* d, int nb,
+                       double near_z, double far_z, const double* hist, double* loss,
+                       double* grad) {
+    long nw = orc_prop_n_weights();
+    double* wd = widen(blob, nw);
+    if (!wd) return -2;
+    if (grad) for (long i = 0; i < nw; ++i) grad[i] = 0.0;
+    double L = 0.0;
+    for (int r = 0; r < n; ++r)
+        L += prop_ray(wd, o + 3 * r, d + 3 * r, nb, near_z, far_z, hist + (long)r * nb, grad);
+    *loss = L / n;
+    if (grad) for (long i = 0; i < nw; ++i) grad[i] /= n;
+    free(wd);
+    return 0;
+}
+
+/* Proposal weights of n rays over nb stratified midpoints (for pins). */
+int orc_prop_weights(const float* blob, int n, const double* o, const double* d, int nb,
+                     double near_z, double far_z, double* wout) {
+    long nw = orc_prop_n_weights();
+    double* wd = widen(blob, nw);
+    if (!wd) return -2;
+    for (int r = 0; r < n; ++r) {
+        const double* oo = o + 3 * r;
+        const double* dd = d + 3 * r;
+        double dn = sqrt(dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2]);
+        double* z = (double*)malloc(sizeof(double) * nb);
+        double* sg = (double*)malloc(sizeof(double) * nb);
+        double* col = (double*)calloc(3 * (size_t)nb, sizeof(double));
+        for (int k = 0; k < nb; ++k) {
+            double g[PROP_IN], a[PROP_DEPTH][PROP_W], h[PROP_DEPTH][PROP_W];
+            z[k] = near_z + (far_z - near_z) * (k + 0.5) / nb;
+            double x[3] = {oo[0] + z[k] * dd[0], oo[1] + z[k] * dd[1], oo[2] + z[k] * dd[2]};
+            sg[k] = prop_forward(wd, x, g, a, h);
+        }
+        double C[3];
+        orc_composite(nb, z, sg, col, dn, wout + (long)r * nb, NULL, C);
+        free(z); free(sg); free(col);
+    }
+    free(wd);
+    return 0;
+}
+
+/* Render with the proposal sampler: n_p proposal samples (stratified
+ * midpoints) -> proposal weights -> n_g importance samples (as the basic
+ * model's inverse CDF, with the proposal weights as the coarse weights) ->
+ * main MLP -> composite -> n_f importance samples from those -> main MLP ->
+ * composite of the n_g + n_f samples; Eq. 5 / F as render_ray.  out as
+ * orc_render_rays (rgb, z_trans, z_opaque, F, ...). */
+int orc_render_rays_proposal(const float* blob, const int* arch, const float* pblob, int n,
+                             const double* o, const double* d, const orc_opts* op, int n_p,
+                             int n_g, double* out) {
+    long nw = orc_n_weights(arch);
+    if (nw < 0) return -1;
+    double* wd = widen(blob, nw);
+    if (!wd) return -2;
+    double* pw = (double*)malloc(sizeof(double) * (size_t)n * n_p);
+    int err = orc_prop_weights(pblob, n, o, d, n_p, op->near_z, op->far_z, pw);
+    int nf = op->n_fine;
+#pragma omp parallel for schedule(dynamic, 1) reduction(| : err)
+    for (int r = 0; r < n; ++r) {
+        const double* oo = o + 3 * r;
+        const double* dd = d + 3 * r;
+        double dn = sqrt(dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2]);
+        double dh[3] = {dd[0] / dn, dd[1] / dn, dd[2] / dn};
+        int ntot = n_g + nf;
+        double* zp = (double*)malloc(sizeof(double) * n_p);
+        double* z = (double*)malloc(sizeof(double) * ntot);
+        double* sg = (double*)malloc(sizeof(double) * ntot);
+        double* cl = (double*)malloc(sizeof(double) * 3 * ntot);
+        double* w = (double*)malloc(sizeof(double) * ntot);
+        double* u = (double*)malloc(sizeof(double) * (n_g > nf ? n_g : nf) + 8);
+        int* ord = (int*)malloc(sizeof(int) * ntot);
+        double* zs = (double*)malloc(sizeof(double) * ntot);
+        double* ss = (double*)malloc(sizeof(double) * ntot);
+        double* cs = (double*)malloc(sizeof(double) * 3 * ntot);
+        for (int k = 0; k < n_p; ++k) zp[k] = op->near_z + (op->far_z - op->near_z) * (k + 0.5) / n_p;
+        for (int j = 0; j < n_g; ++j) u[j] = n_g > 1 ? (double)j / (n_g - 1) : 0.0;
+        orc_sample_pdf(n_p, zp, pw + (long)r * n_p, n_g, u, z);
+        for (int k = 0; k < n_g; ++k) {
+            double x[3] = {oo[0] + z[k] * dd[0], oo[1] + z[k] * dd[1], oo[2] + z[k] * dd[2]};
+            err |= mlp_eval(wd, arch, x, dh, sg + k, cl + 3 * k);
+        }
+        if (nf > 0) {
+            double C0[3];
+            orc_composite(n_g, z, sg, cl, dn, w, NULL, C0);
+            for (int j = 0; j < nf; ++j) u[j] = nf > 1 ? (double)j / (nf - 1) : 0.0;
+            orc_sample_pdf(n_g, z, w, nf, u, z + n_g);
+            for (int k = n_g; k < ntot; ++k) {
+                double x[3] = {oo[0] + z[k] * dd[0], oo[1] + z[k] * dd[1], oo[2] + z[k] * dd[2]};
+                err |= mlp_eval(wd, arch, x, dh, sg + k, cl + 3 * k);
+            }
+        }
+        for (int k = 0; k < ntot; ++k) ord[k] = k;
+        for (int k = 1; k < ntot; ++k) {
+            int v = ord[k], m = k - 1;
+            while (m >= 0 && z[ord[m]] > z[v]) { ord[m + 1] = ord[m]; --m; }
+            ord[m + 1] = v;
+        }
+        for (int k = 0; k < ntot; ++k) {
+            zs[k] = z[ord[k]];
+            ss[k] = sg[ord[k]];
+            for (int c = 0; c < 3; ++c) cs[3 * k + c] = cl[3 * ord[k] + c];
+        }
+        double C[3];
+        double* oout = out + 10 * (long)r;
+        double* Tk = (double*)malloc(sizeof(double) * ntot);
+        orc_composite(ntot, zs, ss, cs, dn, w, Tk, C);
+        oout[0] = C[0]; oout[1] = C[1]; oout[2] = C[2];
+        orc_uncertainty(ntot, zs, w, op->alpha, op->tau, oout + 3, oout + 4, oout + 5, oout + 6,
+                        oout + 9);
+        oout[7] = ss[ntot - 1];
+        oout[8] = Tk[ntot - 1];
+        free(Tk); free(zp); free(z); free(sg); free(cl); free(w); free(u); free(ord);
+        free(zs); free(ss); free(cs);
+    }
+    free(pw); free(wd);
+    return err ? -1 : 0;
+}
+
 int orc_num_threads(void) {
 #ifdef _OPENMP
     return omp_get_max_threads();

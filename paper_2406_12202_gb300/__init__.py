@@ -87,7 +87,14 @@ class Opts(C.Structure):
                 ("use_rejection", C.c_int), ("jitter", C.c_int),
                 ("near_z", C.c_float), ("far_z", C.c_float), ("alpha", C.c_float),
                 ("tau", C.c_float), ("rho_reject", C.c_double), ("s_min", C.c_double),
-                ("seed", C.c_uint64), ("counter", C.c_uint64)]
+                ("seed", C.c_uint64), ("counter", C.c_uint64),
+                ("use_proposal", C.c_int), ("n_proposal", C.c_int), ("n_guided", C.c_int)]
+
+
+class TrainCfg(C.Structure):
+    _fields_ = [("epochs", C.c_int), ("batch_rays", C.c_int), ("n_bins", C.c_int),
+                ("lr", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float),
+                ("eps", C.c_float), ("seed", C.c_uint64), ("lr_end", C.c_float)]
 
 
 class Debug(C.Structure):
@@ -131,6 +138,13 @@ def lib():
             L.mcl_resample_noalloc.argtypes = [vp, i32, i32, f64, vp, vp]
             L.mcl_profile_enable.argtypes = [vp, i32]
             L.mcl_profile_read.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_longlong), i32]
+            L.mcl_proposal_set.argtypes = [vp, vp, C.c_size_t]
+            L.mcl_proposal_get.argtypes = [vp, vp, C.c_size_t]
+            L.mcl_render_histogram.argtypes = [vp, vp, i32, C.POINTER(Intrinsics), i32, vp, i32,
+                                               C.POINTER(Opts), i32, vp, vp]
+            L.mcl_proposal_loss_grad.argtypes = [vp, vp, vp, i32, i32, f32, f32, vp, vp, vp, vp]
+            L.mcl_proposal_train.argtypes = [vp, vp, i32, vp, i32, C.POINTER(Intrinsics), i32,
+                                             C.POINTER(Opts), C.POINTER(TrainCfg), vp, vp]
             L.mcl_last_error.restype = C.c_char_p
             L.mcl_last_error.argtypes = []
             _lib = L
@@ -181,11 +195,15 @@ class UpdateOptions:
     s_min: float = 1e-30
     seed: int = 0
     counter: int = 0
+    use_proposal: bool = False   # learned proposal sampler (Map.proposal_train)
+    n_proposal: int = 64
+    n_guided: int = 32
 
     def c(self) -> Opts:
         return Opts(self.n_coarse, self.n_fine, _PREC[self.precision], int(self.use_rejection),
                     int(self.jitter), self.near, self.far, self.alpha, self.tau,
-                    self.rho_reject, self.s_min, self.seed, self.counter)
+                    self.rho_reject, self.s_min, self.seed, self.counter,
+                    int(self.use_proposal), self.n_proposal, self.n_guided)
 
 
 def intrinsics(fx, fy, cx, cy, width, height) -> Intrinsics:
@@ -339,6 +357,62 @@ class Map:
             out.append(rows)
         return out
 
+    # -------------------------------------------------------------- proposal
+    def proposal_set(self, weights: np.ndarray):
+        w = np.ascontiguousarray(weights, dtype=np.float32)
+        _check(lib().mcl_proposal_set(self.handle, w.ctypes.data, w.size))
+
+    def proposal_get(self) -> np.ndarray:
+        w = np.zeros(PROPOSAL_N_WEIGHTS, dtype=np.float32)
+        _check(lib().mcl_proposal_get(self.handle, w.ctypes.data, w.size))
+        return w
+
+    def render_histogram(self, poses, K: Intrinsics, level: int, pixels, opts: UpdateOptions,
+                         n_bins: int):
+        """Distillation targets [n*B, n_bins] (mcl_render_histogram)."""
+        torch = _torch()
+        n, B = poses.shape[0], pixels.shape[0]
+        out = torch.empty(n * B, n_bins, dtype=torch.float32, device=poses.device)
+        o = opts.c()
+        _check(lib().mcl_render_histogram(
+            self.handle, _ptr(poses, torch.float32, (n, 12), "poses"), n, C.byref(K), int(level),
+            _ptr(pixels, torch.int32, (B, 2), "pixels"), B, C.byref(o), int(n_bins),
+            out.data_ptr(), _stream()))
+        return out
+
+    def proposal_loss_grad(self, o, d, hist, near: float = 2.0, far: float = 6.0):
+        """Mean cross-entropy of the proposal against hist and its gradient
+        (mcl_proposal_loss_grad): (loss float, grad [PROPOSAL_N_WEIGHTS] f32)."""
+        torch = _torch()
+        n, nb = hist.shape
+        loss = torch.empty(1, dtype=torch.float64, device=hist.device)
+        grad = torch.empty(PROPOSAL_N_WEIGHTS, dtype=torch.float32, device=hist.device)
+        _check(lib().mcl_proposal_loss_grad(
+            self.handle, _ptr(o, torch.float32, (n, 3), "o"), _ptr(d, torch.float32, (n, 3), "d"),
+            n, nb, float(near), float(far), _ptr(hist, torch.float32, (n, nb), "hist"),
+            loss.data_ptr(), grad.data_ptr(), _stream()))
+        return float(loss.item()), grad
+
+    def proposal_train(self, poses, pixels, K: Intrinsics, level: int, opts: UpdateOptions,
+                       epochs: int = 10, batch_rays: int = 4096, n_bins: int = 64,
+                       lr: float = 1e-3, beta1: float = 0.9, beta2: float = 0.999,
+                       eps: float = 1e-7, seed: int = 0, lr_end: float = 0.0):
+        """Distil the proposal from the full sampler of opts
+        (mcl_proposal_train); the rate decays geometrically from lr to
+        lr_end (constant if lr_end <= 0).  Returns the mean loss of every
+        epoch."""
+        torch = _torch()
+        n, B = poses.shape[0], pixels.shape[0]
+        log = torch.zeros(epochs, dtype=torch.float32, device=poses.device)
+        cfg = TrainCfg(int(epochs), int(batch_rays), int(n_bins), lr, beta1, beta2, eps, int(seed),
+                       lr_end)
+        o = opts.c()
+        _check(lib().mcl_proposal_train(
+            self.handle, _ptr(poses, torch.float32, (n, 12), "poses"), n,
+            _ptr(pixels, torch.int32, (B, 2), "pixels"), B, C.byref(K), int(level), C.byref(o),
+            C.byref(cfg), log.data_ptr(), _stream()))
+        return log.cpu().numpy()
+
     def read_status(self):
         n = C.c_int(0)
         rc = lib().mcl_read_status(self.handle, C.byref(n), _stream())
@@ -407,7 +481,13 @@ def position_spread(poses, out=None):
 EXPORTED = ("mcl_init_map", "mcl_destroy_map", "mcl_update", "mcl_render", "mcl_resample",
             "mcl_predict", "mcl_downscale", "mcl_position_spread", "mcl_read_status",
             "mcl_profile_enable", "mcl_profile_read", "mcl_map_supports", "mcl_last_error",
-            "mcl_resample_noalloc", "mcl_query", "mcl_draw_pixels", "mcl_localize")
+            "mcl_resample_noalloc", "mcl_query", "mcl_draw_pixels", "mcl_localize",
+            "mcl_proposal_set", "mcl_proposal_get", "mcl_render_histogram",
+            "mcl_proposal_loss_grad", "mcl_proposal_train")
+
+# Weights of the learned proposal (gamma(x) with 6 frequencies -> 4 x 64 ReLU
+# -> density): 64*39+64 + 3*(64*64+64) + 64+1.
+PROPOSAL_N_WEIGHTS = 15105
 
 # Algorithmic multiply-accumulates per sample of the network the tensor-core
 # form evaluates (the linear feature layer folded into the RGB hidden layer):

@@ -99,7 +99,7 @@ static void free_map(mcl_map* m) {
     void* ptrs[] = {m->w32, m->rays, m->gd, m->zc, m->zf, m->out_c, m->out_f, m->e_ray,
                     m->logw64, m->cdf, m->status, m->act0, m->act1, m->gxbuf,
                     m->loop.plan, m->loop.qs, m->loop.n0, (void*)m->loop.imgs, m->loop.pix,
-                    m->loop.P_next, m->loop.w, m->loop.mask, m->loop.idx};
+                    m->loop.P_next, m->loop.w, m->loop.mask, m->loop.idx, m->prop_w};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete m;
@@ -221,6 +221,10 @@ extern "C" int mcl_init_map(const float* host_weights, size_t n_floats, const mc
         free_map(m);
         return rc;
     }
+    if ((rc = proposal_alloc(m))) {
+        free_map(m);
+        return rc;
+    }
     if ((rc = mlp_tc_prepare(m, host_weights))) {
         free_map(m);
         return rc;
@@ -251,17 +255,46 @@ static int check_opts(const mcl_opts* o) {
     return MCL_OK;
 }
 
-// Common front half of mcl_update and mcl_render: rays, both sample passes.
+// Sample counts against the workspace (both samplers).
+static int check_samples(const mcl_map* m, const mcl_opts* o) {
+    if (o->use_proposal) {
+        if (!m->has_proposal) return fail(MCL_ERR_ARG, "use_proposal: no proposal weights set or trained");
+        if (o->n_proposal < 2 || o->n_proposal > kMaxCoarse || o->n_guided < 2 ||
+            o->n_guided > kMaxCoarse)
+            return fail(MCL_ERR_ARG, "n_proposal %d / n_guided %d out of range", o->n_proposal,
+                        o->n_guided);
+        if (o->n_proposal > m->cfg.max_samples || o->n_guided + o->n_fine > m->cfg.max_samples)
+            return fail(MCL_ERR_ARG, "proposal sample counts exceed max_samples %d", m->cfg.max_samples);
+    } else if (o->n_coarse + o->n_fine > m->cfg.max_samples) {
+        return fail(MCL_ERR_ARG, "n_coarse + n_fine > max_samples %d", m->cfg.max_samples);
+    }
+    return MCL_OK;
+}
+
+// The two sample sets the final composite merges (after render_passes).
+struct Passes {
+    const float* za;
+    const float4* oa;
+    int na;
+    const float* zb;
+    const float4* ob;
+    int nb;
+    int factor;
+};
+
+// Common front half of mcl_update, mcl_render and the training targets:
+// rays, then either coarse + importance samples (the basic model's
+// hierarchical sampler) or proposal + guided + importance samples.
 static int render_passes(mcl_map* m, const float* d_poses, int N, const mcl_intrinsics* K,
                          int level, const int32_t* d_pixels, int B, const mcl_opts* o,
-                         int* factor_out, cudaStream_t s) {
+                         Passes* out, cudaStream_t s) {
     int rc;
     if ((rc = check_opts(o))) return rc;
     if (!d_poses || !K || !d_pixels) return fail(MCL_ERR_ARG, "NULL pose / intrinsics / pixel set");
     if (N < 1 || B < 1 || (long)N * B > m->cfg.max_rays)
         return fail(MCL_ERR_ARG, "N*B = %ld outside [1, max_rays=%d]", (long)N * B, m->cfg.max_rays);
-    if (o->n_coarse + o->n_fine > m->cfg.max_samples)
-        return fail(MCL_ERR_ARG, "n_coarse + n_fine > max_samples %d", m->cfg.max_samples);
+    if ((rc = check_samples(m, o))) return rc;
+    const bool prop = o->use_proposal != 0;
     if (level < 0 || level > 2) return fail(MCL_ERR_ARG, "level %d not in 0..2", level);
     const int f = 4 >> level;
     if (K->width < 1 || K->height < 1 || K->width % f || K->height % f)
@@ -270,37 +303,85 @@ static int render_passes(mcl_map* m, const float* d_poses, int N, const mcl_intr
     const int nr = N * B;
     if (o->precision != MCL_PREC_FP32 && !(o->precision == MCL_PREC_BF16 && mlp_tc_available(m)))
         return fail(MCL_ERR_UNSUPPORTED, "precision %d is not available on this device", o->precision);
+    mcl_opts ro = *o;
+    if (prop) {   // stratified midpoints of the proposal (the samples it was trained on)
+        ro.n_coarse = o->n_proposal;
+        ro.jitter = 0;
+    }
     {
         PhaseScope ph(m, MCL_PHASE_RAYGEN, s);
         if ((rc = cuda_check(launch_raygen(d_poses, N, d_pixels, B, K->fx / f, K->fy / f,
-                                           K->cx / f, K->cy / f, *o, m->rays, m->gd, m->zc, s),
+                                           K->cx / f, K->cy / f, ro, m->rays, m->gd, m->zc, s),
                              "raygen")))
             return rc;
         if (o->precision != MCL_PREC_FP32 &&
             (rc = cuda_check(mlp_tc_ray_bias(m, m->gd, nr, nullptr, s), "per-ray bias")))
             return rc;
     }
-    auto mlp = [&](const float* z, int S, float4* out) -> cudaError_t {
-        if (o->precision == MCL_PREC_FP32) return mlp_fp32(m, m->rays, m->gd, z, S, nr, out, s);
-        return mlp_tc(m, o->precision, m->rays, m->gd, z, S, nr, nullptr, out, s);
+    auto mlp = [&](const float* z, int S, float4* dst) -> cudaError_t {
+        if (o->precision == MCL_PREC_FP32) return mlp_fp32(m, m->rays, m->gd, z, S, nr, dst, s);
+        return mlp_tc(m, o->precision, m->rays, m->gd, z, S, nr, nullptr, dst, s);
     };
+    out->factor = f;
+    if (!prop) {
+        {
+            PhaseScope ph(m, MCL_PHASE_MLP_COARSE, s);
+            if ((rc = cuda_check(mlp(m->zc, o->n_coarse, m->out_c), "mlp (coarse)"))) return rc;
+        }
+        if (o->n_fine > 0) {
+            {
+                PhaseScope ph(m, MCL_PHASE_SAMPLE, s);
+                if ((rc = cuda_check(launch_coarse_to_fine(m->rays, nr, nullptr, m->zc, o->n_coarse,
+                                                           m->out_c, o->n_fine, m->zf, s),
+                                     "importance sampling")))
+                    return rc;
+            }
+            PhaseScope ph(m, MCL_PHASE_MLP_FINE, s);
+            if ((rc = cuda_check(mlp(m->zf, o->n_fine, m->out_f), "mlp (fine)"))) return rc;
+        }
+        *out = Passes{m->zc, m->out_c, o->n_coarse, m->zf, m->out_f, o->n_fine, f};
+        return MCL_OK;
+    }
+    // proposal: densities at the stratified samples (into out_f), guided
+    // samples from their weights (into zf), NeRF MLP there (into out_c),
+    // importance samples from those (into zc), NeRF MLP (into out_f)
+    {
+        PhaseScope ph(m, MCL_PHASE_SAMPLE, s);
+        if ((rc = cuda_check(launch_prop_infer(m, m->rays, m->zc, o->n_proposal, nr, nullptr,
+                                               m->out_f, s),
+                             "proposal")))
+            return rc;
+        if ((rc = cuda_check(launch_coarse_to_fine(m->rays, nr, nullptr, m->zc, o->n_proposal,
+                                                   m->out_f, o->n_guided, m->zf, s),
+                             "proposal sampling")))
+            return rc;
+    }
     {
         PhaseScope ph(m, MCL_PHASE_MLP_COARSE, s);
-        if ((rc = cuda_check(mlp(m->zc, o->n_coarse, m->out_c), "mlp (coarse)"))) return rc;
+        if ((rc = cuda_check(mlp(m->zf, o->n_guided, m->out_c), "mlp (guided)"))) return rc;
     }
     if (o->n_fine > 0) {
         {
             PhaseScope ph(m, MCL_PHASE_SAMPLE, s);
-            if ((rc = cuda_check(launch_coarse_to_fine(m->rays, nr, nullptr, m->zc, o->n_coarse, m->out_c,
-                                                       o->n_fine, m->zf, s),
+            if ((rc = cuda_check(launch_coarse_to_fine(m->rays, nr, nullptr, m->zf, o->n_guided,
+                                                       m->out_c, o->n_fine, m->zc, s),
                                  "importance sampling")))
                 return rc;
         }
         PhaseScope ph(m, MCL_PHASE_MLP_FINE, s);
-        if ((rc = cuda_check(mlp(m->zf, o->n_fine, m->out_f), "mlp (fine)"))) return rc;
+        if ((rc = cuda_check(mlp(m->zc, o->n_fine, m->out_f), "mlp (fine)"))) return rc;
     }
-    *factor_out = f;
+    *out = Passes{m->zf, m->out_c, o->n_guided, m->zc, m->out_f, o->n_fine, f};
     return MCL_OK;
+}
+
+// Full-sampler render used for the distillation targets (proposal off).
+static int render_full(mcl_map* m, const float* d_poses, int N, const mcl_intrinsics* K, int level,
+                       const int32_t* d_pixels, int B, const mcl_opts* o, cudaStream_t s) {
+    mcl_opts full = *o;
+    full.use_proposal = 0;
+    Passes ps;
+    return render_passes(m, d_poses, N, K, level, d_pixels, B, &full, &ps, s);
 }
 
 extern "C" int mcl_update(mcl_map* m, const float* d_particles, int N, const float* d_image,
@@ -312,15 +393,16 @@ extern "C" int mcl_update(mcl_map* m, const float* d_particles, int N, const flo
     if (!d_image || !d_logw || !d_w || !d_mask) return fail(MCL_ERR_ARG, "mcl_update: NULL output/image");
     if (N > m->cfg.max_particles) return fail(MCL_ERR_ARG, "N %d > max_particles %d", N, m->cfg.max_particles);
     cudaStream_t s = (cudaStream_t)stream;
-    int f = 1, rc;
-    if ((rc = render_passes(m, d_particles, N, K, level, d_pixels, B, o, &f, s))) return rc;
+    int rc;
+    Passes ps;
+    if ((rc = render_passes(m, d_particles, N, K, level, d_pixels, B, o, &ps, s))) return rc;
     const int nr = N * B;
     {
         PhaseScope ph(m, MCL_PHASE_COMPOSITE, s);
-        if ((rc = cuda_check(launch_final_composite(m->rays, nr, m->zc, m->out_c, o->n_coarse,
-                                                    m->zf, m->out_f, o->n_fine, d_image, K->width,
-                                                    K->height, f, d_pixels, B, *o, m->e_ray, dbg,
-                                                    nullptr, nullptr, s),
+        if ((rc = cuda_check(launch_final_composite(m->rays, nr, ps.za, ps.oa, ps.na, ps.zb, ps.ob,
+                                                    ps.nb, d_image, K->width, K->height, ps.factor,
+                                                    d_pixels, B, *o, m->e_ray, dbg, nullptr,
+                                                    nullptr, s),
                              "composite")))
             return rc;
     }
@@ -355,13 +437,13 @@ extern "C" int mcl_render(mcl_map* m, const float* d_poses, int n_poses, const m
     g_err[0] = 0;
     if (!m || !d_rgb) return fail(MCL_ERR_ARG, "mcl_render: NULL map / output");
     cudaStream_t s = (cudaStream_t)stream;
-    int f = 1, rc;
-    if ((rc = render_passes(m, d_poses, n_poses, K, level, d_pixels, B, o, &f, s))) return rc;
+    int rc;
+    Passes ps;
+    if ((rc = render_passes(m, d_poses, n_poses, K, level, d_pixels, B, o, &ps, s))) return rc;
     PhaseScope ph(m, MCL_PHASE_COMPOSITE, s);
-    return cuda_check(launch_final_composite(m->rays, n_poses * B, m->zc, m->out_c, o->n_coarse,
-                                             m->zf, m->out_f, o->n_fine, nullptr, K->width,
-                                             K->height, f, d_pixels, B, *o, nullptr, nullptr,
-                                             d_rgb, d_F, s),
+    return cuda_check(launch_final_composite(m->rays, n_poses * B, ps.za, ps.oa, ps.na, ps.zb,
+                                             ps.ob, ps.nb, nullptr, K->width, K->height, ps.factor,
+                                             d_pixels, B, *o, nullptr, nullptr, d_rgb, d_F, s),
                       "composite");
 }
 
@@ -512,8 +594,7 @@ extern "C" int mcl_localize(mcl_map* m, int nq, float* d_particles, int stride, 
     if (max_rays_run > m->cfg.max_rays)
         return fail(MCL_ERR_ARG, "mcl_localize: n_queries * stride * max B = %ld > max_rays %d",
                     max_rays_run, m->cfg.max_rays);
-    if (o->n_coarse + o->n_fine > m->cfg.max_samples)
-        return fail(MCL_ERR_ARG, "mcl_localize: n_coarse + n_fine > max_samples");
+    if ((rc = check_samples(m, o))) return rc;
     cudaStream_t caller = (cudaStream_t)stream;
     // graph mode captures on the map's own stream, ordered after the caller's
     // work and before the caller's later work by two events
@@ -566,4 +647,76 @@ extern "C" int mcl_localize(mcl_map* m, int nq, float* d_particles, int stride, 
     if ((rc = cuda_check(cudaGraphLaunch(m->loop.exec, s), "launch graph"))) return rc;
     if ((rc = cuda_check(cudaEventRecord(m->loop.ev_out, s), "event record"))) return rc;
     return cuda_check(cudaStreamWaitEvent(caller, m->loop.ev_out, 0), "stream wait");
+}
+
+extern "C" int mcl_proposal_set(mcl_map* m, const float* host, size_t n) {
+    g_err[0] = 0;
+    if (!m || !host || n != MCL_PROPOSAL_N_WEIGHTS)
+        return fail(MCL_ERR_ARG, "mcl_proposal_set: need %d weights", MCL_PROPOSAL_N_WEIGHTS);
+    for (size_t i = 0; i < n; ++i)
+        if (!std::isfinite(host[i])) return fail(MCL_ERR_ARG, "mcl_proposal_set: weight %zu not finite", i);
+    int rc;
+    if ((rc = cuda_check(cudaMemcpy(m->prop_w, host, sizeof(float) * n, cudaMemcpyHostToDevice),
+                         "upload proposal")))
+        return rc;
+    // fresh optimiser state for the new weights
+    if ((rc = cuda_check(cudaMemset(m->prop_m, 0, sizeof(float) * 2 * n), "clear moments"))) return rc;
+    m->prop_step = 0;
+    m->has_proposal = true;
+    return MCL_OK;
+}
+
+extern "C" int mcl_proposal_get(mcl_map* m, float* host, size_t n) {
+    g_err[0] = 0;
+    if (!m || !host || n != MCL_PROPOSAL_N_WEIGHTS)
+        return fail(MCL_ERR_ARG, "mcl_proposal_get: need %d weights", MCL_PROPOSAL_N_WEIGHTS);
+    return cuda_check(cudaMemcpy(host, m->prop_w, sizeof(float) * n, cudaMemcpyDeviceToHost),
+                      "download proposal");
+}
+
+extern "C" int mcl_render_histogram(mcl_map* m, const float* d_poses, int n_poses,
+                                    const mcl_intrinsics* K, int level, const int32_t* d_pixels,
+                                    int B, const mcl_opts* o, int n_bins, float* d_hist,
+                                    void* stream) {
+    g_err[0] = 0;
+    if (!m || !d_hist || !o) return fail(MCL_ERR_ARG, "mcl_render_histogram: NULL argument");
+    if (n_bins < 2 || n_bins > kMaxCoarse) return fail(MCL_ERR_ARG, "n_bins %d out of range", n_bins);
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc;
+    mcl_opts full = *o;
+    full.use_proposal = 0;
+    Passes ps;
+    if ((rc = render_passes(m, d_poses, n_poses, K, level, d_pixels, B, &full, &ps, s))) return rc;
+    return cuda_check(launch_histogram(m->rays, n_poses * B, ps.za, ps.oa, ps.na, ps.zb, ps.ob,
+                                       ps.nb, n_bins, o->near_z, o->far_z, d_hist, s),
+                      "histogram");
+}
+
+extern "C" int mcl_proposal_loss_grad(mcl_map* m, const float* d_o, const float* d_d, int n,
+                                      int n_bins, float near_z, float far_z, const float* d_hist,
+                                      double* d_loss, float* d_grad, void* stream) {
+    g_err[0] = 0;
+    if (!m || !d_o || !d_d || !d_hist || !d_loss || !d_grad || n < 1)
+        return fail(MCL_ERR_ARG, "mcl_proposal_loss_grad: bad argument");
+    if (n_bins < 2 || n_bins > kMaxCoarse || !(near_z < far_z))
+        return fail(MCL_ERR_ARG, "mcl_proposal_loss_grad: bad bins / range");
+    return proposal_loss_grad(m, d_o, d_d, n, n_bins, near_z, far_z, d_hist, d_loss, d_grad,
+                              (cudaStream_t)stream);
+}
+
+extern "C" int mcl_proposal_train(mcl_map* m, const float* d_poses, int n_poses,
+                                  const int32_t* d_pixels, int B, const mcl_intrinsics* K,
+                                  int level, const mcl_opts* o, const mcl_train_cfg* cfg,
+                                  float* d_loss_log, void* stream) {
+    g_err[0] = 0;
+    if (!m || !d_poses || !d_pixels || !K || !o || !cfg || n_poses < 1 || B < 1)
+        return fail(MCL_ERR_ARG, "mcl_proposal_train: bad argument");
+    if (cfg->epochs < 1 || cfg->batch_rays < 1 || cfg->n_bins < 2 || cfg->n_bins > kMaxCoarse ||
+        !(cfg->lr > 0.f) || !(cfg->beta1 >= 0.f && cfg->beta1 < 1.f) ||
+        !(cfg->beta2 >= 0.f && cfg->beta2 < 1.f) || !(cfg->eps > 0.f))
+        return fail(MCL_ERR_ARG, "mcl_proposal_train: bad training configuration");
+    if (B > m->cfg.max_rays) return fail(MCL_ERR_ARG, "mcl_proposal_train: B > max_rays");
+    if (!m->has_proposal) return fail(MCL_ERR_ARG, "mcl_proposal_train: set initial proposal weights first");
+    return proposal_train(m, d_poses, n_poses, d_pixels, B, *K, level, *o, *cfg, d_loss_log,
+                          (cudaStream_t)stream, render_full);
 }

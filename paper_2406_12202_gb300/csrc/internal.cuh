@@ -116,6 +116,13 @@ struct mcl_map {
     std::vector<cudaEvent_t> pool;
     double phase_ms[MCL_N_PHASES] = {0};
     mcl::LoopWork loop;
+    // learned proposal sampler: weights, Adam moments, gradient
+    float* prop_w = nullptr;
+    float* prop_m = nullptr;
+    float* prop_v = nullptr;
+    float* prop_g = nullptr;
+    int prop_step = 0;
+    bool has_proposal = false;
 };
 
 namespace mcl {
@@ -167,6 +174,22 @@ cudaError_t launch_predict(const float* in, int n_in, const int32_t* idx, int n_
                            cudaStream_t s);
 cudaError_t launch_downscale(const float* img, int W, int H, int f, float* out, cudaStream_t s);
 cudaError_t launch_position_spread(const float* poses, int N, double* out, cudaStream_t s);
+
+// proposal.cu
+int proposal_alloc(mcl_map* m);
+cudaError_t launch_prop_infer(mcl_map* m, const Ray* rays, const float* z, int n_p, int n_rays,
+                              const int* n_rays_dev, float4* out, cudaStream_t s);
+cudaError_t launch_histogram(const Ray* rays, int n_rays, const float* zc, const float4* oc, int nc,
+                             const float* zf, const float4* of, int nf, int nb, float near_z,
+                             float far_z, float* hist, cudaStream_t s);
+int proposal_loss_grad(mcl_map* m, const float* O, const float* D, int n, int nb, float near_z,
+                       float far_z, const float* hist, double* d_loss, float* d_grad,
+                       cudaStream_t s);
+int proposal_train(mcl_map* m, const float* d_poses, int n_poses, const int32_t* d_pixels, int B,
+                   const mcl_intrinsics& K, int level, const mcl_opts& o, const mcl_train_cfg& cfg,
+                   float* d_loss_log, cudaStream_t s,
+                   int (*render_chunk)(mcl_map*, const float*, int, const mcl_intrinsics*, int,
+                                       const int32_t*, int, const mcl_opts*, cudaStream_t));
 
 // loop.cu
 cudaError_t launch_draw_pixels(int W, int H, int B, uint64_t seed, uint64_t ctr, int32_t* out,

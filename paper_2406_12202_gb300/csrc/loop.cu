@@ -245,7 +245,14 @@ int enqueue_localize(mcl_map* m, int nq, float* P_user, int stride, const mcl_in
     LoopWork& L = m->loop;
     int rc;
     const int max_rays_run = L.max_rays_run;
-    const int nc = o.n_coarse, nf = o.n_fine;
+    const bool prop = o.use_proposal != 0;
+    // sample sets: without the proposal, coarse (zc, out_c, nc) + fine (zf,
+    // out_f, nf); with it, stratified proposal samples (zc, np) -> guided
+    // (zf, out_c, ng) -> fine (zc, out_f, nf)
+    const int np = prop ? o.n_proposal : o.n_coarse;
+    const int nc = prop ? o.n_guided : o.n_coarse, nf = o.n_fine;
+    float* const za = prop ? m->zf : m->zc;
+    float* const zb = prop ? m->zc : m->zf;
     const int tb = 128;
     float* Pc = P_user;
     float* Pn = L.P_next;
@@ -256,28 +263,37 @@ int enqueue_localize(mcl_map* m, int nq, float* P_user, int stride, const mcl_in
         k_plan<<<1, 32, 0, s>>>(L.plan, L.qs, nq, sch, nc, nf);
         k_pixels<<<1, 64, 0, s>>>(L.plan, nq, K.width, K.height, o.seed, t, L.pix);
         k_raygen_b<<<(max_rays_run + tb - 1) / tb, tb, 0, s>>>(
-            L.plan, nq, Pc, stride, L.pix, K.fx, K.fy, K.cx, K.cy, nc, o.near_z, o.far_z,
-            o.jitter, o.seed, t, max_rays_run, m->rays, m->gd, m->zc);
+            L.plan, nq, Pc, stride, L.pix, K.fx, K.fy, K.cx, K.cy, np, o.near_z, o.far_z,
+            prop ? 0 : o.jitter, o.seed, t, max_rays_run, m->rays, m->gd, m->zc);
         if ((rc = cuda_check(mlp_tc_ray_bias(m, m->gd, max_rays_run, &L.plan->total_rays, s),
                              "loop ray bias")))
             return rc;
-        if ((rc = cuda_check(mlp_tc(m, o.precision, m->rays, m->gd, m->zc, nc, max_rays_run,
+        if (prop) {
+            if ((rc = cuda_check(launch_prop_infer(m, m->rays, m->zc, np, max_rays_run,
+                                                   &L.plan->total_rays, m->out_f, s),
+                                 "loop proposal")) ||
+                (rc = cuda_check(launch_coarse_to_fine(m->rays, max_rays_run, &L.plan->total_rays,
+                                                       m->zc, np, m->out_f, nc, m->zf, s),
+                                 "loop proposal sampling")))
+                return rc;
+        }
+        if ((rc = cuda_check(mlp_tc(m, o.precision, m->rays, m->gd, za, nc, max_rays_run,
                                     &L.plan->rows_c, m->out_c, s),
                              "loop mlp (coarse)")))
             return rc;
         if (nf > 0) {
             if ((rc = cuda_check(launch_coarse_to_fine(m->rays, max_rays_run, &L.plan->total_rays,
-                                                       m->zc, nc, m->out_c, nf, m->zf, s),
+                                                       za, nc, m->out_c, nf, zb, s),
                                  "loop importance sampling")))
                 return rc;
-            if ((rc = cuda_check(mlp_tc(m, o.precision, m->rays, m->gd, m->zf, nf, max_rays_run,
+            if ((rc = cuda_check(mlp_tc(m, o.precision, m->rays, m->gd, zb, nf, max_rays_run,
                                         &L.plan->rows_f, m->out_f, s),
                                  "loop mlp (fine)")))
                 return rc;
         }
         note_launch(5);
         k_final_b<<<(max_rays_run + tb - 1) / tb, tb, 0, s>>>(
-            L.plan, nq, L.imgs, K.width, L.pix, m->rays, m->zc, m->out_c, nc, m->zf, m->out_f, nf,
+            L.plan, nq, L.imgs, K.width, L.pix, m->rays, za, m->out_c, nc, zb, m->out_f, nf,
             o.alpha, o.tau, o.use_rejection, max_rays_run, m->e_ray);
         k_weights_b<<<nq, kLoopThreads, 0, s>>>(L.plan, L.qs, Pc, stride, m->e_ray, o.s_min,
                                                  o.rho_reject, m->logw64, L.w, L.mask, d_log,

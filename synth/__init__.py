@@ -122,6 +122,116 @@ def blob_from_layers(layers: dict, arch: Arch = Arch()) -> np.ndarray:
     return np.concatenate(parts).astype(np.float32)
 
 
+def room_map_weights(seed: int = 0, half: float = 3.0, eps: float = 0.015625,
+                     density: float = 64.0, n_tex_freq: int = 4,
+                     arch: Arch = Arch()) -> np.ndarray:
+    """Hand-set map of the same architecture with a closed form: a textured
+    cube room.  With m(x) = max(|x|, |y|, |z|),
+        sigma(x) = density * clamp((m(x) - half) / eps, 0, 1)
+    (free space inside the room, solid walls beyond it) and, everywhere,
+        rgb(x) = sigmoid(sum_f a_f f(x)),
+    f running over sin / cos(2^k x_c) for k < n_tex_freq and each axis c,
+    with coefficients a_f ~ N(0, 0.45^2) from the seed.  Built only from the
+    ReLU units the architecture has (|v| = relu(v) + relu(-v), max(a, b) =
+    a + relu(b - a), clamp = relu(t) - relu(t - 1)); the view direction has
+    zero weight.  Returns (blob FP32, coefficient matrix a [3, n_features]).
+    Camera positions in [-1, 1]^3 with near 2 / far 6 see the walls; the
+    texture makes position and yaw identifiable, so a filter on this map has
+    a unique answer."""
+    Wd, gx, gd, Wr = arch.trunk_width, arch.gx, arch.gd, arch.rgb_width
+    rng = np.random.Generator(np.random.PCG64(seed + 179424673))
+    feats = [(k, c, kind) for k in range(n_tex_freq) for c in range(3) for kind in (0, 1)]
+    nf = len(feats)
+    a = rng.normal(0.0, 0.45, size=(3, nf))
+    T0 = 8                        # first texture unit (pairs relu(f), relu(-f))
+    assert T0 + 2 * nf <= Wd
+    tex = np.arange(T0, T0 + 2 * nf)
+
+    def ident(fi):
+        W = np.zeros((Wd, fi))
+        W[tex, tex] = 1.0
+        return W
+
+    L = {}
+    W1 = np.zeros((Wd, gx))
+    for c in range(3):
+        W1[2 * c, c] = 1.0
+        W1[2 * c + 1, c] = -1.0
+    for i, (k, c, kind) in enumerate(feats):
+        col = 3 + 6 * k + c + 3 * kind          # sin(2^k x_c) or cos(2^k x_c)
+        W1[T0 + 2 * i, col] = 1.0
+        W1[T0 + 2 * i + 1, col] = -1.0
+    L["trunk1"] = (W1, np.zeros(Wd))
+    W2 = ident(Wd)                              # |x|, |y|, |z|
+    for c in range(3):
+        W2[c, 2 * c] = W2[c, 2 * c + 1] = 1.0
+    L["trunk2"] = (W2, np.zeros(Wd))
+    W3 = ident(Wd)                              # |x|, relu(|y| - |x|), |z|
+    W3[0, 0] = 1.0
+    W3[1, 1], W3[1, 0] = 1.0, -1.0
+    W3[2, 2] = 1.0
+    L["trunk3"] = (W3, np.zeros(Wd))
+    W4 = ident(Wd)                              # max(|x|,|y|), relu(|z| - max(|x|,|y|))
+    W4[0, 0] = W4[0, 1] = 1.0
+    W4[1, 2], W4[1, 0], W4[1, 1] = 1.0, -1.0, -1.0
+    L["trunk4"] = (W4, np.zeros(Wd))
+    W5 = ident(Wd)                              # relu(t), relu(t - 1), t = (m - half) / eps
+    b5 = np.zeros(Wd)
+    W5[0, 0] = W5[0, 1] = 1.0 / eps
+    W5[1, 0] = W5[1, 1] = 1.0 / eps
+    b5[0] = -half / eps
+    b5[1] = -half / eps - 1.0
+    L["trunk5"] = (W5, b5)
+    W6 = np.zeros((Wd, Wd + gx))                # clamp(t, 0, 1); gamma(x) part unused
+    W6[tex, tex] = 1.0
+    W6[0, 0], W6[0, 1] = 1.0, -1.0
+    L["trunk6"] = (W6, np.zeros(Wd))
+    for l in range(7, arch.trunk_depth + 1):
+        W = ident(Wd)
+        W[0, 0] = 1.0
+        L[f"trunk{l}"] = (W, np.zeros(Wd))
+    Ws = np.zeros((1, Wd))
+    Ws[0, 0] = density
+    L["sigma"] = (Ws, np.zeros(1))
+    L["feature"] = (np.eye(Wd), np.zeros(Wd))
+    beta = np.abs(a).sum(1) + 1.0               # keeps the hidden units positive
+    Wh = np.zeros((Wr, Wd + gd))
+    for c in range(3):
+        for i in range(nf):
+            Wh[c, T0 + 2 * i] = a[c, i]
+            Wh[c, T0 + 2 * i + 1] = -a[c, i]
+    bh = np.zeros(Wr)
+    bh[:3] = beta
+    L["rgb_hidden"] = (Wh, bh)
+    Wo = np.zeros((3, Wr))
+    Wo[[0, 1, 2], [0, 1, 2]] = 1.0
+    L["rgb_out"] = (Wo, -beta)
+    return blob_from_layers(L, arch), a
+
+
+# --------------------------------------------------------------------------
+# Learned proposal sampler: gamma(x) with 6 frequencies (39 inputs), four ReLU
+# layers of 64 units, a linear density head.  Blob: P1 W[64][39] b[64],
+# P2..P4 W[64][64] b[64], head w[64] b[1].
+# --------------------------------------------------------------------------
+PROPOSAL_SHAPES = [("p1", 39, 64), ("p2", 64, 64), ("p3", 64, 64), ("p4", 64, 64), ("head", 64, 1)]
+
+
+def proposal_n_weights() -> int:
+    return sum(fi * fo + fo for _, fi, fo in PROPOSAL_SHAPES)
+
+
+def proposal_init_weights(seed: int = 0, head_bias: float = 1.0) -> np.ndarray:
+    """He-normal proposal weights (FP32 blob), zero hidden biases and a
+    positive density-head bias so that training starts with density > 0."""
+    rng = np.random.Generator(np.random.PCG64(seed + 1299709))
+    parts = []
+    for name, fi, fo in PROPOSAL_SHAPES:
+        parts.append(rng.normal(0.0, math.sqrt(2.0 / fi), size=fo * fi))
+        parts.append(np.full(fo, head_bias) if name == "head" else np.zeros(fo))
+    return np.concatenate(parts).astype(np.float32)
+
+
 # --------------------------------------------------------------------------
 # Poses: particle = T(x, y, z) * R_y(yaw), stored as a row-major 3x4 [R | t].
 # --------------------------------------------------------------------------

@@ -154,6 +154,42 @@ def test_mlp_handset_closed_form():
     assert np.allclose(rgb[:, 2], sig(-4 * 0.25 + np.float32(0.1)), atol=1e-7)
 
 
+def test_room_map_closed_form():
+    """The analytic room map through the full 8-layer trunk, skip input,
+    density head, feature layer and RGB head: density 64 clamp((m - 3)/eps)
+    with m = max |x_c|, colour sigmoid(a . f(x)) of the texture features."""
+    from room_scene import room_rgb, room_sigma
+    blob, a = synth.room_map_weights(0)
+    a32 = a.astype(np.float32).astype(np.float64)
+    rng = np.random.default_rng(4)
+    x = rng.uniform(-4, 4, size=(512, 3))
+    x[:64] = rng.uniform(2.99, 3.02, size=(64, 3)) * rng.choice([-1, 1], size=(64, 3))
+    d = _rand_dirs(rng, 512)
+    s, rgb = oracle.mlp(blob, x, d)
+    assert np.allclose(s, room_sigma(x, 3.0, 0.015625, 64.0), rtol=0, atol=1e-12)
+    assert np.allclose(rgb, room_rgb(x, a32), rtol=0, atol=1e-12)
+
+
+def test_room_render_converges_to_continuous_integral():
+    """Eq. 1 quadrature with 256 coarse + 256 importance samples on the room
+    map approaches the continuous rendering integral (fine trapezoid rule on
+    the closed-form field): colour within 5e-3, z_trans within 2e-2 of the
+    wall, and F = tau on the sharp wall."""
+    from room_scene import pixel_rays, render_continuous, wall_hit
+    blob, a = synth.room_map_weights(0)
+    a32 = a.astype(np.float32).astype(np.float64)
+    P = synth.random_particles(6, 2)[0]
+    px = synth.pixel_set(6, 25, 25, 16)
+    o, d = map(np.concatenate, zip(*[pixel_rays(p, 138.9 / 4, 138.9 / 4, 12.5, 12.5, px)
+                                      for p in P]))
+    ref, t_left = render_continuous(o, d, a32)
+    assert t_left.max() < 1e-6
+    r = oracle.render_rays(blob, o, d, oracle.make_opts(n_coarse=256, n_fine=256))
+    assert np.abs(r["rgb"] - ref).max() < 5e-3
+    assert np.abs(r["z_trans"] - wall_hit(o, d, 3.0)).max() < 2e-2
+    assert np.allclose(r["F"], 0.1)
+
+
 # ---------------------------------------------------------------- rays ----
 def test_ray_closed_form():
     f, cx, cy = 100.0, 50.0, 40.0
@@ -484,3 +520,84 @@ def test_position_spread_closed_form():
     # trace of the population covariance
     xs = np.array([[0, 0, 0], [2, 0, 0], [0, 4, 0]], dtype=float)
     assert s["trace"] == pytest.approx(((xs - xs.mean(0)) ** 2).sum() / 3)
+
+
+# ----------------------------------------------------- proposal sampler ---
+def _prop_rays(seed, n):
+    rng = np.random.default_rng(seed)
+    o = rng.uniform(-1, 1, size=(n, 3))
+    d = rng.normal(size=(n, 3))
+    d[:, 2] = -np.abs(d[:, 2]) - 0.5
+    return o, d
+
+
+def test_proposal_blob_size():
+    assert oracle.prop_n_weights() == synth.proposal_n_weights() == 15105
+
+
+def test_histogram_closed_form():
+    z = np.array([2.05, 2.2, 3.9, 4.1, 5.99, 6.5, 1.0])
+    w = np.array([0.1, 0.2, 0.3, 0.1, 0.2, 0.05, 0.05])
+    h = oracle.histogram(z, w, 4, 2.0, 6.0)
+    # bins [2,3) [3,4) [4,5) [5,6]; z = 6.5 clamps to the last, z = 1 to the first
+    assert np.allclose(h, np.array([0.1 + 0.2 + 0.05, 0.3, 0.1, 0.2 + 0.05]) / 1.0)
+    assert np.allclose(oracle.histogram(z, np.zeros(7), 4, 2.0, 6.0), 0.25)
+
+
+def test_proposal_constant_density_loss_closed_form():
+    """All weights zero and head bias b: density b everywhere, so the
+    composite weights and the cross-entropy have a closed form."""
+    b, nb = float(np.float32(0.8)), 16
+    blob = np.zeros(15105, dtype=np.float32)
+    blob[-1] = b
+    o, d = _prop_rays(1, 3)
+    rng = np.random.default_rng(2)
+    hist = rng.dirichlet(np.ones(nb), size=3)
+    loss, grad = oracle.prop_loss_grad(blob, o, d, hist)
+    ref = 0.0
+    for r in range(3):
+        dz = 4.0 / nb * np.linalg.norm(d[r])
+        k = np.arange(nb)
+        w = np.exp(-b * dz * k) * (1 - np.exp(-b * dz))
+        w[-1] = np.exp(-b * dz * (nb - 1))
+        ref += -(hist[r] * np.log(w / w.sum() + 1e-8)).sum()
+    assert loss == pytest.approx(ref / 3, rel=1e-12)
+    # zero network weights: only the head bias gets a gradient
+    assert np.all(grad[:-1] == 0.0) and grad[-1] != 0.0
+
+
+def test_proposal_gradient_matches_finite_differences():
+    """Analytic gradient (through the ReLU layers and the Eq. 1 compositing)
+    against central differences of the loss, in FP64 on an FP32 blob (the
+    step is the exact difference of the two FP32-rounded parameters)."""
+    base = synth.proposal_init_weights(3)
+    o, d = _prop_rays(4, 2)
+    rng = np.random.default_rng(5)
+    hist = rng.dirichlet(np.ones(16), size=2)
+    f = lambda b: oracle.prop_loss_grad(b, o, d, hist, with_grad=False)[0]
+    _, g = oracle.prop_loss_grad(base, o, d, hist)
+    idx = np.concatenate([rng.choice(15105, 60, replace=False), [15104, 15103, 0, 2559]])
+    checked = 0
+    for i in idx:
+        h = np.float32(2.0 ** -14 * max(1.0, abs(float(base[i]))))
+        bp, bm = base.copy(), base.copy()
+        bp[i] = np.float32(base[i] + h)
+        bm[i] = np.float32(base[i] - h)
+        fd = (f(bp) - f(bm)) / (float(bp[i]) - float(bm[i]))
+        # a ReLU kink inside [-h, h] makes the difference quotient one-sided;
+        # such parameters are detected by comparing the two one-sided slopes
+        f0 = f(base)
+        sp = (f(bp) - f0) / (float(bp[i]) - float(base[i]))
+        sm = (f0 - f(bm)) / (float(base[i]) - float(bm[i]))
+        if abs(sp - sm) > 1e-3 * max(1e-3, abs(sp)):
+            continue
+        assert abs(fd - g[i]) <= 1e-5 * max(1e-3, abs(g[i])) + 1e-9, (i, fd, g[i])
+        checked += 1
+    assert checked >= 50
+
+
+def test_proposal_weights_sum_to_at_most_one():
+    blob = synth.proposal_init_weights(6)
+    o, d = _prop_rays(7, 5)
+    w = oracle.prop_weights(blob, o, d, 64)
+    assert np.all(w >= 0) and np.all(w.sum(1) <= 1 + 1e-12)
