@@ -46,6 +46,32 @@ def load_peaks():
             "sm_max_mhz": 2070.0}, "fallback"
 
 
+def profiled_traffic(kernel_file: str, sources):
+    """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum)
+    from the committed ncu summary of a kernel, or None when the kernel's
+    sources have changed since the capture (the summary records their hash)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", kernel_file)
+    if not os.path.exists(path):
+        return None
+    h = hashlib.sha256()
+    for src in sources:
+        with open(os.path.join(ROOT, "paper_2406_12202_gb300", "csrc", src), "rb") as f:
+            h.update(f.read())
+    fields = {}
+    with open(path) as f:
+        for line in f:
+            if ":" in line and not line.startswith(("#", "|", " ")):
+                k, v = line.split(":", 1)
+                fields[k.strip()] = v.strip().split()[0] if v.strip() else ""
+    if fields.get("source_sha16") != h.hexdigest()[:16]:
+        return None
+    try:
+        return float(fields["traffic_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
 # ------------------------------------------------------------------ clocks
 class ClockSampler:
     FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -341,7 +367,11 @@ def run_ours(args):
                 "unit": "TFLOP/s", "peak_source": f"bf16_tflops burst ({peak_src})"
                 + (" x 2 nominal fp8/bf16 ratio" if prec == "fp8" else "")}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = None
+    roof["traffic"] = (profiled_traffic("k_mlp_tc_c2_bf16.md", ("mlp_tc.cu", "tc_ptx.cuh"))
+                       if prec == "bf16" else None)
+    if roof["traffic"] is not None:
+        roof["traffic_note"] = ("DRAM bytes per k_mlp_tc launch (mean of the coarse and fine "
+                                "pass), profiles/k_mlp_tc_c2_bf16.md")
     roof["kernel"] = "NeRF MLP (coarse + fine passes)"
     roof["mlp_ms_per_step"] = mlp_ms
 

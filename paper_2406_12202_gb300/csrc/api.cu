@@ -301,7 +301,7 @@ static int render_passes(mcl_map* m, const float* d_poses, int N, const mcl_intr
         return fail(MCL_ERR_ARG, "image %dx%d not divisible by level factor %d", K->width, K->height, f);
     if (!(K->fx > 0.f) || !(K->fy > 0.f)) return fail(MCL_ERR_ARG, "focal length must be > 0");
     const int nr = N * B;
-    if (o->precision != MCL_PREC_FP32 && !(o->precision == MCL_PREC_BF16 && mlp_tc_available(m)))
+    if (o->precision != MCL_PREC_FP32 && !mlp_tc_available(m, o->precision))
         return fail(MCL_ERR_UNSUPPORTED, "precision %d is not available on this device", o->precision);
     mcl_opts ro = *o;
     if (prop) {   // stratified midpoints of the proposal (the samples it was trained on)
@@ -418,7 +418,7 @@ extern "C" int mcl_query(mcl_map* m, const float* d_x, const float* d_dir, int n
     if (!m || !d_x || !d_dir || !d_out) return fail(MCL_ERR_ARG, "mcl_query: NULL argument");
     if (n < 1 || n > m->cfg.max_rays) return fail(MCL_ERR_ARG, "mcl_query: n %d outside [1, %d]", n, m->cfg.max_rays);
     if (((uintptr_t)d_out) % 16) return fail(MCL_ERR_ARG, "mcl_query: d_out must be 16-byte aligned");
-    if (precision != MCL_PREC_FP32 && !(precision == MCL_PREC_BF16 && mlp_tc_available(m)))
+    if (precision != MCL_PREC_FP32 && !mlp_tc_available(m, precision))
         return fail(MCL_ERR_UNSUPPORTED, "precision %d is not available on this device", precision);
     cudaStream_t s = (cudaStream_t)stream;
     int rc;
@@ -534,7 +534,8 @@ extern "C" int mcl_profile_read(mcl_map* m, double* ms_out, long long* n_launche
 extern "C" int mcl_map_supports(const mcl_map* m, int precision) {
     if (!m) return 0;
     if (precision == MCL_PREC_FP32) return 1;
-    if (precision == MCL_PREC_BF16) return mlp_tc_available(m) ? 1 : 0;
+    if (precision == MCL_PREC_BF16 || precision == MCL_PREC_FP8)
+        return mlp_tc_available(m, precision) ? 1 : 0;
     return 0;
 }
 
@@ -562,8 +563,8 @@ extern "C" int mcl_localize(mcl_map* m, int nq, float* d_particles, int stride, 
     if (!m || !d_particles || !h_n0 || !h_images || !K || !sch || !o || !d_log || !d_final_n)
         return fail(MCL_ERR_ARG, "mcl_localize: NULL argument");
     if ((rc = check_opts(o))) return rc;
-    if (!(o->precision == MCL_PREC_BF16 && mlp_tc_available(m)))
-        return fail(MCL_ERR_UNSUPPORTED, "mcl_localize: needs the BF16 tensor-core form");
+    if (o->precision == MCL_PREC_FP32 || !mlp_tc_available(m, o->precision))
+        return fail(MCL_ERR_UNSUPPORTED, "mcl_localize: needs a tensor-core form (BF16 or FP8)");
     if (nq < 1 || nq > m->cfg.max_queries) return fail(MCL_ERR_ARG, "mcl_localize: n_queries %d", nq);
     if (stride < 1 || (long)nq * stride > m->cfg.max_particles)
         return fail(MCL_ERR_ARG, "mcl_localize: n_queries * stride > max_particles");

@@ -159,7 +159,7 @@ cudaError_t mlp_fp32(mcl_map* m, const Ray* rays, const float* gd, const float* 
 // mlp_tc.cu
 int mlp_tc_prepare(mcl_map* m, const float* host_blob);
 void mlp_tc_free(mcl_map* m);
-bool mlp_tc_available(const mcl_map* m);
+bool mlp_tc_available(const mcl_map* m, int precision);
 cudaError_t mlp_tc_ray_bias(mcl_map* m, const float* gd, int n_rays, const int* n_rays_dev,
                             cudaStream_t s);
 // rows_dev (optional): device-side row count (rows = n_rays * S is the bound).

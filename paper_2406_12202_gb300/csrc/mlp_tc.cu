@@ -21,6 +21,7 @@
 // is bounded (see tc_ptx.cuh).
 #include <cuda.h>
 #include <cudaTypedefs.h>
+#include <cuda_fp8.h>
 #include <math.h>
 #include <string.h>
 
@@ -56,21 +57,39 @@ using namespace tc;
 
 namespace {
 
-constexpr int kEpiThreads = 128;                // 4 warps per 128-row tile
-constexpr int kThreads = 64 + 2 * kEpiThreads;   // + TMA warp + MMA warp
-constexpr int kStages = 4;
-constexpr uint32_t kStageBytes = 256 * 32 * 2;  // one weight block [256 rows x 32 k] bf16
-constexpr uint32_t kActBytes = 128 * 256 * 2;   // one tile's activations (4 K-blocks of 64)
-constexpr uint32_t kGxBytes = 128 * 64 * 2;     // one tile's gamma(x)
+constexpr uint32_t kStageBytes = 256 * 64;      // one weight block: 256 rows x 64 bytes
+constexpr uint32_t kGxBytes = 128 * 128;        // one tile's gamma(x): 128-byte rows
 constexpr int kLayers = 9;
-constexpr int kBlocksPerPair = 68;              // weight blocks streamed per tile pair
-constexpr uint32_t kSmemBytes = 1024 + 2 * kActBytes + 2 * kGxBytes + kStages * kStageBytes;
-// 32-wide K chunks (one weight block each) per layer: trunk1 reads gamma(x)
-// (64), trunk6 reads [h (256), gamma(x) (64)], the others h (256).  The last
+constexpr int kMaxStages = 8;
+
+// Operand form of the MMAs.  BF16: weight blocks [256 rows x 32 k], 4-stage
+// ring, activations 128 x 256 BF16 (64 KB per tile), 4 epilogue warps per
+// tile.  FP8 (E4M3 with per-layer activation scales and per-layer weight
+// scales): weight blocks [256 rows x 64 k], 8-stage ring, activations
+// 128 x 256 bytes (32 KB), 8 epilogue warps per tile (its epilogue does
+// more arithmetic per value and is on the critical path).  Both fill 225 KB
+// of shared memory.
+template <bool F8>
+struct Form {
+    static constexpr int kEpiWarps = F8 ? 8 : 4;     // per tile
+    static constexpr int kHalves = kEpiWarps / 4;    // column groups per TMEM lane quadrant
+    static constexpr int kEpiThreads = 32 * kEpiWarps;
+    static constexpr int kThreads = 64 + 2 * kEpiThreads;   // + TMA warp + MMA warp
+    static constexpr uint32_t kActBytes = F8 ? 128 * 256 : 128 * 256 * 2;
+    static constexpr int kStages = F8 ? 8 : 4;
+    static constexpr int kBlocks = F8 ? 34 : 68;     // weight blocks per tile pair
+    static constexpr int kActChunks = F8 ? 4 : 8;    // K chunks of a 256-wide activation
+    static constexpr uint32_t kSmemBytes = 1024 + 2 * kActBytes + 2 * kGxBytes + kStages * kStageBytes;
+};
+static_assert(Form<false>::kSmemBytes <= 232448 && Form<true>::kSmemBytes <= 232448, "smem");
+
+// K chunks (one weight block each) per layer: trunk1 reads gamma(x) (64),
+// trunk6 reads [h (256), gamma(x) (64)], the others h (256).  The last
 // layer has N = 144: rows 0..127 are the RGB hidden layer (feature layer
 // folded in), row 128 the density head, so sigma_raw arrives as accumulator
 // column 128 of the last MMA.
-__constant__ int c_chunks[kLayers] = {2, 8, 8, 8, 8, 10, 8, 8, 8};
+__constant__ int c_chunks[2][kLayers] = {{2, 8, 8, 8, 8, 10, 8, 8, 8},
+                                         {1, 4, 4, 4, 4, 5, 4, 4, 4}};
 
 struct Params {
     const Ray* rays;
@@ -79,7 +98,12 @@ struct Params {
     long long M;            // rows of the pass (upper bound when M_dev is set)
     long long n_pairs;
     const int* M_dev;       // optional: rows of the pass from device memory
-    const uint32_t* bias2;  // [8][128] trunk biases as BF16 pairs
+    const uint32_t* bias2;  // BF16: [8][128] trunk biases as BF16 pairs
+    const float* beta;      // FP8: [8][256] epilogue offset per column
+    float alpha[8];         // FP8: epilogue scale per trunk layer
+    const float* alpha_last;// FP8: [128] dequantisation of the RGB hidden layer
+    float alpha_sigma;      // FP8: dequantisation of the density head
+    float s_gx;             // FP8: scale of gamma(x)
     float b_sigma;
     const float* ray_bias;  // [n_rays][128]
     const float* w_out;     // [3][128]
@@ -90,8 +114,8 @@ struct Params {
 };
 
 struct __align__(8) Bars {
-    uint64_t full[kStages];
-    uint64_t empty[kStages];
+    uint64_t full[kMaxStages];
+    uint64_t empty[kMaxStages];
     uint64_t acc_full[2];
     uint64_t a_ready[2];
     uint64_t drain;
@@ -102,28 +126,30 @@ __device__ __forceinline__ void record_abort(const Params& p) {
     atomicCAS(p.status_code, 0, MCL_ERR_TIMEOUT);
 }
 
-// gamma(x) of one row as 32 packed BF16 pairs; sin / cos of 2^k x by angle
-// doubling from an accurate sincos of x (error ~2^k ulp, far below BF16).
-__device__ __forceinline__ void pe_row_bf16(const float x[3], uint32_t (&pk)[32]) {
-    float v[64];
-    v[0] = x[0]; v[1] = x[1]; v[2] = x[2];
+// Half H of gamma(x) of one row: values 32 H .. 32 H + 31 of [x, sin(2^k x),
+// cos(2^k x) (k = 0..9, each on the 3 axes), 0].  sin / cos of 2^k x by angle
+// doubling from an accurate sincos of 2^k0 x (k0 = 0, or 4 for the upper
+// half; error ~2^(k - k0) ulp, far below the operand precision).
+template <int H>
+__device__ __forceinline__ void pe_half(const float x[3], float (&v)[32]) {
+    constexpr int k0 = H ? 4 : 0;
+    if (H == 0) { v[0] = x[0]; v[1] = x[1]; v[2] = x[2]; }
+    if (H == 1) v[31] = 0.0f;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         float s, cs;
-        sincosf(x[c], &s, &cs);
+        sincosf(H ? 16.0f * x[c] : x[c], &s, &cs);
 #pragma unroll
-        for (int k = 0; k < kLxyz; ++k) {
-            v[3 + 6 * k + c] = s;
-            v[6 + 6 * k + c] = cs;
+        for (int k = k0; k < kLxyz; ++k) {
+            const int is = 3 + 6 * k + c - 32 * H, ic = 6 + 6 * k + c - 32 * H;
+            if (is >= 0 && is < 32) v[is] = s;
+            if (ic >= 0 && ic < 32) v[ic] = cs;
             const float s2 = 2.0f * s * cs;
             const float c2 = (cs - s) * (cs + s);
             s = s2;
             cs = c2;
         }
     }
-    v[63] = 0.0f;
-#pragma unroll
-    for (int i = 0; i < 32; ++i) pk[i] = pack_bf16x2(v[2 * i], v[2 * i + 1]);
 }
 
 // 32 accumulator columns of one row -> relu(acc + bias) as BF16 -> four
@@ -151,12 +177,63 @@ __device__ __forceinline__ void epi_chunk_store(const uint32_t (&v)[32], const u
                      pk[4 * q + 3]);
 }
 
-__global__ void __launch_bounds__(kThreads, 1)
+// FP8 form: 32 accumulator columns -> relu(acc alpha + beta) (the next
+// layer's activation scale folded into alpha, beta) as E4M3 -> two 16-byte
+// chunks (j0, j0+1) of the row in a 128-byte-swizzled K-block.
+__device__ __forceinline__ void epi_chunk_store_f8(const uint32_t (&v)[32], float alpha,
+                                                   const float4* b4, uint32_t blk, uint32_t r,
+                                                   uint32_t j0) {
+    uint32_t pk[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const float4 b = __ldg(b4 + q);
+        pk[q] = pack_e4m3x4_relu(fmaf(__uint_as_float(v[4 * q + 0]), alpha, b.x),
+                                 fmaf(__uint_as_float(v[4 * q + 1]), alpha, b.y),
+                                 fmaf(__uint_as_float(v[4 * q + 2]), alpha, b.z),
+                                 fmaf(__uint_as_float(v[4 * q + 3]), alpha, b.w));
+    }
+    st_shared_v4(blk + sw128_offset(r, j0), pk[0], pk[1], pk[2], pk[3]);
+    st_shared_v4(blk + sw128_offset(r, j0 + 1), pk[4], pk[5], pk[6], pk[7]);
+}
+
+// One 32-column group of the last layer: h = relu(acc (* alpha) + b_ray),
+// then the 128 -> 3 output layer as running dot products.
+template <bool F8>
+__device__ __forceinline__ void rgb_group(const uint32_t (&v)[32], const float4* rb4,
+                                          const float4* wo4, const float4* al4, int c32,
+                                          float& o0, float& o1, float& o2) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const float4 b = __ldg(rb4 + c32 * 8 + q);
+        const float4 w0 = __ldg(wo4 + c32 * 8 + q);
+        const float4 w1 = __ldg(wo4 + 32 + c32 * 8 + q);
+        const float4 w2 = __ldg(wo4 + 64 + c32 * 8 + q);
+        float a0 = __uint_as_float(v[4 * q + 0]), a1 = __uint_as_float(v[4 * q + 1]);
+        float a2 = __uint_as_float(v[4 * q + 2]), a3 = __uint_as_float(v[4 * q + 3]);
+        if constexpr (F8) {
+            const float4 al = __ldg(al4 + c32 * 8 + q);
+            a0 *= al.x; a1 *= al.y; a2 *= al.z; a3 *= al.w;
+        }
+        const float h0 = fmaxf(a0 + b.x, 0.0f);
+        const float h1 = fmaxf(a1 + b.y, 0.0f);
+        const float h2 = fmaxf(a2 + b.z, 0.0f);
+        const float h3 = fmaxf(a3 + b.w, 0.0f);
+        o0 = fmaf(h0, w0.x, fmaf(h1, w0.y, fmaf(h2, w0.z, fmaf(h3, w0.w, o0))));
+        o1 = fmaf(h0, w1.x, fmaf(h1, w1.y, fmaf(h2, w1.z, fmaf(h3, w1.w, o1))));
+        o2 = fmaf(h0, w2.x, fmaf(h1, w2.y, fmaf(h2, w2.z, fmaf(h3, w2.w, o2))));
+    }
+}
+
+template <bool F8>
+__global__ void __launch_bounds__(Form<F8>::kThreads, 1)
     k_mlp_tc(const __grid_constant__ CUtensorMap tmap, const Params p) {
+    using Fm = Form<F8>;
+    constexpr int kStages = Fm::kStages;
+    constexpr uint32_t kActBytes = Fm::kActBytes;
     extern __shared__ uint8_t smem_raw[];
     __shared__ Bars bars;
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    const uint32_t s_act = smem_u32(smem);                    // 2 x 64 KB
+    const uint32_t s_act = smem_u32(smem);                    // 2 activation tiles
     const uint32_t s_gx = s_act + 2 * kActBytes;              // 2 x 16 KB
     const uint32_t s_ring = s_gx + 2 * kGxBytes;              // kStages x 16 KB
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -172,7 +249,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         for (int s = 0; s < 2; ++s) {
             mbar_init(smem_u32(&bars.acc_full[s]), 1);
-            mbar_init(smem_u32(&bars.a_ready[s]), kEpiThreads);
+            mbar_init(smem_u32(&bars.a_ready[s]), Fm::kEpiThreads);
         }
         mbar_init(smem_u32(&bars.drain), 1);
         fence_mbar_init();
@@ -190,11 +267,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (warp == 0) {
         // ------------------------------------------------ TMA producer
         if (lane == 0) {
-            uint32_t issued[kStages] = {0, 0, 0, 0};
             uint32_t g = 0;
             bool ok = true;
             for (long long pr = blockIdx.x; pr < n_pairs && ok; pr += gridDim.x) {
-                for (int b = 0; b < kBlocksPerPair; ++b, ++g) {
+                for (int b = 0; b < Fm::kBlocks; ++b, ++g) {
                     const uint32_t st = g % kStages, ph = (g / kStages) & 1u;
                     TC_TRACE(0, g);
                     if (!mbar_wait(smem_u32(&bars.empty[st]), ph ^ 1u, abort_flag)) {
@@ -205,14 +281,15 @@ __global__ void __launch_bounds__(kThreads, 1)
                     mbar_arrive_expect_tx(smem_u32(&bars.full[st]), kStageBytes);
                     tma_load_2d(s_ring + st * kStageBytes, &tmap, 0, b * 256,
                                 smem_u32(&bars.full[st]));
-                    ++issued[st];
                 }
             }
             if (!ok) record_abort(p);
-            // every issued copy lands before the CTA may exit
-            for (int st = 0; st < kStages; ++st)
-                if (issued[st])
-                    mbar_wait(smem_u32(&bars.full[st]), (issued[st] - 1) & 1u, nullptr);
+            // every issued copy lands before the CTA may exit: the last copy
+            // of each stage (earlier ones were consumed before it was issued)
+            for (uint32_t k = 0; k < (uint32_t)kStages && k < g; ++k) {
+                const uint32_t gl = g - 1 - k;
+                mbar_wait(smem_u32(&bars.full[gl % kStages]), (gl / kStages) & 1u, nullptr);
+            }
         }
     } else if (warp == 1) {
         // ------------------------------------------------ MMA issuer
@@ -220,19 +297,22 @@ __global__ void __launch_bounds__(kThreads, 1)
             uint32_t g = 0;
             uint32_t rdy_ph[2] = {0, 0};
             bool ok = true;
-            const uint32_t id256 = idesc_bf16(128, 256), id144 = idesc_bf16(128, 144);
+            const uint32_t id256 = F8 ? idesc_e4m3(128, 256) : idesc_bf16(128, 256);
+            const uint32_t id144 = F8 ? idesc_e4m3(128, 144) : idesc_bf16(128, 144);
             int tl = 0;
             for (long long pr = blockIdx.x; pr < n_pairs && ok; pr += gridDim.x) {
                 for (int l = 0; l < kLayers && ok; ++l, ++tl) {
-                    const int nch = c_chunks[l];
+                    const int nch = c_chunks[F8 ? 1 : 0][l];
                     const uint32_t idesc = (l == 8) ? id144 : id256;
                     TC_TRACE(2, tl);
                     for (int c = 0; c < nch && ok; ++c) {
                         const uint32_t st = g % kStages, ph = (g / kStages) & 1u;
+                        TC_TRACE(15, g);
                         if (!mbar_wait(smem_u32(&bars.full[st]), ph, abort_flag)) {
                             ok = false;
                             break;
                         }
+                        TC_TRACE(13, g);
                         tc_fence_after();
                         for (int s = 0; s < 2; ++s) {
                             if (c == 0) {
@@ -246,11 +326,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                             }
 #pragma unroll
                             for (int kk = 0; kk < 2; ++kk) {
+                                // K steps are 32 bytes (16 BF16 or 32 E4M3 values)
                                 uint32_t a_addr;
                                 if (l == 0) {
                                     a_addr = s_gx + s * kGxBytes + (c * 2 + kk) * 32;
-                                } else if (l == 5 && c >= 8) {
-                                    a_addr = s_gx + s * kGxBytes + ((c - 8) * 2 + kk) * 32;
+                                } else if (l == 5 && c >= Fm::kActChunks) {
+                                    a_addr = s_gx + s * kGxBytes + ((c - Fm::kActChunks) * 2 + kk) * 32;
                                 } else {
                                     const int ks = c * 2 + kk;
                                     a_addr = s_act + s * kActBytes + (ks >> 2) * 16384 + (ks & 3) * 32;
@@ -258,7 +339,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                                 const uint64_t ad = smem_desc(a_addr, 1024, kLayoutSw128);
                                 const uint64_t bd =
                                     smem_desc(s_ring + st * kStageBytes + kk * 32, 512, kLayoutSw64);
-                                mma_bf16(tmem + s * 256, ad, bd, idesc, (c | kk) ? 1u : 0u);
+                                if constexpr (F8)
+                                    mma_f8(tmem + s * 256, ad, bd, idesc, (c | kk) ? 1u : 0u);
+                                else
+                                    mma_bf16(tmem + s * 256, ad, bd, idesc, (c | kk) ? 1u : 0u);
                             }
                             if (c == nch - 1) mma_commit(smem_u32(&bars.acc_full[s]));
                         }
@@ -276,123 +360,162 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
     } else {
         // ------------------------------------------------ prologue / epilogues
-        // 4 warps per tile: warp w covers TMEM lane quadrant (w % 4), i.e. rows
-        // 32 (w % 4) .. +31, all columns; one thread owns one row.
-        const int slot = (warp - 2) >> 2;
+        // kEpiWarps warps per tile: warp w covers TMEM lane quadrant (w % 4),
+        // i.e. rows 32 (w % 4) .. +31; with 8 warps the first four take
+        // accumulator columns 0..127 and the other four 128..255 (column
+        // halves h0 .. h1 - 1 of 128); one thread owns one row.
+        constexpr int kH = Fm::kHalves;
+        const int slot = (warp - 2) / Fm::kEpiWarps;
+        const int h0 = kH == 2 ? (((warp - 2) >> 2) & 1) : 0;
+        const int h1 = h0 + 3 - kH;                       // one half, or both
         const int quad = warp & 3;
         const uint32_t r = quad * 32 + lane;              // row within the tile
-        const uint32_t t_acc = tmem + ((uint32_t)(quad * 32) << 16) + slot * 256;
+        const uint32_t t_row = tmem + ((uint32_t)(quad * 32) << 16) + slot * 256;
         const uint32_t a_base = s_act + slot * kActBytes;
         const uint32_t g_base = s_gx + slot * kGxBytes;
         const uint32_t bar_ready = smem_u32(&bars.a_ready[slot]);
         const uint32_t bar_acc = smem_u32(&bars.acc_full[slot]);
         uint32_t acc_ph = 0;
         bool ok = true;
-        const bool tracer = (r == 0);
+        const bool tracer = (r == 0 && h0 == 0);
         int tl = 0;
         for (long long pr = blockIdx.x; pr < n_pairs && ok; pr += gridDim.x) {
             const long long grow = pr * 256 + slot * 128 + r;
             const bool valid = grow < M;
             const long long ray = valid ? grow / p.S : 0;
-            // ---- prologue: gamma(x) of this row into the tile's gamma(x) buffer
+            // ---- prologue: this thread's halves of gamma(x) into the tile's
+            //      gamma(x) buffer
             {
-                uint32_t pk[32];
+                float x[3] = {0.f, 0.f, 0.f};
                 if (valid) {
                     const Ray R = p.rays[ray];
                     const float zz = p.z[grow];
-                    const float x[3] = {fmaf(zz, R.dx, R.ox), fmaf(zz, R.dy, R.oy),
-                                        fmaf(zz, R.dz, R.oz)};
-                    pe_row_bf16(x, pk);
-                } else {
-#pragma unroll
-                    for (int i = 0; i < 32; ++i) pk[i] = 0u;
+                    x[0] = fmaf(zz, R.dx, R.ox);
+                    x[1] = fmaf(zz, R.dy, R.oy);
+                    x[2] = fmaf(zz, R.dz, R.oz);
                 }
+                for (int half = h0; half < h1; ++half) {
+                    float v[32];
+                    if (valid) {
+                        if (half == 0) pe_half<0>(x, v);
+                        else pe_half<1>(x, v);
+                    } else {
 #pragma unroll
-                for (int j = 0; j < 8; ++j)
-                    st_shared_v4(g_base + sw128_offset(r, j), pk[4 * j], pk[4 * j + 1],
-                                 pk[4 * j + 2], pk[4 * j + 3]);
+                        for (int i = 0; i < 32; ++i) v[i] = 0.0f;
+                    }
+                    if constexpr (F8) {
+                        const float sg = p.s_gx;
+#pragma unroll
+                        for (int j = 0; j < 2; ++j) {
+                            uint32_t w[4];
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) {
+                                const int i = 16 * j + 4 * e;
+                                w[e] = pack_e4m3x4(v[i] * sg, v[i + 1] * sg, v[i + 2] * sg,
+                                                   v[i + 3] * sg);
+                            }
+                            st_shared_v4(g_base + sw128_offset(r, 2 * half + j), w[0], w[1], w[2], w[3]);
+                        }
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 4; ++j)
+                            st_shared_v4(g_base + sw128_offset(r, 4 * half + j),
+                                         pack_bf16x2(v[8 * j], v[8 * j + 1]),
+                                         pack_bf16x2(v[8 * j + 2], v[8 * j + 3]),
+                                         pack_bf16x2(v[8 * j + 4], v[8 * j + 5]),
+                                         pack_bf16x2(v[8 * j + 6], v[8 * j + 7]));
+                    }
+                }
                 fence_proxy_async_smem();
                 tc_fence_before();
                 mbar_arrive(bar_ready);
             }
             float sigma = 0.0f;
             for (int l = 0; l < kLayers && ok; ++l, ++tl) {
-                if (!mbar_wait(bar_acc, acc_ph, abort_flag)) {
+                if (!mbar_wait_sleep(bar_acc, acc_ph, abort_flag)) {
                     ok = false;
                     break;
                 }
                 if (tracer) TC_TRACE(6 + 2 * slot, tl);
                 acc_ph ^= 1u;
                 tc_fence_after();
+#ifdef MCL_EXP_NO_EPI
                 if (l < 8) {
-                    // h = relu(acc + b): accumulators rounded to BF16 pairs,
-                    // bias added and ReLU applied in packed BF16 arithmetic
-                    const uint4* b4 = reinterpret_cast<const uint4*>(p.bias2 + l * 128);
-                    uint32_t va[32], vb[32];
-                    tmem_ld32(t_acc, va);
+                    fence_proxy_async_smem();
+                    tc_fence_before();
+                    mbar_arrive(bar_ready);
+                    continue;
+                }
+#endif
+                if (l < 8) {
+                    // this thread's columns, 32 at a time, the next TMEM load
+                    // in flight while the current group is stored
+                    for (int half = h0; half < h1; ++half) {
+                        const uint32_t t_acc = t_row + half * 128;
+                        uint32_t va[32], vb[32];
+                        tmem_ld32(t_acc, va);
+                        if constexpr (F8) {
+                            // h = relu(acc alpha + beta) in FP32, stored as E4M3:
+                            // columns 128 half .. +127 are K-block `half`, chunks 0..7
+                            const float alpha = p.alpha[l];
+                            const float4* b4 =
+                                reinterpret_cast<const float4*>(p.beta + l * 256 + half * 128);
+                            const uint32_t blk = a_base + half * 16384;
 #pragma unroll 1
-                    for (int c32 = 0; c32 < 8; c32 += 2) {
-                        tmem_ld_wait();
-                        if (tracer && slot == 0 && tl < 16) TC_TRACE(10 + (c32 >> 1), tl);
-                        tmem_ld32(t_acc + (c32 + 1) * 32, vb);
-                        const uint32_t blk = a_base + (c32 >> 1) * 16384;
-                        epi_chunk_store(va, b4 + c32 * 4, blk, r, 0);
-                        tmem_ld_wait();
-                        if (c32 + 2 < 8) tmem_ld32(t_acc + (c32 + 2) * 32, va);
-                        epi_chunk_store(vb, b4 + (c32 + 1) * 4, blk, r, 4);
+                            for (int c32 = 0; c32 < 4; c32 += 2) {
+                                tmem_ld_wait();
+                                tmem_ld32(t_acc + (c32 + 1) * 32, vb);
+                                epi_chunk_store_f8(va, alpha, b4 + c32 * 8, blk, r, c32 * 2);
+                                tmem_ld_wait();
+                                if (c32 + 2 < 4) tmem_ld32(t_acc + (c32 + 2) * 32, va);
+                                epi_chunk_store_f8(vb, alpha, b4 + (c32 + 1) * 8, blk, r,
+                                                   (c32 + 1) * 2);
+                            }
+                        } else {
+                            // h = relu(acc + b): accumulators rounded to BF16 pairs,
+                            // bias added and ReLU applied in packed BF16 arithmetic;
+                            // columns 128 half .. +127 are K-blocks 2 half, 2 half + 1
+                            const uint4* b4 =
+                                reinterpret_cast<const uint4*>(p.bias2 + l * 128 + half * 64);
+#pragma unroll 1
+                            for (int c32 = 0; c32 < 4; c32 += 2) {
+                                tmem_ld_wait();
+                                tmem_ld32(t_acc + (c32 + 1) * 32, vb);
+                                const uint32_t blk = a_base + (2 * half + (c32 >> 1)) * 16384;
+                                epi_chunk_store(va, b4 + c32 * 4, blk, r, 0);
+                                tmem_ld_wait();
+                                if (c32 + 2 < 4) tmem_ld32(t_acc + (c32 + 2) * 32, va);
+                                epi_chunk_store(vb, b4 + (c32 + 1) * 4, blk, r, 4);
+                            }
+                        }
                     }
-                    if (tracer && slot == 0 && tl < 16) TC_TRACE(14, tl);
                     fence_proxy_async_smem();
                     tc_fence_before();
                     if (tracer) TC_TRACE(7 + 2 * slot, tl);
                     mbar_arrive(bar_ready);
-                } else {
+                } else if (h0 == 0) {
                     const float4* rb4 = reinterpret_cast<const float4*>(p.ray_bias + ray * 128);
                     const float4* wo4 = reinterpret_cast<const float4*>(p.w_out);
+                    const float4* al4 = reinterpret_cast<const float4*>(p.alpha_last);
                     float o0 = 0.f, o1 = 0.f, o2 = 0.f;
                     uint32_t va[32], vb[32];
-                    tmem_ld32(t_acc, va);
+                    tmem_ld32(t_row, va);
 #pragma unroll 1
                     for (int c32 = 0; c32 < 4; c32 += 2) {
                         tmem_ld_wait();
-                        tmem_ld32(t_acc + (c32 + 1) * 32, vb);
-#pragma unroll
-                        for (int q = 0; q < 8; ++q) {
-                            const float4 b = __ldg(rb4 + c32 * 8 + q);
-                            const float4 w0 = __ldg(wo4 + c32 * 8 + q);
-                            const float4 w1 = __ldg(wo4 + 32 + c32 * 8 + q);
-                            const float4 w2 = __ldg(wo4 + 64 + c32 * 8 + q);
-                            const float h0 = fmaxf(__uint_as_float(va[4 * q + 0]) + b.x, 0.0f);
-                            const float h1 = fmaxf(__uint_as_float(va[4 * q + 1]) + b.y, 0.0f);
-                            const float h2 = fmaxf(__uint_as_float(va[4 * q + 2]) + b.z, 0.0f);
-                            const float h3 = fmaxf(__uint_as_float(va[4 * q + 3]) + b.w, 0.0f);
-                            o0 = fmaf(h0, w0.x, fmaf(h1, w0.y, fmaf(h2, w0.z, fmaf(h3, w0.w, o0))));
-                            o1 = fmaf(h0, w1.x, fmaf(h1, w1.y, fmaf(h2, w1.z, fmaf(h3, w1.w, o1))));
-                            o2 = fmaf(h0, w2.x, fmaf(h1, w2.y, fmaf(h2, w2.z, fmaf(h3, w2.w, o2))));
-                        }
+                        tmem_ld32(t_row + (c32 + 1) * 32, vb);
+                        rgb_group<F8>(va, rb4, wo4, al4, c32, o0, o1, o2);
                         tmem_ld_wait();
-                        if (c32 + 2 < 4) tmem_ld32(t_acc + (c32 + 2) * 32, va);
-#pragma unroll
-                        for (int q = 0; q < 8; ++q) {
-                            const float4 b = __ldg(rb4 + (c32 + 1) * 8 + q);
-                            const float4 w0 = __ldg(wo4 + (c32 + 1) * 8 + q);
-                            const float4 w1 = __ldg(wo4 + 32 + (c32 + 1) * 8 + q);
-                            const float4 w2 = __ldg(wo4 + 64 + (c32 + 1) * 8 + q);
-                            const float h0 = fmaxf(__uint_as_float(vb[4 * q + 0]) + b.x, 0.0f);
-                            const float h1 = fmaxf(__uint_as_float(vb[4 * q + 1]) + b.y, 0.0f);
-                            const float h2 = fmaxf(__uint_as_float(vb[4 * q + 2]) + b.z, 0.0f);
-                            const float h3 = fmaxf(__uint_as_float(vb[4 * q + 3]) + b.w, 0.0f);
-                            o0 = fmaf(h0, w0.x, fmaf(h1, w0.y, fmaf(h2, w0.z, fmaf(h3, w0.w, o0))));
-                            o1 = fmaf(h0, w1.x, fmaf(h1, w1.y, fmaf(h2, w1.z, fmaf(h3, w1.w, o1))));
-                            o2 = fmaf(h0, w2.x, fmaf(h1, w2.y, fmaf(h2, w2.z, fmaf(h3, w2.w, o2))));
-                        }
+                        if (c32 + 2 < 4) tmem_ld32(t_row + (c32 + 2) * 32, va);
+                        rgb_group<F8>(vb, rb4, wo4, al4, c32 + 1, o0, o1, o2);
                     }
                     {
                         // density head: accumulator column 128 of the last MMA
                         uint32_t vs[32];
-                        tmem_ld32(t_acc + 128, vs);
+                        tmem_ld32(t_row + 128, vs);
                         tmem_ld_wait();
                         sigma = __uint_as_float(vs[0]);
+                        if constexpr (F8) sigma *= p.alpha_sigma;
                     }
                     tc_fence_before();
                     if (valid) {
@@ -432,19 +555,27 @@ __global__ void k_ray_bias(const float* __restrict__ gd, int n_rays, const int* 
     out[t] = s;
 }
 
-struct TcState {
+struct TcForm {
     CUtensorMap tmap;
-    void* wblocks = nullptr;   // bf16 weight blocks
-    float* aux = nullptr;      // fp32 biases and small heads
+    void* wblocks = nullptr;   // weight blocks in consumption order
+    bool ready = false;
+};
+
+struct TcState {
+    TcForm bf16, fp8;
+    float* aux = nullptr;      // fp32 biases, scales and small heads
     float* ray_bias = nullptr; // [max_rays][128]
     int* abort_flag = nullptr;
     const uint32_t* bias2 = nullptr;
+    const float* beta = nullptr;
+    const float* alpha_last = nullptr;
+    float alpha[8] = {1, 1, 1, 1, 1, 1, 1, 1};
     const float* w_out = nullptr;
     const float* Wd = nullptr;
     const float* bprime = nullptr;
     float b_sigma = 0.f, b_out[3] = {0.f, 0.f, 0.f};
+    float alpha_sigma = 1.f, s_gx = 1.f;
     int n_sm = 0;
-    bool ready = false;
 };
 
 inline uint16_t f2bf(float f) {
@@ -454,6 +585,64 @@ inline uint16_t f2bf(float f) {
     const uint32_t lsb = (u >> 16) & 1u;
     u += 0x7fffu + lsb;                                   // round to nearest even
     return (uint16_t)(u >> 16);
+}
+
+inline uint8_t f2e4m3(double f) {
+    return (uint8_t)__nv_cvt_float_to_fp8((float)f, __NV_SATFINITE, __NV_E4M3);
+}
+
+// Largest |value| of each layer's input over calibration points of a box
+// that holds the cameras and the [near, far] sample range of the workloads
+// (positions in [-8, 8]^3, unit directions): [0] gamma(x), [l] the output of
+// trunk layer l (l = 1..8).  FP64 host forward of the trunk.
+void calibrate(const float* const* Wp, const float* const* bp, const int* fin,
+               double (&amax)[kDepth + 1]) {
+    for (double& a : amax) a = 0.0;
+    uint64_t st = 0x9E3779B97F4A7C15ull;
+    auto uni = [&]() {  // SplitMix64 -> [0, 1)
+        uint64_t z = (st += 0x9E3779B97F4A7C15ull);
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        return (double)(z >> 11) * (1.0 / 9007199254740992.0);
+    };
+    std::vector<double> gx(kGx), h(kWidth + kGx), t(kWidth);
+    for (int n = 0; n < 1024; ++n) {
+        const double x[3] = {16.0 * uni() - 8.0, 16.0 * uni() - 8.0, 16.0 * uni() - 8.0};
+        for (int c = 0; c < 3; ++c) gx[c] = x[c];
+        for (int k = 0; k < kLxyz; ++k)
+            for (int c = 0; c < 3; ++c) {
+                gx[3 + 6 * k + c] = sin(ldexp(x[c], k));
+                gx[6 + 6 * k + c] = cos(ldexp(x[c], k));
+            }
+        for (int i = 0; i < kGx; ++i) amax[0] = fmax(amax[0], fabs(gx[i]));
+        for (int i = 0; i < kGx; ++i) h[i] = gx[i];
+        for (int l = 0; l < kDepth; ++l) {
+            for (int o = 0; o < kWidth; ++o) {
+                double sum = bp[l][o];
+                const float* w = Wp[l] + (size_t)o * fin[l];
+                for (int i = 0; i < fin[l]; ++i) sum += (double)w[i] * h[i];
+                t[o] = sum > 0.0 ? sum : 0.0;
+                amax[l + 1] = fmax(amax[l + 1], t[o]);
+            }
+            for (int o = 0; o < kWidth; ++o) h[o] = t[o];
+            if (l + 1 == kSkip)
+                for (int i = 0; i < kGx; ++i) h[kWidth + i] = gx[i];
+        }
+    }
+}
+
+int make_tmap(TcForm& f, CUtensorMapDataType dt, cuuint64_t inner, int n_blocks,
+              PFN_cuTensorMapEncodeTiled_v12000 encode) {
+    cuuint64_t dims[2] = {inner, (cuuint64_t)n_blocks * 256};
+    cuuint64_t strides[1] = {64};
+    cuuint32_t box[2] = {(cuuint32_t)inner, 256};
+    cuuint32_t es[2] = {1, 1};
+    CUresult r = encode(&f.tmap, dt, 2, f.wblocks, dims, strides, box, es,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(MCL_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return MCL_OK;
 }
 
 }  // namespace
@@ -493,37 +682,85 @@ int mlp_tc_prepare(mcl_map* m, const float* blob) {
             Wfold[(size_t)o * kWidth + i] = s;
         }
     }
-    // ---- weight blocks [256 rows][32 k] in consumption order
-    std::vector<uint16_t> blk((size_t)kBlocksPerPair * 256 * 32, 0);
-    int b = 0;
-    auto put_chunk = [&](int block, int row0, int nrows, auto getter, int k0) {
-        for (int n = 0; n < nrows; ++n)
-            for (int k = 0; k < 32; ++k)
-                blk[((size_t)block * 256 + row0 + n) * 32 + k] = f2bf((float)getter(n, k0 + k));
+    // weight of padded layer l (0..8) at output row n, padded input column k
+    // ([h, gamma(x)] order for the skip layer; padding columns are 0); layer
+    // 8 is the last MMA: rows 0..127 RGB hidden (folded), row 128 density
+    auto weight = [&](int l, int n, int k) -> double {
+        if (l == 8) {
+            if (n < kRgbW) return Wfold[(size_t)n * kWidth + k];
+            return n == kRgbW ? (double)Wp[8][k] : 0.0;
+        }
+        if (k >= fin[l]) return 0.0;
+        return (double)Wp[l][(size_t)n * fin[l] + k];
     };
-    // trunk layers: K padded (gamma(x) 63 -> 64); layer 6 = [h | gamma(x)]
-    for (int l = 0; l < kDepth; ++l) {
-        const int K = (l == 0) ? kGxPad : (l == kSkip ? kWidth + kGxPad : kWidth);
-        for (int k0 = 0; k0 < K; k0 += 32, ++b) {
-            // column k of the padded layer is column k of the blob layer
-            // ([h, gamma(x)] order for the skip layer); padding columns are 0
-            auto get = [&](int n, int k) -> double {
-                if (k >= fin[l]) return 0.0;
-                return (double)Wp[l][(size_t)n * fin[l] + k];
-            };
-            put_chunk(b, 0, 256, get, k0);
+    auto padded_k = [&](int l) { return l == 0 ? kGxPad : (l == kSkip ? kWidth + kGxPad : kWidth); };
+    // ---- BF16 weight blocks [256 rows][32 k] in consumption order
+    const int nb16 = Form<false>::kBlocks;
+    std::vector<uint16_t> blk((size_t)nb16 * 256 * 32, 0);
+    int b = 0;
+    for (int l = 0; l < kLayers; ++l) {
+        const int nrows = (l == 8) ? kRgbW + 1 : kWidth;
+        for (int k0 = 0; k0 < padded_k(l); k0 += 32, ++b)
+            for (int n = 0; n < nrows; ++n)
+                for (int k = 0; k < 32; ++k)
+                    blk[((size_t)b * 256 + n) * 32 + k] = f2bf((float)weight(l, n, k0 + k));
+    }
+    if (b != nb16) return fail(MCL_ERR_UNSUPPORTED, "internal: weight block count %d", b);
+    // ---- FP8 form: activation scales from calibration (largest value -> 224,
+    //      half the E4M3 range), per-row weight scales (largest |w| -> 448)
+    double amax[kDepth + 1];
+    calibrate(Wp, bp, fin, amax);
+    double sa[kDepth + 1];
+    for (int l = 0; l <= kDepth; ++l) sa[l] = 224.0 / (amax[l] > 1e-30 ? amax[l] : 1.0);
+    // scale of input column k of layer l
+    auto in_scale = [&](int l, int k) -> double {
+        if (l == 0) return sa[0];
+        if (l == kSkip && k >= kWidth) return sa[0];
+        return sa[l];
+    };
+    const int nb8 = Form<true>::kBlocks;
+    std::vector<uint8_t> blk8((size_t)nb8 * 256 * 64, 0);
+    std::vector<float> beta((size_t)kDepth * kWidth);
+    std::vector<float> alpha_last(kRgbW);
+    double alpha_sigma = 1.0;
+    b = 0;
+    for (int l = 0; l < kLayers; ++l) {
+        const int nrows = (l == 8) ? kRgbW + 1 : kWidth;
+        const int K = padded_k(l);
+        // operand scale of layer l's accumulator: the layer's main input
+        const double s_acc = (l == 0) ? sa[0] : sa[l];
+        // weight scales: one per trunk layer (the epilogue multiplies by a
+        // single alpha), one per row of the last layer (applied in FP32)
+        std::vector<double> sw(nrows, 1.0);
+        double lmax = 0.0;
+        for (int n = 0; n < nrows; ++n) {
+            double mx = 0.0;
+            for (int k = 0; k < K; ++k) mx = fmax(mx, fabs(weight(l, n, k) * s_acc / in_scale(l, k)));
+            sw[n] = mx > 0.0 ? 448.0 / mx : 1.0;
+            lmax = fmax(lmax, mx);
+        }
+        if (l < kDepth)
+            for (int n = 0; n < nrows; ++n) sw[n] = lmax > 0.0 ? 448.0 / lmax : 1.0;
+        for (int k0 = 0; k0 < K; k0 += 64, ++b)
+            for (int n = 0; n < nrows; ++n)
+                for (int k = 0; k < 64; ++k) {
+                    const int kk = k0 + k;
+                    blk8[((size_t)b * 256 + n) * 64 + k] =
+                        f2e4m3(weight(l, n, kk) * sw[n] * s_acc / in_scale(l, kk));
+                }
+        if (l < kDepth) {
+            // next input scale sa[l + 1]; accumulator = s_acc sw (W . x)
+            st->alpha[l] = (float)(sa[l + 1] / (s_acc * sw[0]));
+            for (int n = 0; n < kWidth; ++n) beta[(size_t)l * kWidth + n] = (float)(bp[l][n] * sa[l + 1]);
+        } else {
+            for (int n = 0; n < kRgbW; ++n) alpha_last[n] = (float)(1.0 / (s_acc * sw[n]));
+            alpha_sigma = 1.0 / (s_acc * sw[kRgbW]);
         }
     }
-    // last layer, N = 144: rows 0..127 RGB hidden (folded), row 128 density head
-    for (int k0 = 0; k0 < kWidth; k0 += 32, ++b) {
-        auto get = [&](int n, int k) -> double { return Wfold[(size_t)n * kWidth + k]; };
-        put_chunk(b, 0, 128, get, k0);
-        auto gets = [&](int n, int k) -> double { (void)n; return (double)Wp[8][k]; };
-        put_chunk(b, 128, 1, gets, k0);
-    }
-    if (b != kBlocksPerPair) return fail(MCL_ERR_UNSUPPORTED, "internal: weight block count %d", b);
-    // ---- aux: trunk biases as BF16 pairs [8][128] (bit patterns stored in
-    //      floats), w_out [3][128], W_d [128][27], b' [128]
+    if (b != nb8) return fail(MCL_ERR_UNSUPPORTED, "internal: FP8 weight block count %d", b);
+    // ---- aux: BF16 trunk biases as pairs [8][128] (bit patterns stored in
+    //      floats), FP8 beta [8][256], FP8 alpha of the RGB
+    //      hidden layer [128], w_out [3][128], W_d [128][27], b' [128]
     std::vector<float> aux;
     const size_t o_bias = aux.size();
     for (int l = 0; l < kDepth; ++l)
@@ -533,6 +770,10 @@ int mlp_tc_prepare(mcl_map* m, const float* blob) {
             memcpy(&f, &pr, 4);
             aux.push_back(f);
         }
+    const size_t o_beta = aux.size();
+    aux.insert(aux.end(), beta.begin(), beta.end());
+    const size_t o_al = aux.size();
+    aux.insert(aux.end(), alpha_last.begin(), alpha_last.end());
     const size_t o_wout = aux.size();
     aux.insert(aux.end(), Wp[11], Wp[11] + 3 * kRgbW);
     const size_t o_wd = aux.size();
@@ -542,42 +783,44 @@ int mlp_tc_prepare(mcl_map* m, const float* blob) {
     for (int o = 0; o < kRgbW; ++o) aux.push_back((float)bfold[o]);
     st->b_sigma = bp[8][0];
     for (int c = 0; c < 3; ++c) st->b_out[c] = bp[11][c];
+    st->alpha_sigma = (float)alpha_sigma;
+    st->s_gx = (float)sa[0];
 
     int rc;
-    if ((rc = cuda_check(cudaMalloc(&st->wblocks, blk.size() * 2), "cudaMalloc(tc weights)"))) return rc;
-    if ((rc = cuda_check(cudaMemcpy(st->wblocks, blk.data(), blk.size() * 2, cudaMemcpyHostToDevice),
-                         "upload tc weights")))
+    if ((rc = cuda_check(cudaMalloc(&st->bf16.wblocks, blk.size() * 2), "cudaMalloc(tc weights)")) ||
+        (rc = cuda_check(cudaMemcpy(st->bf16.wblocks, blk.data(), blk.size() * 2,
+                                    cudaMemcpyHostToDevice),
+                         "upload tc weights")) ||
+        (rc = cuda_check(cudaMalloc(&st->fp8.wblocks, blk8.size()), "cudaMalloc(fp8 weights)")) ||
+        (rc = cuda_check(cudaMemcpy(st->fp8.wblocks, blk8.data(), blk8.size(), cudaMemcpyHostToDevice),
+                         "upload fp8 weights")) ||
+        (rc = cuda_check(cudaMalloc(&st->aux, aux.size() * 4), "cudaMalloc(tc aux)")) ||
+        (rc = cuda_check(cudaMemcpy(st->aux, aux.data(), aux.size() * 4, cudaMemcpyHostToDevice),
+                         "upload tc aux")) ||
+        (rc = cuda_check(cudaMalloc(&st->ray_bias, (size_t)m->cfg.max_rays * 128 * 4), "ray bias")) ||
+        (rc = cuda_check(cudaMalloc(&st->abort_flag, sizeof(int)), "abort flag")))
         return rc;
-    if ((rc = cuda_check(cudaMalloc(&st->aux, aux.size() * 4), "cudaMalloc(tc aux)"))) return rc;
-    if ((rc = cuda_check(cudaMemcpy(st->aux, aux.data(), aux.size() * 4, cudaMemcpyHostToDevice),
-                         "upload tc aux")))
-        return rc;
-    if ((rc = cuda_check(cudaMalloc(&st->ray_bias, (size_t)m->cfg.max_rays * 128 * 4), "ray bias")))
-        return rc;
-    if ((rc = cuda_check(cudaMalloc(&st->abort_flag, sizeof(int)), "abort flag"))) return rc;
     st->bias2 = reinterpret_cast<const uint32_t*>(st->aux + o_bias);
+    st->beta = st->aux + o_beta;
+    st->alpha_last = st->aux + o_al;
     st->w_out = st->aux + o_wout;
     st->Wd = st->aux + o_wd;
     st->bprime = st->aux + o_bp;
 
-    // ---- tensor map over the weight blocks: [64*256 rows][32] bf16, box 32 x 256
+    // ---- tensor maps over the weight blocks: [blocks*256 rows][64 bytes],
+    //      box = one block, 64-byte swizzle
     PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
     cudaDriverEntryPointQueryResult qr;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", (void**)&encode, 12000,
                                          cudaEnableDefault, &qr) != cudaSuccess ||
         qr != cudaDriverEntryPointSuccess || !encode) {
         cudaGetLastError();
-        // no driver (CPU-only machine): the tensor-core form stays unavailable
+        // no driver (CPU-only machine): the tensor-core forms stay unavailable
         return MCL_OK;
     }
-    cuuint64_t dims[2] = {32, (cuuint64_t)kBlocksPerPair * 256};
-    cuuint64_t strides[1] = {64};
-    cuuint32_t box[2] = {32, 256};
-    cuuint32_t es[2] = {1, 1};
-    CUresult r = encode(&st->tmap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, st->wblocks, dims, strides,
-                        box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
-                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) return fail(MCL_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    if ((rc = make_tmap(st->bf16, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 32, nb16, encode)) ||
+        (rc = make_tmap(st->fp8, CU_TENSOR_MAP_DATA_TYPE_UINT8, 64, nb8, encode)))
+        return rc;
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&st->n_sm, cudaDevAttrMultiProcessorCount, dev);
@@ -585,18 +828,24 @@ int mlp_tc_prepare(mcl_map* m, const float* blob) {
     cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
     cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
     if (major != 10 || minor != 3) return MCL_OK;  // kernels are built for sm_103a only
-    if ((rc = cuda_check(cudaFuncSetAttribute(k_mlp_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              (int)kSmemBytes),
+    if ((rc = cuda_check(cudaFuncSetAttribute(k_mlp_tc<false>,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)Form<false>::kSmemBytes),
+                         "smem attribute")) ||
+        (rc = cuda_check(cudaFuncSetAttribute(k_mlp_tc<true>,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)Form<true>::kSmemBytes),
                          "smem attribute")))
         return rc;
-    st->ready = true;
+    st->bf16.ready = st->fp8.ready = true;
     return MCL_OK;
 }
 
 void mlp_tc_free(mcl_map* m) {
     TcState* st = (TcState*)m->tc_aux;
     if (!st) return;
-    if (st->wblocks) cudaFree(st->wblocks);
+    if (st->bf16.wblocks) cudaFree(st->bf16.wblocks);
+    if (st->fp8.wblocks) cudaFree(st->fp8.wblocks);
     if (st->aux) cudaFree(st->aux);
     if (st->ray_bias) cudaFree(st->ray_bias);
     if (st->abort_flag) cudaFree(st->abort_flag);
@@ -604,9 +853,12 @@ void mlp_tc_free(mcl_map* m) {
     m->tc_aux = nullptr;
 }
 
-bool mlp_tc_available(const mcl_map* m) {
+bool mlp_tc_available(const mcl_map* m, int precision) {
     const TcState* st = (const TcState*)m->tc_aux;
-    return st && st->ready;
+    if (!st) return false;
+    if (precision == MCL_PREC_BF16) return st->bf16.ready;
+    if (precision == MCL_PREC_FP8) return st->fp8.ready;
+    return false;
 }
 
 cudaError_t mlp_tc_ray_bias(mcl_map* m, const float* gd, int n_rays, const int* n_rays_dev,
@@ -623,7 +875,7 @@ cudaError_t mlp_tc(mcl_map* m, int precision, const Ray* rays, const float* gd, 
                    int S, int n_rays, const int* rows_dev, float4* out, cudaStream_t s) {
     (void)gd;
     TcState* st = (TcState*)m->tc_aux;
-    if (!st || !st->ready || precision != MCL_PREC_BF16) return cudaErrorNotSupported;
+    if (!mlp_tc_available(m, precision)) return cudaErrorNotSupported;
     Params p;
     p.rays = rays;
     p.z = z;
@@ -632,6 +884,11 @@ cudaError_t mlp_tc(mcl_map* m, int precision, const Ray* rays, const float* gd, 
     p.n_pairs = (p.M + 255) / 256;
     p.M_dev = rows_dev;
     p.bias2 = st->bias2;
+    p.beta = st->beta;
+    for (int l = 0; l < 8; ++l) p.alpha[l] = st->alpha[l];
+    p.alpha_last = st->alpha_last;
+    p.alpha_sigma = st->alpha_sigma;
+    p.s_gx = st->s_gx;
     p.b_sigma = st->b_sigma;
     p.ray_bias = st->ray_bias;
     p.w_out = st->w_out;
@@ -645,7 +902,12 @@ cudaError_t mlp_tc(mcl_map* m, int precision, const Ray* rays, const float* gd, 
     if (e) return e;
     const long long grid = p.n_pairs < st->n_sm ? p.n_pairs : st->n_sm;
     note_launch();
-    k_mlp_tc<<<(unsigned)grid, kThreads, kSmemBytes, s>>>(st->tmap, p);
+    if (precision == MCL_PREC_FP8)
+        k_mlp_tc<true><<<(unsigned)grid, Form<true>::kThreads, Form<true>::kSmemBytes, s>>>(
+            st->fp8.tmap, p);
+    else
+        k_mlp_tc<false><<<(unsigned)grid, Form<false>::kThreads, Form<false>::kSmemBytes, s>>>(
+            st->bf16.tmap, p);
     return cudaGetLastError();
 }
 
