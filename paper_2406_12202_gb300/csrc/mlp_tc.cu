@@ -1,24 +1,29 @@
 // mlp_tc.cu -- the NeRF MLP on the 5th-generation tensor cores (tcgen05,
-// BF16 operands, FP32 accumulation in TMEM), fused across all layers.
+// FP32 accumulation in TMEM), fused across all layers, in two operand
+// forms: BF16, and FP8 (E4M3 with calibrated scales).
 //
 // One persistent CTA per SM walks over pairs of 128-row tiles (rows are the
 // samples of the pass, row = ray * S + k).  Per pair:
-//   prologue   x = o + z d, gamma(x) (63 -> 64, BF16) into shared memory;
+//   prologue   x = o + z d, gamma(x) (63 -> 64) into shared memory;
 //   9 layers   trunk 1..8 (ReLU; gamma(x) re-enters layer 6 through the skip),
 //              then the RGB hidden layer with the feature layer folded in
 //              (W' = W_rgb_hidden[:, :256] W_feature, computed in FP64 when
-//              the map is loaded: the feature layer has no activation);
-//   epilogues  TMEM -> registers, bias + ReLU, BF16 back into the same
-//              shared-memory tile as the next layer's A operand; the density
-//              head (256 -> 1) as a per-row dot product after trunk layer 8;
-//              the RGB output layer (128 -> 3, sigmoid) after the last MMA,
-//              with gamma(d)'s contribution added as a per-ray bias.
-// Warp roles: warp 0 streams weight blocks [256 x 32] (64-byte swizzle) by
-// TMA through a 4-stage ring; warp 1 allocates TMEM and issues the MMAs for
-// both tiles from the same weight block (M = 128, N = 256, K = 16 per
-// instruction); warps 2-5 and 6-9 run prologue and epilogues of tile 0 and
-// tile 1 (one warp per TMEM lane quadrant, one thread per row).  Every wait
-// is bounded (see tc_ptx.cuh).
+//              the map is loaded: the feature layer has no activation) and
+//              the density head as its row 128;
+//   epilogues  TMEM -> registers, bias + ReLU (and the FP8 scales), back
+//              into the same shared-memory tile as the next layer's A
+//              operand; after the last MMA the RGB output layer (128 -> 3,
+//              sigmoid) with gamma(d)'s contribution added as a per-ray bias.
+// Warp roles: warp 0 streams weight blocks (256 rows x 64 bytes, stored in
+// global memory already in the 64-byte-swizzled shared-memory layout) with
+// contiguous bulk copies through a ring; warp 1 allocates TMEM and issues
+// the MMAs (M = 128, N = 256, 32 bytes of K per instruction); the other warps
+// run prologue and epilogues, 4 (BF16) or 8 (FP8) per tile, one warp per TMEM
+// lane quadrant and column half, one thread per row.  BF16 runs the two
+// tiles in lockstep, each weight block serving both at once; FP8 staggers
+// them (tile 1 runs a layer on the resident blocks after tile 0), so each
+// tile's epilogue overlaps the other's MMAs.  Every wait is bounded (see
+// tc_ptx.cuh).
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_fp8.h>
@@ -92,6 +97,7 @@ __constant__ int c_chunks[2][kLayers] = {{2, 8, 8, 8, 8, 10, 8, 8, 8},
                                          {1, 4, 4, 4, 4, 5, 4, 4, 4}};
 
 struct Params {
+    const uint8_t* wblocks; // weight blocks of the form, pre-swizzled, in consumption order
     const Ray* rays;
     const float* z;
     int S;
@@ -226,7 +232,7 @@ __device__ __forceinline__ void rgb_group(const uint32_t (&v)[32], const float4*
 
 template <bool F8>
 __global__ void __launch_bounds__(Form<F8>::kThreads, 1)
-    k_mlp_tc(const __grid_constant__ CUtensorMap tmap, const Params p) {
+    k_mlp_tc(const __grid_constant__ Params p) {
     using Fm = Form<F8>;
     constexpr int kStages = Fm::kStages;
     constexpr uint32_t kActBytes = Fm::kActBytes;
@@ -253,7 +259,6 @@ __global__ void __launch_bounds__(Form<F8>::kThreads, 1)
         }
         mbar_init(smem_u32(&bars.drain), 1);
         fence_mbar_init();
-        tma_prefetch_desc(&tmap);
     }
     if (warp == 1) {
         tmem_alloc(smem_u32(&bars.tmem_base), 512);
@@ -279,8 +284,8 @@ __global__ void __launch_bounds__(Form<F8>::kThreads, 1)
                     }
                     TC_TRACE(1, g);
                     mbar_arrive_expect_tx(smem_u32(&bars.full[st]), kStageBytes);
-                    tma_load_2d(s_ring + st * kStageBytes, &tmap, 0, b * 256,
-                                smem_u32(&bars.full[st]));
+                    bulk_load(s_ring + st * kStageBytes, p.wblocks + (size_t)b * kStageBytes,
+                              kStageBytes, smem_u32(&bars.full[st]));
                 }
             }
             if (!ok) record_abort(p);
@@ -300,55 +305,92 @@ __global__ void __launch_bounds__(Form<F8>::kThreads, 1)
             const uint32_t id256 = F8 ? idesc_e4m3(128, 256) : idesc_bf16(128, 256);
             const uint32_t id144 = F8 ? idesc_e4m3(128, 144) : idesc_bf16(128, 144);
             int tl = 0;
+            // A operand (shared-memory address) of tile s, chunk c, K step kk
+            // of layer l; K steps are 32 bytes (16 BF16 or 32 E4M3 values)
+            auto a_operand = [&](int l, int s, int c, int kk) -> uint32_t {
+                if (l == 0) return s_gx + s * kGxBytes + (c * 2 + kk) * 32;
+                if (l == 5 && c >= Fm::kActChunks)
+                    return s_gx + s * kGxBytes + ((c - Fm::kActChunks) * 2 + kk) * 32;
+                const int ks = c * 2 + kk;
+                return s_act + s * kActBytes + (ks >> 2) * 16384 + (ks & 3) * 32;
+            };
+            auto issue = [&](int l, int s, int c, uint32_t st, uint32_t idesc) {
+#pragma unroll
+                for (int kk = 0; kk < 2; ++kk) {
+                    const uint64_t ad = smem_desc(a_operand(l, s, c, kk), 1024, kLayoutSw128);
+                    const uint64_t bd =
+                        smem_desc(s_ring + st * kStageBytes + kk * 32, 512, kLayoutSw64);
+                    if constexpr (F8)
+                        mma_f8(tmem + s * 256, ad, bd, idesc, (c | kk) ? 1u : 0u);
+                    else
+                        mma_bf16(tmem + s * 256, ad, bd, idesc, (c | kk) ? 1u : 0u);
+                }
+            };
             for (long long pr = blockIdx.x; pr < n_pairs && ok; pr += gridDim.x) {
                 for (int l = 0; l < kLayers && ok; ++l, ++tl) {
                     const int nch = c_chunks[F8 ? 1 : 0][l];
                     const uint32_t idesc = (l == 8) ? id144 : id256;
                     TC_TRACE(2, tl);
-                    for (int c = 0; c < nch && ok; ++c) {
-                        const uint32_t st = g % kStages, ph = (g / kStages) & 1u;
-                        TC_TRACE(15, g);
-                        if (!mbar_wait(smem_u32(&bars.full[st]), ph, abort_flag)) {
-                            ok = false;
-                            break;
-                        }
-                        TC_TRACE(13, g);
-                        tc_fence_after();
-                        for (int s = 0; s < 2; ++s) {
-                            if (c == 0) {
-                                if (!mbar_wait(smem_u32(&bars.a_ready[s]), rdy_ph[s], abort_flag)) {
-                                    ok = false;
-                                    break;
-                                }
-                                TC_TRACE(3 + s, tl);
-                                rdy_ph[s] ^= 1u;
-                                tc_fence_after();
+                    if constexpr (F8) {
+                        // Staggered tiles: all of layer l for tile 0, then all
+                        // of it for tile 1 from the same resident weight
+                        // blocks (a layer is at most 5 of the 8 stages), so
+                        // tile 0's epilogue runs under tile 1's MMAs and vice
+                        // versa.  A stage is released after tile 1's MMAs.
+                        for (int s = 0; s < 2 && ok; ++s) {
+                            if (!mbar_wait(smem_u32(&bars.a_ready[s]), rdy_ph[s], abort_flag)) {
+                                ok = false;
+                                break;
                             }
-#pragma unroll
-                            for (int kk = 0; kk < 2; ++kk) {
-                                // K steps are 32 bytes (16 BF16 or 32 E4M3 values)
-                                uint32_t a_addr;
-                                if (l == 0) {
-                                    a_addr = s_gx + s * kGxBytes + (c * 2 + kk) * 32;
-                                } else if (l == 5 && c >= Fm::kActChunks) {
-                                    a_addr = s_gx + s * kGxBytes + ((c - Fm::kActChunks) * 2 + kk) * 32;
-                                } else {
-                                    const int ks = c * 2 + kk;
-                                    a_addr = s_act + s * kActBytes + (ks >> 2) * 16384 + (ks & 3) * 32;
+                            TC_TRACE(3 + s, tl);
+                            rdy_ph[s] ^= 1u;
+                            tc_fence_after();
+                            for (int c = 0; c < nch; ++c) {
+                                const uint32_t gc = g + c;
+                                const uint32_t st = gc % kStages, ph = (gc / kStages) & 1u;
+                                if (s == 0) {
+                                    TC_TRACE(15, gc);
+                                    if (!mbar_wait(smem_u32(&bars.full[st]), ph, abort_flag)) {
+                                        ok = false;
+                                        break;
+                                    }
+                                    TC_TRACE(13, gc);
                                 }
-                                const uint64_t ad = smem_desc(a_addr, 1024, kLayoutSw128);
-                                const uint64_t bd =
-                                    smem_desc(s_ring + st * kStageBytes + kk * 32, 512, kLayoutSw64);
-                                if constexpr (F8)
-                                    mma_f8(tmem + s * 256, ad, bd, idesc, (c | kk) ? 1u : 0u);
-                                else
-                                    mma_bf16(tmem + s * 256, ad, bd, idesc, (c | kk) ? 1u : 0u);
+                                issue(l, s, c, st, idesc);
+                                if (s == 1) mma_commit(smem_u32(&bars.empty[st]));
                             }
-                            if (c == nch - 1) mma_commit(smem_u32(&bars.acc_full[s]));
+                            if (!ok) break;
+                            mma_commit(smem_u32(&bars.acc_full[s]));
                         }
-                        if (!ok) break;
-                        mma_commit(smem_u32(&bars.empty[st]));
-                        ++g;
+                        g += nch;
+                    } else {
+                        // Lockstep tiles: each weight block serves both tiles
+                        // at once (a BF16 layer does not fit in the ring).
+                        for (int c = 0; c < nch && ok; ++c) {
+                            const uint32_t st = g % kStages, ph = (g / kStages) & 1u;
+                            TC_TRACE(15, g);
+                            if (!mbar_wait(smem_u32(&bars.full[st]), ph, abort_flag)) {
+                                ok = false;
+                                break;
+                            }
+                            TC_TRACE(13, g);
+                            for (int s = 0; s < 2; ++s) {
+                                if (c == 0) {
+                                    if (!mbar_wait(smem_u32(&bars.a_ready[s]), rdy_ph[s], abort_flag)) {
+                                        ok = false;
+                                        break;
+                                    }
+                                    TC_TRACE(3 + s, tl);
+                                    rdy_ph[s] ^= 1u;
+                                    tc_fence_after();
+                                }
+                                issue(l, s, c, st, idesc);
+                                if (c == nch - 1) mma_commit(smem_u32(&bars.acc_full[s]));
+                            }
+                            if (!ok) break;
+                            mma_commit(smem_u32(&bars.empty[st]));
+                            ++g;
+                        }
                     }
                     TC_TRACE(5, tl);
                 }
@@ -439,14 +481,6 @@ __global__ void __launch_bounds__(Form<F8>::kThreads, 1)
                 if (tracer) TC_TRACE(6 + 2 * slot, tl);
                 acc_ph ^= 1u;
                 tc_fence_after();
-#ifdef MCL_EXP_NO_EPI
-                if (l < 8) {
-                    fence_proxy_async_smem();
-                    tc_fence_before();
-                    mbar_arrive(bar_ready);
-                    continue;
-                }
-#endif
                 if (l < 8) {
                     // this thread's columns, 32 at a time, the next TMEM load
                     // in flight while the current group is stored
@@ -556,8 +590,7 @@ __global__ void k_ray_bias(const float* __restrict__ gd, int n_rays, const int* 
 }
 
 struct TcForm {
-    CUtensorMap tmap;
-    void* wblocks = nullptr;   // weight blocks in consumption order
+    uint8_t* wblocks = nullptr;  // weight blocks in consumption order, 64-byte swizzled
     bool ready = false;
 };
 
@@ -630,19 +663,6 @@ void calibrate(const float* const* Wp, const float* const* bp, const int* fin,
                 for (int i = 0; i < kGx; ++i) h[kWidth + i] = gx[i];
         }
     }
-}
-
-int make_tmap(TcForm& f, CUtensorMapDataType dt, cuuint64_t inner, int n_blocks,
-              PFN_cuTensorMapEncodeTiled_v12000 encode) {
-    cuuint64_t dims[2] = {inner, (cuuint64_t)n_blocks * 256};
-    cuuint64_t strides[1] = {64};
-    cuuint32_t box[2] = {(cuuint32_t)inner, 256};
-    cuuint32_t es[2] = {1, 1};
-    CUresult r = encode(&f.tmap, dt, 2, f.wblocks, dims, strides, box, es,
-                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
-                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) return fail(MCL_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
-    return MCL_OK;
 }
 
 }  // namespace
@@ -786,13 +806,24 @@ int mlp_tc_prepare(mcl_map* m, const float* blob) {
     st->alpha_sigma = (float)alpha_sigma;
     st->s_gx = (float)sa[0];
 
+    // blocks of 256 rows x 64 bytes are stored as the 64-byte swizzle lays
+    // them out in shared memory, so one contiguous bulk copy fills a stage
+    auto swizzle = [](const uint8_t* src, size_t n_blocks) {
+        std::vector<uint8_t> out(n_blocks * kStageBytes);
+        for (size_t b = 0; b < n_blocks; ++b)
+            for (uint32_t r = 0; r < 256; ++r)
+                for (uint32_t c = 0; c < 64; ++c)
+                    out[b * kStageBytes + sw64_offset(r, c)] = src[b * kStageBytes + r * 64 + c];
+        return out;
+    };
+    const std::vector<uint8_t> sw16 = swizzle(reinterpret_cast<const uint8_t*>(blk.data()), nb16);
+    const std::vector<uint8_t> sw8 = swizzle(blk8.data(), nb8);
     int rc;
-    if ((rc = cuda_check(cudaMalloc(&st->bf16.wblocks, blk.size() * 2), "cudaMalloc(tc weights)")) ||
-        (rc = cuda_check(cudaMemcpy(st->bf16.wblocks, blk.data(), blk.size() * 2,
-                                    cudaMemcpyHostToDevice),
+    if ((rc = cuda_check(cudaMalloc(&st->bf16.wblocks, sw16.size()), "cudaMalloc(tc weights)")) ||
+        (rc = cuda_check(cudaMemcpy(st->bf16.wblocks, sw16.data(), sw16.size(), cudaMemcpyHostToDevice),
                          "upload tc weights")) ||
-        (rc = cuda_check(cudaMalloc(&st->fp8.wblocks, blk8.size()), "cudaMalloc(fp8 weights)")) ||
-        (rc = cuda_check(cudaMemcpy(st->fp8.wblocks, blk8.data(), blk8.size(), cudaMemcpyHostToDevice),
+        (rc = cuda_check(cudaMalloc(&st->fp8.wblocks, sw8.size()), "cudaMalloc(fp8 weights)")) ||
+        (rc = cuda_check(cudaMemcpy(st->fp8.wblocks, sw8.data(), sw8.size(), cudaMemcpyHostToDevice),
                          "upload fp8 weights")) ||
         (rc = cuda_check(cudaMalloc(&st->aux, aux.size() * 4), "cudaMalloc(tc aux)")) ||
         (rc = cuda_check(cudaMemcpy(st->aux, aux.data(), aux.size() * 4, cudaMemcpyHostToDevice),
@@ -807,20 +838,6 @@ int mlp_tc_prepare(mcl_map* m, const float* blob) {
     st->Wd = st->aux + o_wd;
     st->bprime = st->aux + o_bp;
 
-    // ---- tensor maps over the weight blocks: [blocks*256 rows][64 bytes],
-    //      box = one block, 64-byte swizzle
-    PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
-    cudaDriverEntryPointQueryResult qr;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", (void**)&encode, 12000,
-                                         cudaEnableDefault, &qr) != cudaSuccess ||
-        qr != cudaDriverEntryPointSuccess || !encode) {
-        cudaGetLastError();
-        // no driver (CPU-only machine): the tensor-core forms stay unavailable
-        return MCL_OK;
-    }
-    if ((rc = make_tmap(st->bf16, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 32, nb16, encode)) ||
-        (rc = make_tmap(st->fp8, CU_TENSOR_MAP_DATA_TYPE_UINT8, 64, nb8, encode)))
-        return rc;
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&st->n_sm, cudaDevAttrMultiProcessorCount, dev);
@@ -877,6 +894,7 @@ cudaError_t mlp_tc(mcl_map* m, int precision, const Ray* rays, const float* gd, 
     TcState* st = (TcState*)m->tc_aux;
     if (!mlp_tc_available(m, precision)) return cudaErrorNotSupported;
     Params p;
+    p.wblocks = precision == MCL_PREC_FP8 ? st->fp8.wblocks : st->bf16.wblocks;
     p.rays = rays;
     p.z = z;
     p.S = S;
@@ -903,11 +921,9 @@ cudaError_t mlp_tc(mcl_map* m, int precision, const Ray* rays, const float* gd, 
     const long long grid = p.n_pairs < st->n_sm ? p.n_pairs : st->n_sm;
     note_launch();
     if (precision == MCL_PREC_FP8)
-        k_mlp_tc<true><<<(unsigned)grid, Form<true>::kThreads, Form<true>::kSmemBytes, s>>>(
-            st->fp8.tmap, p);
+        k_mlp_tc<true><<<(unsigned)grid, Form<true>::kThreads, Form<true>::kSmemBytes, s>>>(p);
     else
-        k_mlp_tc<false><<<(unsigned)grid, Form<false>::kThreads, Form<false>::kSmemBytes, s>>>(
-            st->bf16.tmap, p);
+        k_mlp_tc<false><<<(unsigned)grid, Form<false>::kThreads, Form<false>::kSmemBytes, s>>>(p);
     return cudaGetLastError();
 }
 

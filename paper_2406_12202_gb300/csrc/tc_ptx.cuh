@@ -115,6 +115,25 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* m, 
         : "memory");
 }
 
+// Contiguous bulk copy (TMA engine, no tensor map) of `bytes` (a multiple of
+// 16; both addresses 16-byte aligned) from global to shared memory,
+// completing on `bar`.
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes,
+                                          uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            dst),
+        "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(bar)
+        : "memory");
+}
+
+// Byte offset of (row, byte) in a block of 64-byte rows laid out with the
+// 64-byte swizzle (16-byte chunk index XOR (row / 2) mod 4, i.e. address
+// bits [4, 6) XOR bits [7, 9)); the block base must be 1024-byte aligned.
+__host__ __device__ constexpr uint32_t sw64_offset(uint32_t row, uint32_t byte) {
+    return (row * 64u + byte) ^ ((((row * 64u + byte) >> 7) & 3u) << 4);
+}
+
 // Make generic-proxy writes to shared memory visible to the async proxy
 // (tensor-core operand reads).
 __device__ __forceinline__ void fence_proxy_async_smem() {
