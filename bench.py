@@ -188,6 +188,214 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------- further workloads
+def _pct(v, q):
+    v = sorted(v)
+    if not v:
+        return None
+    k = min(len(v) - 1, max(0, int(round(q / 100.0 * (len(v) - 1)))))
+    return v[k]
+
+
+def _pose_error(est, gt_xyz, gt_yaw):
+    d = math.sqrt(sum((est[i] - gt_xyz[i]) ** 2 for i in range(3)))
+    y = abs((est[3] - gt_yaw + math.pi) % (2 * math.pi) - math.pi)
+    return d, math.degrees(y)
+
+
+def _update_latencies(recs):
+    """Per-update latencies (ms) from the iteration start times of a run."""
+    t = [r["t_start_ns"] for r in recs]
+    return [(b - a) / 1e6 for a, b in zip(t[:-1], t[1:])]
+
+
+def run_coarse_to_fine(M, img, K, seed, prec, fp32_replay=True):
+    """Three levels (100, 200, 400 px wide: factors 4, 2, 1) with 16 / 32 /
+    64 pixels, 1500 initial particles, survivors after rejection decide the
+    next count, 20 MCL iterations with sigma_t = sigma_yaw = 0.05, one
+    device-driven run under a CUDA graph.  The plain FP32 form is timed on
+    the same sequence of (particles, pixels, level) through mcl_update."""
+    import numpy as np
+    import torch
+    import synth
+    N0, iters = 1500, 20
+    gm = M.Map(synth.he_init_weights(0), max_rays=N0 * 64, max_samples=192, max_particles=N0,
+               max_queries=1)
+    P = torch.tensor(synth.random_particles(seed + 1, N0)[0], dtype=torch.float32,
+                     device="cuda").reshape(1, N0, 12)
+    _, gxyz, gyaw = synth.gt_pose(seed)
+    sch = M.schedule([0, 1, 2], [16, 32, 64], [N0, 1000, 600], n_min=100, iter_caps=[7, 7, 6],
+                     refine=[0.05, 0.01, 0.0], iterations=iters, sigma_t=0.05, sigma_yaw=0.05)
+    opts = M.UpdateOptions(n_coarse=64, n_fine=128, precision=prec, seed=seed)
+    gm.localize(P.clone(), [N0], [img], K, sch, opts, use_graph=True)      # build + warm
+    torch.cuda.synchronize()
+    Pw = P.clone()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    log, fin = gm.localize(Pw, [N0], [img], K, sch, opts, use_graph=True)
+    b.record()
+    torch.cuda.synchronize()
+    total = a.elapsed_time(b)
+    recs = M.Map.decode_log(log, 1, iters)[0]
+    lat = _update_latencies(recs)
+    perr, yerr = _pose_error(recs[-1]["est"], gxyz, gyaw)
+    out = {"workload": "coarse-to-fine: 3 levels (1/4, 1/2, 1 of 400x400) x 16/32/64 px, "
+                       "1500 initial particles, 20 iterations, 64+128 samples",
+           "precision": prec, "run_ms": total, "ms_per_update": total / iters,
+           "update_ms_p50": _pct(lat, 50), "update_ms_p99": _pct(lat, 99),
+           "particles_per_iteration": [r["n_particles"] for r in recs],
+           "levels": [r["level"] for r in recs],
+           "final_position_error": perr, "final_yaw_error_deg": yerr,
+           "note": "seeded He-init map: a high-frequency random field, so pose error is "
+                   "reported, not expected to be small"}
+    if fp32_replay:
+        o32 = M.UpdateOptions(n_coarse=64, n_fine=128, precision="fp32")
+        Pf = P.reshape(N0, 12)
+        e32 = []
+        for t, r in enumerate(recs):
+            n, B, lev = r["n_particles"], r["n_pixels"], r["level"]
+            f = 4 >> lev
+            px = M.draw_pixels(img.shape[1] // f, img.shape[0] // f, B, seed, t)
+            x, y = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            x.record()
+            gm.update(Pf[:n].contiguous(), img, K, lev, px, o32)
+            y.record()
+            torch.cuda.synchronize()
+            e32.append(x.elapsed_time(y))
+        out["fp32_form_ms_per_update_same_sizes"] = sum(e32) / len(e32)
+        out["speedup_vs_fp32_form"] = out["fp32_form_ms_per_update_same_sizes"] / out["ms_per_update"]
+    gm.close()
+    return out
+
+
+def run_proposal_fp8(M, gm, img, K, seed, steps, warmup, wl):
+    """Learned proposal + FP8 MLP on the full-update workload: the proposal
+    (4 x 64, gamma with 6 frequencies) is distilled on the GPU from the
+    64 + 128 FP32 sampler over 2000 seeded poses x 64 pixels (128,000 rays,
+    64 bins); then 64 proposal samples -> 32 guided + 32 importance samples
+    per ray through the FP8 MLP.  Accuracy against the FP32 full sampler on
+    the same particles and pixels."""
+    import numpy as np
+    import torch
+    import synth
+    N, Bpx, W, H = wl["N"], wl["B"], wl["W"], wl["H"]
+    Ptr = torch.tensor(synth.random_particles(seed + 77, 2000)[0], dtype=torch.float32, device="cuda")
+    pxtr = torch.tensor(synth.pixel_set(seed + 78, W, H, Bpx), dtype=torch.int32, device="cuda")
+    gm.proposal_set(synth.proposal_init_weights(0))
+    full32 = M.UpdateOptions(n_coarse=64, n_fine=128, precision="fp32")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    losses = gm.proposal_train(Ptr, pxtr, K, wl["level"], full32, epochs=8, batch_rays=4096,
+                               n_bins=64, lr=3e-3, lr_end=1e-4, seed=seed)
+    train_s = time.perf_counter() - t0
+    prop = M.UpdateOptions(n_coarse=64, n_fine=32, precision="fp8", use_proposal=True,
+                           n_proposal=64, n_guided=32)
+    P = torch.tensor(synth.random_particles(seed, N)[0], dtype=torch.float32, device="cuda")
+    pxs = [torch.tensor(synth.pixel_set(seed + 7 * t, W, H, Bpx), dtype=torch.int32, device="cuda")
+           for t in range(steps + warmup)]
+    out = {"logw": torch.empty(N, device="cuda"), "w": torch.empty(N, dtype=torch.float64, device="cuda"),
+           "mask": torch.empty(N, dtype=torch.uint8, device="cuda")}
+    idx = torch.empty(N, dtype=torch.int32, device="cuda")
+    Pn = torch.empty_like(P)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    ms = []
+    for t in range(warmup + steps):
+        if t == warmup:
+            gm.profile_read(reset=True)
+            gm.profile(True)
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        gm.update(P, img, K, wl["level"], pxs[t], prop, out=out)
+        gm.resample(out["w"], N, 0.5, idx=idx)
+        M.predict(P, idx, N, wl["sigma_t"], wl["sigma_yaw"], seed, t, out=Pn)
+        b.record()
+        torch.cuda.synchronize()
+        if t >= warmup:
+            ms.append(a.elapsed_time(b))
+    phases, _ = gm.profile_read(reset=True)
+    gm.profile(False)
+    # accuracy against the FP32 full sampler (same particles, pixel set 0)
+    g = gm.update(P, img, K, wl["level"], pxs[0], prop, debug=True)
+    r = gm.update(P, img, K, wl["level"], pxs[0], full32, debug=True)
+    torch.cuda.synchronize()
+    from scipy.stats import spearmanr
+    e = (g["rgb"] - r["rgb"]).abs()
+    lw_g, lw_r = g["logw"].cpu().numpy(), r["logw"].cpu().numpy()
+    fin = np.isfinite(lw_g) & np.isfinite(lw_r)
+    top = len(set(np.argsort(-lw_g)[:10]) & set(np.argsort(-lw_r)[:10]))
+    mean_ms = sum(ms) / len(ms)
+    return {"workload": "learned proposal (64 -> 32 guided + 32 importance) + FP8 MLP, "
+                        "600 particles x 64 px of 400x400",
+            "ms_per_step": mean_ms, "ray_samples_per_s": N * Bpx * 64 / (mean_ms / 1e3),
+            "phases_ms_per_step": {k: v / steps for k, v in phases.items()},
+            "phase_note": "sample = proposal MLP + inverse-CDF sampling; mlp_coarse = NeRF MLP on "
+                          "the guided samples",
+            "train_s": train_s, "train_rays": 2000 * Bpx, "train_loss_first_last": [float(losses[0]), float(losses[-1])],
+            "vs_fp32_full_sampler": {"rgb_mean_abs": float(e.mean()), "rgb_max_abs": float(e.max()),
+                                     "spearman_logw": float(spearmanr(lw_g[fin], lw_r[fin]).correlation),
+                                     "top10_overlap": top}}
+
+
+def run_batched(M, seed, W, H, focal, use_proposal_blob=None):
+    """16 independent queries on one map, N_q ~ U{1000..4000} (seeded), own
+    ground-truth poses, 3 levels (16 / 32 / 64 px), 100 iterations, FP8 MLP
+    with the learned proposal, one CUDA graph for the whole run; per-update
+    latency from the GPU timer at the start of every iteration."""
+    import numpy as np
+    import torch
+    import synth
+    Q, stride, iters = 16, 4000, 100
+    rng = np.random.Generator(np.random.PCG64(seed + 4242))
+    n0 = [int(v) for v in rng.integers(1000, 4001, size=Q)]
+    blob = synth.he_init_weights(0)
+    gm = M.Map(blob, max_rays=Q * stride * 16, max_samples=96, max_particles=Q * stride,
+               max_queries=Q)
+    K = M.intrinsics(focal, focal, W / 2, H / 2, W, H)
+    if use_proposal_blob is not None:
+        gm.proposal_set(use_proposal_blob)
+    # observations: BF16 renders of the full image at each query's ground truth
+    allpx = np.stack(np.meshgrid(np.arange(W), np.arange(H), indexing="xy"), -1).reshape(-1, 2)
+    o16 = M.UpdateOptions(n_coarse=64, n_fine=32, precision="bf16")
+    imgs = []
+    for q in range(Q):
+        gt = torch.tensor(synth.gt_pose(seed + 100 + q)[0][None], dtype=torch.float32, device="cuda")
+        im = torch.empty(H * W, 3, device="cuda")
+        for c0 in range(0, H * W, 40000):
+            pc = torch.tensor(allpx[c0:c0 + 40000], dtype=torch.int32, device="cuda")
+            im[c0:c0 + pc.shape[0]] = gm.render(gt, K, 2, pc, o16)
+        imgs.append(im.reshape(H, W, 3).contiguous())
+    P = torch.zeros(Q, stride, 12, dtype=torch.float32, device="cuda")
+    for q in range(Q):
+        P[q, :n0[q]] = torch.tensor(synth.random_particles(seed + 200 + q, n0[q])[0], dtype=torch.float32)
+    sch = M.schedule([0, 1, 2], [16, 32, 64], [stride, 2000, 500], n_min=64, iter_caps=[34, 33, 33],
+                     refine=[0.05, 0.01, 0.0], iterations=iters, sigma_t=0.05, sigma_yaw=0.05)
+    opts = M.UpdateOptions(n_coarse=64, n_fine=32, precision="fp8", seed=seed,
+                           use_proposal=use_proposal_blob is not None, n_proposal=64, n_guided=32)
+    gm.localize(P.clone(), n0, imgs, K, sch, opts, use_graph=True)        # capture + warm
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    Pw = P.clone()
+    a.record()
+    log, fin = gm.localize(Pw, n0, imgs, K, sch, opts, use_graph=True)
+    b.record()
+    torch.cuda.synchronize()
+    total = a.elapsed_time(b)
+    recs = M.Map.decode_log(log, Q, iters)
+    lat = _update_latencies(recs[0])
+    samples = sum(r["n_particles"] * r["n_pixels"] * 64 for q in range(Q) for r in recs[q])
+    errs = [_pose_error(recs[q][-1]["est"], synth.gt_pose(seed + 100 + q)[1],
+                        synth.gt_pose(seed + 100 + q)[2]) for q in range(Q)]
+    gm.close()
+    return {"workload": "16 queries, N ~ U{1000..4000}, 3 levels x 16/32/64 px of 400x400, "
+                        "100 iterations, FP8 + learned proposal (64 -> 32 + 32), one CUDA graph",
+            "initial_particles": n0, "run_ms": total, "ms_per_batched_update": total / iters,
+            "update_ms_p50": _pct(lat, 50), "update_ms_p99": _pct(lat, 99),
+            "ray_samples_per_s": samples / (total / 1e3),
+            "final_position_error_median": float(np.median([e[0] for e in errs])),
+            "final_yaw_error_deg_median": float(np.median([e[1] for e in errs]))}
+
+
 # --------------------------------------------------------------- GPU arm
 def run_ours(args):
     import numpy as np
@@ -382,6 +590,18 @@ def run_ours(args):
         except Exception as e:  # the baseline must never hide the GPU line
             cpu = {"value": None, "unit": UNIT, "cores": None, "kind": "oracle",
                    "sample": f"failed: {e}"}
+    extra = {}
+    if world == 1 and not args.no_extra:
+        for name, fn in (
+                ("coarse_to_fine", lambda: run_coarse_to_fine(M, img, K, seed, prec)),
+                ("proposal_fp8", lambda: run_proposal_fp8(M, gm, img, K, seed, args.steps,
+                                                          args.warmup, wl)),
+                ("batched_queries", lambda: run_batched(M, seed, W, H, wl["focal"],
+                                                        gm.proposal_get()))):
+            try:
+                extra[name] = fn()
+            except Exception as e:  # an extra workload must never hide the main line
+                extra[name] = {"failed": f"{type(e).__name__}: {e}"}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": sum(ms) / len(ms), "higher_is_better": True,
@@ -402,6 +622,7 @@ def run_ours(args):
                 "d2h_bytes_per_step": bo, "ms_per_step": 1e3 * e2e_t / args.steps},
         "gpu_launches": launches,
         "clocks": clk,
+        "workloads": extra,
     }
     print(json.dumps(line), flush=True)
     if dist is not None:
@@ -417,6 +638,8 @@ def main():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--precision", choices=("auto", "fp32", "bf16", "fp8"), default="auto")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the coarse-to-fine, proposal and batched-query workloads")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -265,6 +265,9 @@ typedef struct {
     int status;            /* particles with a non-finite loss this iteration */
     double spread;         /* weighted trace of the position covariance       */
     double est[4];         /* weighted mean position (x, y, z), circular yaw  */
+    uint64_t t_start_ns;   /* GPU global timer (ns) when the iteration began:
+                              differences of consecutive records are the
+                              per-update latencies of the run               */
 } mcl_iter_record;
 
 /* Run Monte Carlo localisation (Alg. 1 iterated, Sec. III-C schedule) on the
@@ -281,7 +284,11 @@ typedef struct {
  * stay on the device: with use_graph != 0 the run is captured into a CUDA
  * graph on the map's own stream (ordered after earlier work on `stream` and
  * before later work on it) and kept; later calls with the same shapes and
- * pointers relaunch it.  opts->precision must be MCL_PREC_BF16. */
+ * pointers relaunch it.  opts->precision must be a tensor-core form
+ * (MCL_PREC_BF16 or MCL_PREC_FP8); opts->use_proposal selects the learned
+ * sampler.  The map must hold the largest iteration: n_queries * max(max_q
+ * h_n0[q] * n_pixels[0], max_s min(n_cap[s], stride) * n_pixels[s]) <=
+ * max_rays, and n_queries * stride <= max_particles. */
 int mcl_localize(mcl_map* map, int n_queries, float* d_particles, int stride,
                  const int* h_n0, const float* const* h_images,
                  const mcl_intrinsics* K, const mcl_schedule* sch,
@@ -342,6 +349,30 @@ int mcl_proposal_train(mcl_map* map, const float* d_poses, int n_poses,
                        int level, const mcl_opts* sampler_opts,
                        const mcl_train_cfg* cfg, float* d_loss_log,
                        void* stream);
+
+/* Kernel variants of the tensor-core MLP (index: precision, epilogue warps
+ * per 128-row tile, tile schedule):
+ *   0 BF16 4 lockstep   1 BF16 8 lockstep   2 FP8 4 lockstep
+ *   3 FP8 8 lockstep    4 FP8 4 staggered   5 FP8 8 staggered
+ * Lockstep: each streamed weight block serves both tiles of a pair at once;
+ * staggered: the second tile runs each layer after the first on the resident
+ * blocks, so one tile's epilogue overlaps the other's MMAs (FP8 only: a BF16
+ * layer does not fit in the weight ring).  All variants of a precision give
+ * bit-identical results.  Untuned defaults: 0 (BF16) and 5 (FP8). */
+#define MCL_MLP_VARIANTS 6
+
+/* Autotuner: time every variant of `precision` (MCL_PREC_BF16 or _FP8) on
+ * `rows` synthetic samples (256 <= rows <= max_rays * min(64, max_samples);
+ * uses the map workspace), keep the fastest for all later MLP launches of
+ * the map, return its index in *chosen and the mean ms of each variant in
+ * ms[MCL_MLP_VARIANTS] (-1 for variants of other precisions); either may be
+ * NULL.  Synchronous; must not be called during stream capture.
+ * mcl_localize runs it once per precision before its first graph capture. */
+int mcl_autotune(mcl_map* map, int precision, long long rows, int* chosen, float* ms,
+                 void* stream);
+
+/* Pin the MLP kernel variant of a precision (see MCL_MLP_VARIANTS). */
+int mcl_set_mlp_variant(mcl_map* map, int precision, int variant);
 
 /* Phases timed when profiling is on (indices into the array of
  * mcl_profile_read). */

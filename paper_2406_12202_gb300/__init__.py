@@ -62,7 +62,7 @@ class Schedule(C.Structure):
 class IterRecord(C.Structure):
     _fields_ = [("stage", C.c_int), ("level", C.c_int), ("n_particles", C.c_int),
                 ("n_pixels", C.c_int), ("n_survivors", C.c_int), ("status", C.c_int),
-                ("spread", C.c_double), ("est", C.c_double * 4)]
+                ("spread", C.c_double), ("est", C.c_double * 4), ("t_start_ns", C.c_uint64)]
 
 
 def schedule(levels, pixels, caps, n_min=64, iter_caps=None, refine=None, iterations=20,
@@ -145,6 +145,9 @@ def lib():
             L.mcl_proposal_loss_grad.argtypes = [vp, vp, vp, i32, i32, f32, f32, vp, vp, vp, vp]
             L.mcl_proposal_train.argtypes = [vp, vp, i32, vp, i32, C.POINTER(Intrinsics), i32,
                                              C.POINTER(Opts), C.POINTER(TrainCfg), vp, vp]
+            L.mcl_autotune.argtypes = [vp, i32, C.c_longlong, C.POINTER(C.c_int),
+                                       C.POINTER(C.c_float), vp]
+            L.mcl_set_mlp_variant.argtypes = [vp, i32, i32]
             L.mcl_last_error.restype = C.c_char_p
             L.mcl_last_error.argtypes = []
             _lib = L
@@ -353,7 +356,7 @@ class Map:
                 r = recs[q * iterations + t]
                 rows.append(dict(stage=r.stage, level=r.level, n_particles=r.n_particles,
                                  n_pixels=r.n_pixels, n_survivors=r.n_survivors, status=r.status,
-                                 spread=r.spread, est=list(r.est)))
+                                 spread=r.spread, est=list(r.est), t_start_ns=r.t_start_ns))
             out.append(rows)
         return out
 
@@ -412,6 +415,19 @@ class Map:
             _ptr(pixels, torch.int32, (B, 2), "pixels"), B, C.byref(K), int(level), C.byref(o),
             C.byref(cfg), log.data_ptr(), _stream()))
         return log.cpu().numpy()
+
+    def autotune(self, precision: str, rows: int):
+        """Time the MLP kernel variants of `precision` on `rows` synthetic
+        samples and keep the fastest (mcl_autotune).  Returns (chosen index,
+        {index: ms})."""
+        ch = C.c_int(-1)
+        ms = (C.c_float * MLP_VARIANTS)()
+        _check(lib().mcl_autotune(self.handle, _PREC[precision], int(rows), C.byref(ch), ms,
+                                  _stream()))
+        return ch.value, {i: float(ms[i]) for i in range(MLP_VARIANTS) if ms[i] >= 0}
+
+    def set_mlp_variant(self, precision: str, variant: int):
+        _check(lib().mcl_set_mlp_variant(self.handle, _PREC[precision], int(variant)))
 
     def read_status(self):
         n = C.c_int(0)
@@ -483,7 +499,14 @@ EXPORTED = ("mcl_init_map", "mcl_destroy_map", "mcl_update", "mcl_render", "mcl_
             "mcl_profile_enable", "mcl_profile_read", "mcl_map_supports", "mcl_last_error",
             "mcl_resample_noalloc", "mcl_query", "mcl_draw_pixels", "mcl_localize",
             "mcl_proposal_set", "mcl_proposal_get", "mcl_render_histogram",
-            "mcl_proposal_loss_grad", "mcl_proposal_train")
+            "mcl_proposal_loss_grad", "mcl_proposal_train", "mcl_autotune",
+            "mcl_set_mlp_variant")
+
+# Kernel variants of the tensor-core MLP (include/mcl.h, MCL_MLP_VARIANTS):
+# (precision, epilogue warps per tile, staggered tiles)
+MLP_VARIANTS = 6
+MLP_VARIANT_TABLE = {0: ("bf16", 4, False), 1: ("bf16", 8, False), 2: ("fp8", 4, False),
+                     3: ("fp8", 8, False), 4: ("fp8", 4, True), 5: ("fp8", 8, True)}
 
 # Weights of the learned proposal (gamma(x) with 6 frequencies -> 4 x 64 ReLU
 # -> density): 64*39+64 + 3*(64*64+64) + 64+1.

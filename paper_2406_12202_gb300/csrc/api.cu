@@ -4,6 +4,8 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
+
 #include <atomic>
 #include <cmath>
 #include <vector>
@@ -591,12 +593,28 @@ extern "C" int mcl_localize(mcl_map* m, int nq, float* d_particles, int stride, 
         if (h_n0[q] < 1 || h_n0[q] > stride) return fail(MCL_ERR_ARG, "mcl_localize: n0[%d]", q);
         if (!h_images[q]) return fail(MCL_ERR_ARG, "mcl_localize: image %d is NULL", q);
     }
-    const long max_rays_run = (long)nq * stride * maxB;
+    // largest rays of one iteration: a query has its n0 particles in the
+    // first iteration and at most its stage's cap afterwards
+    int max_n0 = 0;
+    for (int q = 0; q < nq; ++q) max_n0 = std::max(max_n0, h_n0[q]);
+    long per_query = (long)max_n0 * sch->n_pixels[0];
+    for (int st = 0; st < sch->n_stages; ++st)
+        per_query = std::max(per_query, (long)std::min(sch->n_cap[st], stride) * sch->n_pixels[st]);
+    const long max_rays_run = (long)nq * per_query;
+    (void)maxB;
     if (max_rays_run > m->cfg.max_rays)
-        return fail(MCL_ERR_ARG, "mcl_localize: n_queries * stride * max B = %ld > max_rays %d",
+        return fail(MCL_ERR_ARG, "mcl_localize: %ld rays in the largest iteration > max_rays %d",
                     max_rays_run, m->cfg.max_rays);
     if ((rc = check_samples(m, o))) return rc;
     cudaStream_t caller = (cudaStream_t)stream;
+    // the first graph-mode run of a precision picks the MLP kernel variant
+    // (synchronous; never inside a capture)
+    if (use_graph && !mlp_tc_tuned(m, o->precision)) {
+        const int S = std::min(64, m->cfg.max_samples);
+        const long long rows = std::min((long long)max_rays_run * S, (long long)m->cfg.max_rays * S);
+        if (rows >= 256 && (rc = mlp_tc_autotune(m, o->precision, rows, nullptr, nullptr, caller)))
+            return rc;
+    }
     // graph mode captures on the map's own stream, ordered after the caller's
     // work and before the caller's later work by two events
     cudaStream_t s = use_graph ? m->loop.stream : caller;
@@ -624,6 +642,7 @@ extern "C" int mcl_localize(mcl_map* m, int nq, float* d_particles, int stride, 
     key = mix_key(key, K, sizeof(*K));
     key = mix_key(key, sch, sizeof(*sch));
     key = mix_key(key, o, sizeof(*o));
+    key = mix_key(key, &max_rays_run, sizeof(max_rays_run));
     if (!m->loop.exec || m->loop.key != key) {
         if (m->loop.exec) {
             cudaGraphExecDestroy(m->loop.exec);
@@ -648,6 +667,21 @@ extern "C" int mcl_localize(mcl_map* m, int nq, float* d_particles, int stride, 
     if ((rc = cuda_check(cudaGraphLaunch(m->loop.exec, s), "launch graph"))) return rc;
     if ((rc = cuda_check(cudaEventRecord(m->loop.ev_out, s), "event record"))) return rc;
     return cuda_check(cudaStreamWaitEvent(caller, m->loop.ev_out, 0), "stream wait");
+}
+
+extern "C" int mcl_autotune(mcl_map* m, int precision, long long rows, int* chosen, float* ms,
+                            void* stream) {
+    g_err[0] = 0;
+    if (!m) return fail(MCL_ERR_ARG, "mcl_autotune: NULL map");
+    if (precision != MCL_PREC_BF16 && precision != MCL_PREC_FP8)
+        return fail(MCL_ERR_ARG, "mcl_autotune: precision %d has no kernel variants", precision);
+    return mlp_tc_autotune(m, precision, rows, chosen, ms, (cudaStream_t)stream);
+}
+
+extern "C" int mcl_set_mlp_variant(mcl_map* m, int precision, int variant) {
+    g_err[0] = 0;
+    if (!m) return fail(MCL_ERR_ARG, "mcl_set_mlp_variant: NULL map");
+    return mlp_tc_set_variant(m, precision, variant);
 }
 
 extern "C" int mcl_proposal_set(mcl_map* m, const float* host, size_t n) {

@@ -49,6 +49,7 @@ constexpr int kLoopMaxPixels = 256;
 
 struct LoopPlan {
     int total_rays, rows_c, rows_f, pad;
+    unsigned long long t_start;   // global timer at the start of the iteration
     int ray_off[kLoopMaxQueries + 1];
     int N[kLoopMaxQueries], B[kLoopMaxQueries], factor[kLoopMaxQueries], Nnext[kLoopMaxQueries];
 };
@@ -160,6 +161,10 @@ cudaError_t mlp_fp32(mcl_map* m, const Ray* rays, const float* gd, const float* 
 int mlp_tc_prepare(mcl_map* m, const float* host_blob);
 void mlp_tc_free(mcl_map* m);
 bool mlp_tc_available(const mcl_map* m, int precision);
+int mlp_tc_set_variant(mcl_map* m, int precision, int variant);
+int mlp_tc_autotune(mcl_map* m, int precision, long long rows, int* chosen, float* ms_out,
+                    cudaStream_t s);
+bool mlp_tc_tuned(const mcl_map* m, int precision);
 cudaError_t mlp_tc_ray_bias(mcl_map* m, const float* gd, int n_rays, const int* n_rays_dev,
                             cudaStream_t s);
 // rows_dev (optional): device-side row count (rows = n_rays * S is the bound).

@@ -34,6 +34,9 @@ __device__ __forceinline__ int query_of_ray(const LoopPlan* pl, int nq, int r) {
 __global__ void k_plan(LoopPlan* __restrict__ pl, const LoopQuery* __restrict__ qs, int nq,
                        mcl_schedule sch, int nc, int nf) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    pl->t_start = t;
     int off = 0;
     for (int q = 0; q < nq; ++q) {
         const int st = qs[q].stage;
@@ -155,6 +158,7 @@ __global__ __launch_bounds__(kLoopThreads) void k_weights_b(
         rec.spread = var;
         rec.est[0] = m[1]; rec.est[1] = m[2]; rec.est[2] = m[3];
         rec.est[3] = atan2(m[4], m[5]);
+        rec.t_start_ns = pl->t_start;
         log[(size_t)q * iterations + t] = rec;
     }
 }

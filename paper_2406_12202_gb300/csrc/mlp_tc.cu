@@ -30,6 +30,7 @@
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "internal.cuh"
@@ -68,18 +69,12 @@ constexpr int kLayers = 9;
 constexpr int kMaxStages = 8;
 
 // Operand form of the MMAs.  BF16: weight blocks [256 rows x 32 k], 4-stage
-// ring, activations 128 x 256 BF16 (64 KB per tile), 4 epilogue warps per
-// tile.  FP8 (E4M3 with per-layer activation scales and per-layer weight
-// scales): weight blocks [256 rows x 64 k], 8-stage ring, activations
-// 128 x 256 bytes (32 KB), 8 epilogue warps per tile (its epilogue does
-// more arithmetic per value and is on the critical path).  Both fill 225 KB
-// of shared memory.
+// ring, activations 128 x 256 BF16 (64 KB per tile).  FP8 (E4M3 with
+// per-layer activation scales and per-layer weight scales): weight blocks
+// [256 rows x 64 k], 8-stage ring, activations 128 x 256 bytes (32 KB).
+// Both fill 225 KB of shared memory.
 template <bool F8>
 struct Form {
-    static constexpr int kEpiWarps = F8 ? 8 : 4;     // per tile
-    static constexpr int kHalves = kEpiWarps / 4;    // column groups per TMEM lane quadrant
-    static constexpr int kEpiThreads = 32 * kEpiWarps;
-    static constexpr int kThreads = 64 + 2 * kEpiThreads;   // + TMA warp + MMA warp
     static constexpr uint32_t kActBytes = F8 ? 128 * 256 : 128 * 256 * 2;
     static constexpr int kStages = F8 ? 8 : 4;
     static constexpr int kBlocks = F8 ? 34 : 68;     // weight blocks per tile pair
@@ -87,6 +82,22 @@ struct Form {
     static constexpr uint32_t kSmemBytes = 1024 + 2 * kActBytes + 2 * kGxBytes + kStages * kStageBytes;
 };
 static_assert(Form<false>::kSmemBytes <= 232448 && Form<true>::kSmemBytes <= 232448, "smem");
+
+// Kernel variant: operand form, epilogue warps per tile (4: one per TMEM lane
+// quadrant, each thread a whole row; 8: two per quadrant, each thread half a
+// row), and the tile schedule (lockstep: each weight block serves both
+// tiles at once; staggered: tile 1 runs a layer after tile 0 on the
+// resident blocks, so each tile's epilogue overlaps the other's MMAs; needs
+// a whole layer in the ring, i.e. FP8).  The autotuner picks among them.
+template <bool F8, int EPIW, bool STAG>
+struct Variant {
+    static_assert(EPIW == 4 || EPIW == 8, "epilogue warps");
+    static_assert(!STAG || F8, "a BF16 layer does not fit in the weight ring");
+    static constexpr int kEpiWarps = EPIW;
+    static constexpr int kHalves = EPIW / 4;          // column groups per TMEM lane quadrant
+    static constexpr int kEpiThreads = 32 * EPIW;
+    static constexpr int kThreads = 64 + 2 * kEpiThreads;   // + TMA warp + MMA warp
+};
 
 // K chunks (one weight block each) per layer: trunk1 reads gamma(x) (64),
 // trunk6 reads [h (256), gamma(x) (64)], the others h (256).  The last
@@ -230,10 +241,11 @@ __device__ __forceinline__ void rgb_group(const uint32_t (&v)[32], const float4*
     }
 }
 
-template <bool F8>
-__global__ void __launch_bounds__(Form<F8>::kThreads, 1)
+template <bool F8, int EPIW, bool STAG>
+__global__ void __launch_bounds__(Variant<F8, EPIW, STAG>::kThreads, 1)
     k_mlp_tc(const __grid_constant__ Params p) {
     using Fm = Form<F8>;
+    using Vt = Variant<F8, EPIW, STAG>;
     constexpr int kStages = Fm::kStages;
     constexpr uint32_t kActBytes = Fm::kActBytes;
     extern __shared__ uint8_t smem_raw[];
@@ -255,7 +267,7 @@ __global__ void __launch_bounds__(Form<F8>::kThreads, 1)
         }
         for (int s = 0; s < 2; ++s) {
             mbar_init(smem_u32(&bars.acc_full[s]), 1);
-            mbar_init(smem_u32(&bars.a_ready[s]), Fm::kEpiThreads);
+            mbar_init(smem_u32(&bars.a_ready[s]), Vt::kEpiThreads);
         }
         mbar_init(smem_u32(&bars.drain), 1);
         fence_mbar_init();
@@ -331,7 +343,7 @@ __global__ void __launch_bounds__(Form<F8>::kThreads, 1)
                     const int nch = c_chunks[F8 ? 1 : 0][l];
                     const uint32_t idesc = (l == 8) ? id144 : id256;
                     TC_TRACE(2, tl);
-                    if constexpr (F8) {
+                    if constexpr (STAG) {
                         // Staggered tiles: all of layer l for tile 0, then all
                         // of it for tile 1 from the same resident weight
                         // blocks (a layer is at most 5 of the 8 stages), so
@@ -365,7 +377,7 @@ __global__ void __launch_bounds__(Form<F8>::kThreads, 1)
                         g += nch;
                     } else {
                         // Lockstep tiles: each weight block serves both tiles
-                        // at once (a BF16 layer does not fit in the ring).
+                        // at once.
                         for (int c = 0; c < nch && ok; ++c) {
                             const uint32_t st = g % kStages, ph = (g / kStages) & 1u;
                             TC_TRACE(15, g);
@@ -406,8 +418,8 @@ __global__ void __launch_bounds__(Form<F8>::kThreads, 1)
         // i.e. rows 32 (w % 4) .. +31; with 8 warps the first four take
         // accumulator columns 0..127 and the other four 128..255 (column
         // halves h0 .. h1 - 1 of 128); one thread owns one row.
-        constexpr int kH = Fm::kHalves;
-        const int slot = (warp - 2) / Fm::kEpiWarps;
+        constexpr int kH = Vt::kHalves;
+        const int slot = (warp - 2) / Vt::kEpiWarps;
         const int h0 = kH == 2 ? (((warp - 2) >> 2) & 1) : 0;
         const int h1 = h0 + 3 - kH;                       // one half, or both
         const int quad = warp & 3;
@@ -589,6 +601,28 @@ __global__ void k_ray_bias(const float* __restrict__ gd, int n_rays, const int* 
     out[t] = s;
 }
 
+// The kernel variants (see Variant): precision, epilogue warps, staggered.
+struct TcVariant {
+    int precision, epi_warps;
+    bool staggered;
+    void (*fn)(Params);
+    int threads;
+    uint32_t smem;
+};
+template <bool F8, int W, bool S>
+constexpr TcVariant make_variant() {
+    return TcVariant{F8 ? MCL_PREC_FP8 : MCL_PREC_BF16, W, S, &k_mlp_tc<F8, W, S>,
+                     Variant<F8, W, S>::kThreads, Form<F8>::kSmemBytes};
+}
+const TcVariant kVariants[] = {
+    make_variant<false, 4, false>(), make_variant<false, 8, false>(),
+    make_variant<true, 4, false>(),  make_variant<true, 8, false>(),
+    make_variant<true, 4, true>(),   make_variant<true, 8, true>(),
+};
+constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
+// untuned choice per precision: BF16 4 warps lockstep, FP8 8 warps staggered
+constexpr int kDefaultVariant[3] = {-1, 0, 5};
+
 struct TcForm {
     uint8_t* wblocks = nullptr;  // weight blocks in consumption order, 64-byte swizzled
     bool ready = false;
@@ -609,6 +643,9 @@ struct TcState {
     float b_sigma = 0.f, b_out[3] = {0.f, 0.f, 0.f};
     float alpha_sigma = 1.f, s_gx = 1.f;
     int n_sm = 0;
+    int variant[3] = {-1, kDefaultVariant[1], kDefaultVariant[2]};   // by precision
+    float tuned_ms[kNumVariants] = {};                                // last autotune
+    bool tuned[3] = {false, false, false};
 };
 
 inline uint16_t f2bf(float f) {
@@ -845,15 +882,11 @@ int mlp_tc_prepare(mcl_map* m, const float* blob) {
     cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
     cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
     if (major != 10 || minor != 3) return MCL_OK;  // kernels are built for sm_103a only
-    if ((rc = cuda_check(cudaFuncSetAttribute(k_mlp_tc<false>,
-                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              (int)Form<false>::kSmemBytes),
-                         "smem attribute")) ||
-        (rc = cuda_check(cudaFuncSetAttribute(k_mlp_tc<true>,
-                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              (int)Form<true>::kSmemBytes),
-                         "smem attribute")))
-        return rc;
+    for (const TcVariant& v : kVariants)
+        if ((rc = cuda_check(cudaFuncSetAttribute(v.fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                  (int)v.smem),
+                             "smem attribute")))
+            return rc;
     st->bf16.ready = st->fp8.ready = true;
     return MCL_OK;
 }
@@ -888,9 +921,19 @@ cudaError_t mlp_tc_ray_bias(mcl_map* m, const float* gd, int n_rays, const int* 
     return cudaGetLastError();
 }
 
+static cudaError_t mlp_tc_variant(mcl_map* m, int precision, int variant, const Ray* rays,
+                                  const float* z, int S, int n_rays, const int* rows_dev,
+                                  float4* out, cudaStream_t s);
+
 cudaError_t mlp_tc(mcl_map* m, int precision, const Ray* rays, const float* gd, const float* z,
                    int S, int n_rays, const int* rows_dev, float4* out, cudaStream_t s) {
     (void)gd;
+    return mlp_tc_variant(m, precision, -1, rays, z, S, n_rays, rows_dev, out, s);
+}
+
+static cudaError_t mlp_tc_variant(mcl_map* m, int precision, int variant, const Ray* rays,
+                                  const float* z, int S, int n_rays, const int* rows_dev,
+                                  float4* out, cudaStream_t s) {
     TcState* st = (TcState*)m->tc_aux;
     if (!mlp_tc_available(m, precision)) return cudaErrorNotSupported;
     Params p;
@@ -919,12 +962,111 @@ cudaError_t mlp_tc(mcl_map* m, int precision, const Ray* rays, const float* gd, 
     cudaError_t e = cudaMemsetAsync(st->abort_flag, 0, sizeof(int), s);
     if (e) return e;
     const long long grid = p.n_pairs < st->n_sm ? p.n_pairs : st->n_sm;
+    const TcVariant& v = kVariants[variant >= 0 ? variant : st->variant[precision]];
     note_launch();
-    if (precision == MCL_PREC_FP8)
-        k_mlp_tc<true><<<(unsigned)grid, Form<true>::kThreads, Form<true>::kSmemBytes, s>>>(p);
-    else
-        k_mlp_tc<false><<<(unsigned)grid, Form<false>::kThreads, Form<false>::kSmemBytes, s>>>(p);
+    v.fn<<<(unsigned)grid, v.threads, v.smem, s>>>(p);
     return cudaGetLastError();
+}
+
+// Synthetic inputs for timing the kernel variants: rays from points in
+// [-1, 1]^3 in unit directions, z uniform in [2, 6], gamma(d) zero.
+__global__ void k_tune_inputs(Ray* __restrict__ rays, float* __restrict__ z,
+                              float* __restrict__ gd, int n_rays, int S) {
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < (long)n_rays * S) {
+        uint32_t h = (uint32_t)t * 2654435761u + 12345u;
+        h ^= h >> 15; h *= 0x2c1b3c6du; h ^= h >> 12;
+        z[t] = 2.0f + 4.0f * (float)(h >> 8) * (1.0f / 16777216.0f);
+    }
+    if (t < n_rays) {
+        uint32_t h = (uint32_t)t * 0x9E3779B9u + 777u;
+        float v[6];
+        for (int i = 0; i < 6; ++i) {
+            h ^= h >> 15; h *= 0x2c1b3c6du; h ^= h >> 12;
+            v[i] = 2.0f * (float)(h >> 8) * (1.0f / 16777216.0f) - 1.0f;
+        }
+        const float n = rsqrtf(v[3] * v[3] + v[4] * v[4] + v[5] * v[5] + 1e-6f);
+        Ray r{};
+        r.ox = v[0]; r.oy = v[1]; r.oz = v[2];
+        r.dx = v[3] * n; r.dy = v[4] * n; r.dz = v[5] * n;
+        r.dnorm = 1.0f;
+        rays[t] = r;
+        for (int i = 0; i < kGdPad; ++i) gd[(long)t * kGdPad + i] = 0.0f;
+    }
+}
+
+int mlp_tc_set_variant(mcl_map* m, int precision, int variant) {
+    TcState* st = (TcState*)m->tc_aux;
+    if (!mlp_tc_available(m, precision)) return fail(MCL_ERR_UNSUPPORTED, "precision %d unavailable", precision);
+    if (variant < 0 || variant >= kNumVariants || kVariants[variant].precision != precision)
+        return fail(MCL_ERR_ARG, "variant %d is not a variant of precision %d", variant, precision);
+    st->variant[precision] = variant;
+    return MCL_OK;
+}
+
+int mlp_tc_autotune(mcl_map* m, int precision, long long rows, int* chosen, float* ms_out,
+                    cudaStream_t s) {
+    TcState* st = (TcState*)m->tc_aux;
+    if (!mlp_tc_available(m, precision)) return fail(MCL_ERR_UNSUPPORTED, "precision %d unavailable", precision);
+    const int S = std::min(64, m->cfg.max_samples);
+    const long long cap = (long long)m->cfg.max_rays * S;
+    if (rows < 256 || rows > cap) return fail(MCL_ERR_ARG, "autotune rows %lld not in [256, %lld]", rows, cap);
+    const int n_rays = (int)((rows + S - 1) / S);
+    int rc;
+    note_launch();
+    k_tune_inputs<<<(unsigned)(((long)n_rays * S + 255) / 256), 256, 0, s>>>(m->rays, m->zc, m->gd,
+                                                                             n_rays, S);
+    if ((rc = cuda_check(cudaGetLastError(), "tune inputs")) ||
+        (rc = cuda_check(mlp_tc_ray_bias(m, m->gd, n_rays, nullptr, s), "tune ray bias")))
+        return rc;
+    cudaEvent_t a = nullptr, b = nullptr;
+    if ((rc = cuda_check(cudaEventCreate(&a), "event")) || (rc = cuda_check(cudaEventCreate(&b), "event")))
+        return rc;
+    int best = -1;
+    float best_ms = 0.f;
+    for (int v = 0; v < kNumVariants && !rc; ++v) {
+        if (ms_out) ms_out[v] = -1.f;
+        if (kVariants[v].precision != precision) continue;
+        float tot = 0.f;
+        for (int rep = 0; rep < 4 && !rc; ++rep) {
+            rc = cuda_check(cudaEventRecord(a, s), "event");
+            if (!rc) rc = cuda_check(mlp_tc_variant(m, precision, v, m->rays, m->zc, S, n_rays, nullptr,
+                                                    m->out_c, s), "tune launch");
+            if (!rc) rc = cuda_check(cudaEventRecord(b, s), "event");
+            if (!rc) rc = cuda_check(cudaEventSynchronize(b), "event sync");
+            float ms = 0.f;
+            if (!rc) rc = cuda_check(cudaEventElapsedTime(&ms, a, b), "elapsed");
+            if (rep > 0) tot += ms;       // the first launch warms caches
+        }
+        if (rc) break;
+        const float mean = tot / 3.f;
+        st->tuned_ms[v] = mean;
+        if (ms_out) ms_out[v] = mean;
+        if (best < 0 || mean < best_ms) {
+            best = v;
+            best_ms = mean;
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (rc) return rc;
+    if (m->status) {
+        // a timed-out wait inside a trial launch is an error, not a timing
+        int code = 0;
+        if ((rc = cuda_check(cudaMemcpy(&code, &m->status->code, sizeof(int), cudaMemcpyDeviceToHost),
+                             "read status")))
+            return rc;
+        if (code) return fail(code, "autotune: a trial launch reported error %d", code);
+    }
+    st->variant[precision] = best;
+    st->tuned[precision] = true;
+    if (chosen) *chosen = best;
+    return MCL_OK;
+}
+
+bool mlp_tc_tuned(const mcl_map* m, int precision) {
+    const TcState* st = (const TcState*)m->tc_aux;
+    return st && precision >= 0 && precision < 3 && st->tuned[precision];
 }
 
 }  // namespace mcl
