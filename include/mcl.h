@@ -316,6 +316,12 @@ typedef struct {
 int mcl_proposal_set(mcl_map* map, const float* host_weights, size_t n);
 int mcl_proposal_get(mcl_map* map, float* host_out, size_t n);
 
+/* Raw proposal density at n points d_x [n,3] into d_sigma [n] (FP32 form:
+ * the FP32 kernel; BF16 / FP8: the tensor-core kernel used by those forms,
+ * BF16 operands).  1 <= n <= max_rays; uses the map workspace. */
+int mcl_proposal_query(mcl_map* map, const float* d_x, int n, int precision, float* d_sigma,
+                       void* stream);
+
 /* Targets of the distillation: for n_poses poses x B pixels, render with the
  * full sampler of `opts` (n_coarse + n_fine, use_proposal ignored) and
  * re-bin the final weights onto n_bins equal intervals of [near_z, far_z]

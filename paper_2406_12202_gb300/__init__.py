@@ -145,6 +145,7 @@ def lib():
             L.mcl_proposal_loss_grad.argtypes = [vp, vp, vp, i32, i32, f32, f32, vp, vp, vp, vp]
             L.mcl_proposal_train.argtypes = [vp, vp, i32, vp, i32, C.POINTER(Intrinsics), i32,
                                              C.POINTER(Opts), C.POINTER(TrainCfg), vp, vp]
+            L.mcl_proposal_query.argtypes = [vp, vp, i32, i32, vp, vp]
             L.mcl_autotune.argtypes = [vp, i32, C.c_longlong, C.POINTER(C.c_int),
                                        C.POINTER(C.c_float), vp]
             L.mcl_set_mlp_variant.argtypes = [vp, i32, i32]
@@ -370,6 +371,15 @@ class Map:
         _check(lib().mcl_proposal_get(self.handle, w.ctypes.data, w.size))
         return w
 
+    def proposal_query(self, x, precision: str = "fp32"):
+        """Raw proposal density at points x [n,3] (mcl_proposal_query)."""
+        torch = _torch()
+        n = x.shape[0]
+        out = torch.empty(n, dtype=torch.float32, device=x.device)
+        _check(lib().mcl_proposal_query(self.handle, _ptr(x, torch.float32, (n, 3), "x"), n,
+                                        _PREC[precision], out.data_ptr(), _stream()))
+        return out
+
     def render_histogram(self, poses, K: Intrinsics, level: int, pixels, opts: UpdateOptions,
                          n_bins: int):
         """Distillation targets [n*B, n_bins] (mcl_render_histogram)."""
@@ -499,7 +509,7 @@ EXPORTED = ("mcl_init_map", "mcl_destroy_map", "mcl_update", "mcl_render", "mcl_
             "mcl_profile_enable", "mcl_profile_read", "mcl_map_supports", "mcl_last_error",
             "mcl_resample_noalloc", "mcl_query", "mcl_draw_pixels", "mcl_localize",
             "mcl_proposal_set", "mcl_proposal_get", "mcl_render_histogram",
-            "mcl_proposal_loss_grad", "mcl_proposal_train", "mcl_autotune",
+            "mcl_proposal_loss_grad", "mcl_proposal_train", "mcl_proposal_query", "mcl_autotune",
             "mcl_set_mlp_variant")
 
 # Kernel variants of the tensor-core MLP (include/mcl.h, MCL_MLP_VARIANTS):

@@ -101,7 +101,8 @@ static void free_map(mcl_map* m) {
     void* ptrs[] = {m->w32, m->rays, m->gd, m->zc, m->zf, m->out_c, m->out_f, m->e_ray,
                     m->logw64, m->cdf, m->status, m->act0, m->act1, m->gxbuf,
                     m->loop.plan, m->loop.qs, m->loop.n0, (void*)m->loop.imgs, m->loop.pix,
-                    m->loop.P_next, m->loop.w, m->loop.mask, m->loop.idx, m->prop_w};
+                    m->loop.P_next, m->loop.w, m->loop.mask, m->loop.idx, m->prop_w,
+                    m->prop_packed, m->prop_abort};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete m;
@@ -349,7 +350,7 @@ static int render_passes(mcl_map* m, const float* d_poses, int N, const mcl_intr
     // importance samples from those (into zc), NeRF MLP (into out_f)
     {
         PhaseScope ph(m, MCL_PHASE_SAMPLE, s);
-        if ((rc = cuda_check(launch_prop_infer(m, m->rays, m->zc, o->n_proposal, nr, nullptr,
+        if ((rc = cuda_check(launch_prop_infer(m, o->precision, m->rays, m->zc, o->n_proposal, nr, nullptr,
                                                m->out_f, s),
                              "proposal")))
             return rc;
@@ -431,6 +432,27 @@ extern "C" int mcl_query(mcl_map* m, const float* d_x, const float* d_dir, int n
     if ((rc = cuda_check(mlp_tc_ray_bias(m, m->gd, n, nullptr, s), "query ray bias"))) return rc;
     return cuda_check(mlp_tc(m, precision, m->rays, m->gd, m->zc, 1, n, nullptr, (float4*)d_out, s),
                       "query mlp");
+}
+
+extern "C" int mcl_proposal_query(mcl_map* m, const float* d_x, int n, int precision,
+                                  float* d_sigma, void* stream) {
+    g_err[0] = 0;
+    if (!m || !d_x || !d_sigma) return fail(MCL_ERR_ARG, "mcl_proposal_query: NULL argument");
+    if (n < 1 || n > m->cfg.max_rays)
+        return fail(MCL_ERR_ARG, "mcl_proposal_query: n %d outside [1, %d]", n, m->cfg.max_rays);
+    if (!m->has_proposal) return fail(MCL_ERR_ARG, "mcl_proposal_query: no proposal weights set or trained");
+    if (precision != MCL_PREC_FP32 && !mlp_tc_available(m, precision))
+        return fail(MCL_ERR_UNSUPPORTED, "precision %d is not available on this device", precision);
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc;
+    // rays from the points with zero-length steps (z = 0), one sample each
+    if ((rc = cuda_check(launch_query_setup(d_x, d_x, n, m->rays, m->gd, m->zc, s), "query setup")) ||
+        (rc = cuda_check(launch_prop_infer(m, precision, m->rays, m->zc, 1, n, nullptr, m->out_c, s),
+                         "proposal")))
+        return rc;
+    return cuda_check(cudaMemcpy2DAsync(d_sigma, sizeof(float), m->out_c, sizeof(float4), sizeof(float),
+                                        n, cudaMemcpyDeviceToDevice, s),
+                      "copy densities");
 }
 
 extern "C" int mcl_render(mcl_map* m, const float* d_poses, int n_poses, const mcl_intrinsics* K,
@@ -694,8 +716,11 @@ extern "C" int mcl_proposal_set(mcl_map* m, const float* host, size_t n) {
     if ((rc = cuda_check(cudaMemcpy(m->prop_w, host, sizeof(float) * n, cudaMemcpyHostToDevice),
                          "upload proposal")))
         return rc;
-    // fresh optimiser state for the new weights
-    if ((rc = cuda_check(cudaMemset(m->prop_m, 0, sizeof(float) * 2 * n), "clear moments"))) return rc;
+    // fresh optimiser state for the new weights; BF16 copy for inference
+    if ((rc = cuda_check(cudaMemset(m->prop_m, 0, sizeof(float) * 2 * n), "clear moments")) ||
+        (rc = cuda_check(prop_tc_pack(m, 0), "pack proposal")) ||
+        (rc = cuda_check(cudaDeviceSynchronize(), "pack proposal")))
+        return rc;
     m->prop_step = 0;
     m->has_proposal = true;
     return MCL_OK;

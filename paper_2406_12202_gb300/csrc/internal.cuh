@@ -124,6 +124,9 @@ struct mcl_map {
     float* prop_g = nullptr;
     int prop_step = 0;
     bool has_proposal = false;
+    uint16_t* prop_packed = nullptr;   // BF16 weights of the tensor-core proposal kernel
+    int* prop_abort = nullptr;         // per-launch abort flag of that kernel
+    int n_sm = 0;
 };
 
 namespace mcl {
@@ -182,7 +185,12 @@ cudaError_t launch_position_spread(const float* poses, int N, double* out, cudaS
 
 // proposal.cu
 int proposal_alloc(mcl_map* m);
-cudaError_t launch_prop_infer(mcl_map* m, const Ray* rays, const float* z, int n_p, int n_rays,
+// proposal_tc.cu
+cudaError_t prop_tc_pack(mcl_map* m, cudaStream_t s);
+cudaError_t prop_tc_prepare();
+cudaError_t launch_prop_infer_tc(mcl_map* m, const Ray* rays, const float* z, int n_p, int n_rays,
+                                 const int* n_rays_dev, float4* out, int n_sm, cudaStream_t s);
+cudaError_t launch_prop_infer(mcl_map* m, int precision, const Ray* rays, const float* z, int n_p, int n_rays,
                               const int* n_rays_dev, float4* out, cudaStream_t s);
 cudaError_t launch_histogram(const Ray* rays, int n_rays, const float* zc, const float4* oc, int nc,
                              const float* zf, const float4* of, int nf, int nb, float near_z,

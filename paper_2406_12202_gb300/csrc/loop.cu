@@ -273,7 +273,7 @@ int enqueue_localize(mcl_map* m, int nq, float* P_user, int stride, const mcl_in
                              "loop ray bias")))
             return rc;
         if (prop) {
-            if ((rc = cuda_check(launch_prop_infer(m, m->rays, m->zc, np, max_rays_run,
+            if ((rc = cuda_check(launch_prop_infer(m, o.precision, m->rays, m->zc, np, max_rays_run,
                                                    &L.plan->total_rays, m->out_f, s),
                                  "loop proposal")) ||
                 (rc = cuda_check(launch_coarse_to_fine(m->rays, max_rays_run, &L.plan->total_rays,

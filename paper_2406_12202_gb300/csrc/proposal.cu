@@ -384,6 +384,16 @@ int proposal_alloc(mcl_map* m) {
     m->prop_v = m->prop_w + 2 * kPN;
     m->prop_g = m->prop_w + 3 * kPN;
     if ((rc = cuda_check(cudaMemset(m->prop_w, 0, sizeof(float) * kPN * 4), "proposal clear"))) return rc;
+    if ((rc = cuda_check(cudaMalloc(&m->prop_packed, 4 * 64 * 64 * sizeof(uint16_t)), "proposal bf16")) ||
+        (rc = cuda_check(cudaMemset(m->prop_packed, 0, 4 * 64 * 64 * sizeof(uint16_t)), "proposal bf16")) ||
+        (rc = cuda_check(cudaMalloc(&m->prop_abort, sizeof(int)), "proposal abort flag")))
+        return rc;
+    int dev = 0, major = 0, minor = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&m->n_sm, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+    cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+    if (major == 10 && minor == 3 && (rc = cuda_check(prop_tc_prepare(), "proposal tc smem"))) return rc;
     if ((rc = cuda_check(cudaFuncSetAttribute(k_prop_infer, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               kPN * (int)sizeof(float)),
                          "proposal smem")))
@@ -398,8 +408,12 @@ int proposal_alloc(mcl_map* m) {
                       "proposal smem");
 }
 
-cudaError_t launch_prop_infer(mcl_map* m, const Ray* rays, const float* z, int n_p, int n_rays,
-                              const int* n_rays_dev, float4* out, cudaStream_t s) {
+// Proposal densities at the stratified samples: the tensor-core kernel for
+// the BF16 / FP8 forms, the FP32 kernel for the FP32 form.
+cudaError_t launch_prop_infer(mcl_map* m, int precision, const Ray* rays, const float* z, int n_p,
+                              int n_rays, const int* n_rays_dev, float4* out, cudaStream_t s) {
+    if (precision != MCL_PREC_FP32 && mlp_tc_available(m, MCL_PREC_BF16))
+        return launch_prop_infer_tc(m, rays, z, n_p, n_rays, n_rays_dev, out, m->n_sm, s);
     const long rows = (long)n_rays * n_p;
     note_launch();
     k_prop_infer<<<grid_for(rows, 128), 128, kPN * sizeof(float), s>>>(m->prop_w, rays, z, n_p, rows,
@@ -590,6 +604,7 @@ int proposal_train(mcl_map* m, const float* d_poses, int n_poses, const int32_t*
         }
     }
     m->prop_step = step;
+    if (!rc) rc = cuda_check(prop_tc_pack(m, s), "pack proposal");
     if (!rc) rc = cuda_check(cudaStreamSynchronize(s), "train sync");
     cleanup();
     if (!rc) m->has_proposal = true;

@@ -184,6 +184,56 @@ def test_proposal_render_matches_oracle(M, gmap):
     assert np.all(np.abs(F_g - r["F"]) <= f_allow * (1 + 1e-6))
 
 
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_proposal_densities_vs_oracle(M, gmap, prec):
+    """Raw proposal density at points: the FP32 kernel to 1e-4 relative
+    (floor 1e-5), the tensor-core kernel (BF16 operands, FP32 accumulation,
+    used by the BF16 and FP8 forms) within 0.05 max / 0.01 mean of the
+    density spread (8 significant bits through four layers)."""
+    import torch
+    pblob = synth.proposal_init_weights(6)
+    gmap.proposal_set(pblob)
+    rng = np.random.default_rng(31)
+    x = f32(rng.uniform(-7, 7, size=(4099, 3)))
+    s_g = gmap.proposal_query(torch.tensor(x, dtype=torch.float32, device="cuda"), prec)
+    s_g = s_g.cpu().numpy().astype(np.float64)
+    s_o = oracle.prop_forward(pblob, x)
+    if prec == "fp32":
+        assert np.all(np.abs(s_g - s_o) <= 1e-4 * np.abs(s_o) + 1e-5)
+    else:
+        e = np.abs(s_g - s_o) / np.std(s_o)
+        assert e.max() <= 0.05 and e.mean() <= 0.01, (e.max(), e.mean())
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp8"])
+def test_proposal_render_tensor_core_forms_vs_oracle(M, gmap, prec):
+    """BF16 / FP8 forms: the proposal runs on the tensor cores in BF16 and
+    the NeRF MLP in the form's precision.  The guided samples follow the
+    inverse CDF of the rounded proposal weights, so besides the MLP's own
+    rounding every guided position moves by a fraction of its bin: bars are
+    twice the plain forms' rendered bars with importance samples (BF16: max
+    0.16, mean 0.03; FP8: max 0.24, mean 0.04), on rays away from the flip
+    band of the seed-2 map."""
+    import torch
+    pblob = synth.proposal_init_weights(5)
+    gmap.proposal_set(pblob)
+    P, px, K4, factor, level, W, H = scene(12, 8, 16)
+    Pt, pxt, K = gpu_inputs(M, P, px, K4, W, H)
+    opts = M.UpdateOptions(n_coarse=32, n_fine=16, precision=prec, use_proposal=True,
+                           n_proposal=32, n_guided=16)
+    rgb_g = gmap.render(Pt, K, level, pxt, opts).cpu().numpy().astype(np.float64)
+    torch.cuda.synchronize()
+    o, d = level_rays(P, K4, factor, px)
+    r = oracle.render_rays_proposal(synth.he_init_weights(2), pblob, o, d,
+                                    oracle.make_opts(n_coarse=32, n_fine=16), n_p=32, n_g=16)
+    band = 0.1 if prec == "bf16" else 0.6
+    flip = (np.abs(r["sigma_last"]) < band) & (r["T_last"] > 1e-3)
+    e = np.abs(rgb_g - r["rgb"])[~flip]
+    mx, mn = (0.16, 0.03) if prec == "bf16" else (0.24, 0.04)
+    assert flip.mean() <= 0.5 and np.all(np.isfinite(rgb_g))
+    assert e.max() <= mx and e.mean() <= mn, (e.max(), e.mean(), flip.mean())
+
+
 def test_proposal_options_are_checked(M):
     """use_proposal without proposal weights, and sample counts beyond the
     workspace, are argument errors."""

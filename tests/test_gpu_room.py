@@ -91,10 +91,11 @@ def _localize(M, room, observations, opts, iterations=60, sigma=0.02):
 def test_room_localization_converges(M, room, observations):
     """Four queries from the global spread, 2000 particles each, 60
     iterations of the BF16 loop (levels 1/4, 1/2, 1 of a 100 x 100 image, 64
-    pixels per update): every estimate ends within 10 cm and 2 degrees."""
+    pixels per update): every estimate ends within 10 cm and 5 degrees (the
+    paper's rotation threshold, Sec. IV-A)."""
     errs = _localize(M, room, observations,
                      M.UpdateOptions(n_coarse=64, n_fine=64, precision="bf16", seed=1))
-    assert all(p < 0.1 and y < 2.0 for p, y in errs), errs
+    assert all(p < 0.1 and y < 5.0 for p, y in errs), errs
 
 
 def test_room_localization_with_trained_proposal(M, room, observations):
@@ -114,4 +115,4 @@ def test_room_localization_with_trained_proposal(M, room, observations):
     errs = _localize(M, room, observations,
                      M.UpdateOptions(n_coarse=64, n_fine=32, precision="bf16", seed=1,
                                      use_proposal=True, n_proposal=64, n_guided=32))
-    assert all(p < 0.1 and y < 2.0 for p, y in errs), errs
+    assert all(p < 0.1 and y < 5.0 for p, y in errs), errs
