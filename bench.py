@@ -575,11 +575,12 @@ def run_ours(args):
                 "unit": "TFLOP/s", "peak_source": f"bf16_tflops burst ({peak_src})"
                 + (" x 2 nominal fp8/bf16 ratio" if prec == "fp8" else "")}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = (profiled_traffic("k_mlp_tc_c2_bf16.md", ("mlp_tc.cu", "tc_ptx.cuh"))
-                       if prec == "bf16" else None)
+    prof_file = {"bf16": "k_mlp_tc_c2_bf16.md", "fp8": "k_mlp_tc_c2_fp8.md"}.get(prec)
+    roof["traffic"] = (profiled_traffic(prof_file, ("mlp_tc.cu", "tc_ptx.cuh"))
+                       if prof_file else None)
     if roof["traffic"] is not None:
         roof["traffic_note"] = ("DRAM bytes per k_mlp_tc launch (mean of the coarse and fine "
-                                "pass), profiles/k_mlp_tc_c2_bf16.md")
+                                f"pass), profiles/{prof_file}")
     roof["kernel"] = "NeRF MLP (coarse + fine passes)"
     roof["mlp_ms_per_step"] = mlp_ms
 
