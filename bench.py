@@ -268,6 +268,48 @@ def run_coarse_to_fine(M, img, K, seed, prec, fp32_replay=True):
     return out
 
 
+def run_ablation(M, img, K, seed, prec):
+    """Module ablation of Table 3 (Sec. IV-C) on synthetic data: particle
+    rejection (Eq. 6 with F, or Eq. 4 with F = 1) x coarse-to-fine (three
+    levels 1/4, 1/2, 1 with 16 / 32 / 64 px and a survivor-driven particle
+    count, or the full level with 64 px and a fixed count), 20 iterations
+    from 1500 particles; ms per update and final pose error, one device run
+    each under a CUDA graph."""
+    import torch
+    import synth
+    N0, iters = 1500, 20
+    gm = M.Map(synth.he_init_weights(0), max_rays=N0 * 64, max_samples=192, max_particles=N0,
+               max_queries=1)
+    _, gxyz, gyaw = synth.gt_pose(seed)
+    P0 = torch.tensor(synth.random_particles(seed + 1, N0)[0], dtype=torch.float32,
+                      device="cuda").reshape(1, N0, 12)
+    out = {}
+    for rej in (True, False):
+        for c2f in (True, False):
+            if c2f:
+                sch = M.schedule([0, 1, 2], [16, 32, 64], [N0, 1000, 600], n_min=100,
+                                 iter_caps=[7, 7, 6], refine=[0.05, 0.01, 0.0], iterations=iters)
+            else:
+                sch = M.schedule([2], [64], [N0], n_min=N0, iter_caps=[iters], refine=[0.0],
+                                 iterations=iters)
+            opts = M.UpdateOptions(n_coarse=64, n_fine=128, precision=prec, seed=seed,
+                                   use_rejection=rej)
+            gm.localize(P0.clone(), [N0], [img], K, sch, opts, use_graph=True)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            log, _ = gm.localize(P0.clone(), [N0], [img], K, sch, opts, use_graph=True)
+            b.record()
+            torch.cuda.synchronize()
+            recs = M.Map.decode_log(log, 1, iters)[0]
+            perr, yerr = _pose_error(recs[-1]["est"], gxyz, gyaw)
+            key = ("rejection" if rej else "no_rejection") + "+" + ("coarse_to_fine" if c2f else "single_level")
+            out[key] = {"ms_per_update": a.elapsed_time(b) / iters, "final_position_error": perr,
+                        "final_yaw_error_deg": yerr}
+    gm.close()
+    return out
+
+
 def run_proposal_fp8(M, gm, img, K, seed, steps, warmup, wl):
     """Learned proposal + FP8 MLP on the full-update workload: the proposal
     (4 x 64, gamma with 6 frequencies) is distilled on the GPU from the
@@ -595,6 +637,7 @@ def run_ours(args):
     if world == 1 and not args.no_extra:
         for name, fn in (
                 ("coarse_to_fine", lambda: run_coarse_to_fine(M, img, K, seed, prec)),
+                ("ablation", lambda: run_ablation(M, img, K, seed, prec)),
                 ("proposal_fp8", lambda: run_proposal_fp8(M, gm, img, K, seed, args.steps,
                                                           args.warmup, wl)),
                 ("batched_queries", lambda: run_batched(M, seed, W, H, wl["focal"],

@@ -585,6 +585,264 @@ __global__ void __launch_bounds__(Variant<F8, EPIW, STAG>::kThreads, 1)
     }
 }
 
+// ---------------------------------------------------------------------------
+// BF16, split schedule: every layer runs as two 128-column halves (N = 128)
+// over weight blocks [128 output rows x 64 k] (128-byte swizzle), tiles in
+// lockstep.  Half 0's accumulators are committed once every MMA that reads
+// activation columns 0..127 has completed (after half 1's first two K
+// chunks), so the epilogue of columns 0..127 runs while half 1 finishes, and
+// the next layer's first two K chunks start as soon as it is done; the
+// epilogue of columns 128..255 then overlaps those.  The last layer's half 1
+// is the density head (one row, N = 16).  Same arithmetic as the lockstep
+// kernel.
+struct __align__(8) SplitBars {
+    uint64_t full[4];
+    uint64_t empty[4];
+    uint64_t acc_lo[2], acc_hi[2];
+    uint64_t rdy_lo[2], rdy_hi[2];
+    uint64_t drain;
+    uint32_t tmem_base;
+};
+constexpr int kSplitStages = 4;
+constexpr int kSplitThreads = 64 + 2 * 128;
+constexpr uint32_t kSplitSmem = Form<false>::kSmemBytes;
+
+// K chunks (64 k each) of layer l: trunk1 gamma(x) (64), skip layer 320, else 256
+__device__ __forceinline__ int split_chunks(int l) { return l == 0 ? 1 : (l == 5 ? 5 : 4); }
+
+__global__ void __launch_bounds__(kSplitThreads, 1) k_mlp_tc_split(const __grid_constant__ Params p) {
+    constexpr uint32_t kActBytes = Form<false>::kActBytes;
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ SplitBars bars;
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const uint32_t s_act = smem_u32(smem);
+    const uint32_t s_gx = s_act + 2 * kActBytes;
+    const uint32_t s_ring = s_gx + 2 * kGxBytes;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    volatile int* abort_flag = p.abort_flag;
+    const long long M = p.M_dev ? min(p.M, (long long)*p.M_dev) : p.M;
+    const long long n_pairs = (M + 255) / 256;
+    if (tid == 0) {
+        for (int i = 0; i < kSplitStages; ++i) {
+            mbar_init(smem_u32(&bars.full[i]), 1);
+            mbar_init(smem_u32(&bars.empty[i]), 1);
+        }
+        for (int s = 0; s < 2; ++s) {
+            mbar_init(smem_u32(&bars.acc_lo[s]), 1);
+            mbar_init(smem_u32(&bars.acc_hi[s]), 1);
+            mbar_init(smem_u32(&bars.rdy_lo[s]), 128);
+            mbar_init(smem_u32(&bars.rdy_hi[s]), 128);
+        }
+        mbar_init(smem_u32(&bars.drain), 1);
+        fence_mbar_init();
+    }
+    if (warp == 1) {
+        tmem_alloc(smem_u32(&bars.tmem_base), 512);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = bars.tmem_base;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            uint32_t g = 0;
+            bool ok = true;
+            for (long long pr = blockIdx.x; pr < n_pairs && ok; pr += gridDim.x) {
+                for (int b = 0; b < Form<false>::kBlocks; ++b, ++g) {
+                    const uint32_t st = g % kSplitStages, ph = (g / kSplitStages) & 1u;
+                    if (!mbar_wait(smem_u32(&bars.empty[st]), ph ^ 1u, abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_arrive_expect_tx(smem_u32(&bars.full[st]), kStageBytes);
+                    bulk_load(s_ring + st * kStageBytes, p.wblocks + (size_t)b * kStageBytes,
+                              kStageBytes, smem_u32(&bars.full[st]));
+                }
+            }
+            if (!ok) record_abort(p);
+            for (uint32_t k = 0; k < (uint32_t)kSplitStages && k < g; ++k) {
+                const uint32_t gl = g - 1 - k;
+                mbar_wait(smem_u32(&bars.full[gl % kSplitStages]), (gl / kSplitStages) & 1u, nullptr);
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            uint32_t g = 0;
+            uint32_t ph_lo[2] = {0, 0}, ph_hi[2] = {0, 0};
+            bool ok = true;
+            const uint32_t id128 = idesc_bf16(128, 128), id16 = idesc_bf16(128, 16);
+            auto wait_rdy = [&](uint64_t* bar, uint32_t& ph) -> bool {
+                if (!mbar_wait(smem_u32(bar), ph, abort_flag)) return false;
+                ph ^= 1u;
+                tc_fence_after();
+                return true;
+            };
+            for (long long pr = blockIdx.x; pr < n_pairs && ok; pr += gridDim.x) {
+                for (int l = 0; l < kLayers && ok; ++l) {
+                    const int nch = split_chunks(l);
+                    for (int h = 0; h < 2 && ok; ++h) {
+                        const uint32_t idesc = (l == 8 && h == 1) ? id16 : id128;
+                        for (int c = 0; c < nch && ok; ++c) {
+                            const uint32_t st = g % kSplitStages, ph = (g / kSplitStages) & 1u;
+                            if (!mbar_wait(smem_u32(&bars.full[st]), ph, abort_flag)) {
+                                ok = false;
+                                break;
+                            }
+                            for (int s = 0; s < 2 && ok; ++s) {
+                                // accumulator half h of tile s is free and its
+                                // A chunk written: columns 0..127 of the previous
+                                // output before K chunk 0, 128..255 before chunk 2
+                                if (h == 0 && c == 0) ok = wait_rdy(&bars.rdy_lo[s], ph_lo[s]);
+                                if (ok && ((l > 0 && h == 0 && c == 2) || (l == 0 && h == 1 && c == 0)))
+                                    ok = wait_rdy(&bars.rdy_hi[s], ph_hi[s]);
+                                if (!ok) break;
+                                uint32_t a0;
+                                if (l == 0) a0 = s_gx + s * kGxBytes;
+                                else if (l == 5 && c == 4) a0 = s_gx + s * kGxBytes;
+                                else a0 = s_act + s * kActBytes + c * 16384;
+#pragma unroll
+                                for (int kk = 0; kk < 4; ++kk) {
+                                    const uint64_t ad = smem_desc(a0 + kk * 32, 1024, kLayoutSw128);
+                                    const uint64_t bd =
+                                        smem_desc(s_ring + st * kStageBytes + kk * 32, 1024, kLayoutSw128);
+                                    mma_bf16(tmem + s * 256 + h * 128, ad, bd, idesc, (c | kk) ? 1u : 0u);
+                                }
+                                // columns 0..127 are final once no pending MMA reads
+                                // activation columns 0..127: after half 0 (layer 0:
+                                // reads gamma(x) only) or after half 1's chunk 1
+                                if ((l == 0 && h == 0 && c == nch - 1) || (l > 0 && h == 1 && c == 1))
+                                    mma_commit(smem_u32(&bars.acc_lo[s]));
+                                if (h == 1 && c == nch - 1) mma_commit(smem_u32(&bars.acc_hi[s]));
+                            }
+                            if (!ok) break;
+                            mma_commit(smem_u32(&bars.empty[st]));
+                            ++g;
+                        }
+                    }
+                }
+            }
+            if (!ok) record_abort(p);
+            mma_commit(smem_u32(&bars.drain));
+            mbar_wait(smem_u32(&bars.drain), 0, nullptr);
+        }
+    } else {
+        const int slot = (warp - 2) >> 2;
+        const int quad = warp & 3;
+        const uint32_t r = quad * 32 + lane;
+        const uint32_t t_row = tmem + ((uint32_t)(quad * 32) << 16) + slot * 256;
+        const uint32_t a_base = s_act + slot * kActBytes;
+        const uint32_t g_base = s_gx + slot * kGxBytes;
+        const uint32_t b_lo = smem_u32(&bars.acc_lo[slot]), b_hi = smem_u32(&bars.acc_hi[slot]);
+        const uint32_t r_lo = smem_u32(&bars.rdy_lo[slot]), r_hi = smem_u32(&bars.rdy_hi[slot]);
+        uint32_t ph_lo = 0, ph_hi = 0;
+        bool ok = true;
+        for (long long pr = blockIdx.x; pr < n_pairs && ok; pr += gridDim.x) {
+            const long long grow = pr * 256 + slot * 128 + r;
+            const bool valid = grow < M;
+            const long long ray = valid ? grow / p.S : 0;
+            {
+                float x[3] = {0.f, 0.f, 0.f};
+                if (valid) {
+                    const Ray R = p.rays[ray];
+                    const float zz = p.z[grow];
+                    x[0] = fmaf(zz, R.dx, R.ox);
+                    x[1] = fmaf(zz, R.dy, R.oy);
+                    x[2] = fmaf(zz, R.dz, R.oz);
+                }
+                for (int half = 0; half < 2; ++half) {
+                    float v[32];
+                    if (valid) {
+                        if (half == 0) pe_half<0>(x, v);
+                        else pe_half<1>(x, v);
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < 32; ++i) v[i] = 0.0f;
+                    }
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        st_shared_v4(g_base + sw128_offset(r, 4 * half + j),
+                                     pack_bf16x2(v[8 * j], v[8 * j + 1]),
+                                     pack_bf16x2(v[8 * j + 2], v[8 * j + 3]),
+                                     pack_bf16x2(v[8 * j + 4], v[8 * j + 5]),
+                                     pack_bf16x2(v[8 * j + 6], v[8 * j + 7]));
+                }
+                fence_proxy_async_smem();
+                tc_fence_before();
+                mbar_arrive(r_lo);
+                mbar_arrive(r_hi);
+            }
+            float o0 = 0.f, o1 = 0.f, o2 = 0.f;
+            const float4* rb4 = reinterpret_cast<const float4*>(p.ray_bias + ray * 128);
+            const float4* wo4 = reinterpret_cast<const float4*>(p.w_out);
+            for (int l = 0; l < kLayers && ok; ++l) {
+                for (int h = 0; h < 2 && ok; ++h) {
+                    if (!mbar_wait(h ? b_hi : b_lo, h ? ph_hi : ph_lo, abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    if (h) ph_hi ^= 1u;
+                    else ph_lo ^= 1u;
+                    tc_fence_after();
+                    const uint32_t t_acc = t_row + h * 128;
+                    if (l < 8) {
+                        const uint4* b4 = reinterpret_cast<const uint4*>(p.bias2 + l * 128 + h * 64);
+                        uint32_t va[32], vb[32];
+                        tmem_ld32(t_acc, va);
+#pragma unroll 1
+                        for (int c32 = 0; c32 < 4; c32 += 2) {
+                            tmem_ld_wait();
+                            tmem_ld32(t_acc + (c32 + 1) * 32, vb);
+                            const uint32_t blk = a_base + (2 * h + (c32 >> 1)) * 16384;
+                            epi_chunk_store(va, b4 + c32 * 4, blk, r, 0);
+                            tmem_ld_wait();
+                            if (c32 + 2 < 4) tmem_ld32(t_acc + (c32 + 2) * 32, va);
+                            epi_chunk_store(vb, b4 + (c32 + 1) * 4, blk, r, 4);
+                        }
+                        fence_proxy_async_smem();
+                        tc_fence_before();
+                        mbar_arrive(h ? r_hi : r_lo);
+                    } else if (h == 0) {
+                        uint32_t va[32], vb[32];
+                        tmem_ld32(t_acc, va);
+#pragma unroll 1
+                        for (int c32 = 0; c32 < 4; c32 += 2) {
+                            tmem_ld_wait();
+                            tmem_ld32(t_acc + (c32 + 1) * 32, vb);
+                            rgb_group<false>(va, rb4, wo4, nullptr, c32, o0, o1, o2);
+                            tmem_ld_wait();
+                            if (c32 + 2 < 4) tmem_ld32(t_acc + (c32 + 2) * 32, va);
+                            rgb_group<false>(vb, rb4, wo4, nullptr, c32 + 1, o0, o1, o2);
+                        }
+                    } else {
+                        // density head: accumulator column 128 of the last layer
+                        uint32_t vs[32];
+                        tmem_ld32(t_acc, vs);
+                        tmem_ld_wait();
+                        tc_fence_before();
+                        if (valid) {
+                            float4 res;
+                            res.x = __uint_as_float(vs[0]) + p.b_sigma;
+                            res.y = 1.0f / (1.0f + __expf(-(o0 + p.b_out0)));
+                            res.z = 1.0f / (1.0f + __expf(-(o1 + p.b_out1)));
+                            res.w = 1.0f / (1.0f + __expf(-(o2 + p.b_out2)));
+                            p.out[grow] = res;
+                        }
+                    }
+                }
+            }
+        }
+        if (!ok) record_abort(p);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem, 512);
+    }
+}
+
 // Per-ray bias of the RGB hidden layer: b'_ray = b' + W_rgb_hidden[:, 256:283] gamma(d).
 __global__ void k_ray_bias(const float* __restrict__ gd, int n_rays, const int* __restrict__ n_dev,
                            const float* __restrict__ Wd, const float* __restrict__ bprime,
@@ -604,7 +862,7 @@ __global__ void k_ray_bias(const float* __restrict__ gd, int n_rays, const int* 
 // The kernel variants (see Variant): precision, epilogue warps, staggered.
 struct TcVariant {
     int precision, epi_warps;
-    bool staggered;
+    bool staggered;             // FP8: staggered tiles; BF16: split schedule (own weight layout)
     void (*fn)(Params);
     int threads;
     uint32_t smem;
@@ -618,10 +876,12 @@ const TcVariant kVariants[] = {
     make_variant<false, 4, false>(), make_variant<false, 8, false>(),
     make_variant<true, 4, false>(),  make_variant<true, 8, false>(),
     make_variant<true, 4, true>(),   make_variant<true, 8, true>(),
+    TcVariant{MCL_PREC_BF16, 4, true, &k_mlp_tc_split, kSplitThreads, kSplitSmem},
 };
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
-// untuned choice per precision: BF16 4 warps lockstep, FP8 8 warps staggered
-constexpr int kDefaultVariant[3] = {-1, 0, 5};
+// untuned choice per precision (fastest measured at all sizes on GB300):
+// BF16 4 warps lockstep, FP8 4 warps staggered
+constexpr int kDefaultVariant[3] = {-1, 0, 4};
 
 struct TcForm {
     uint8_t* wblocks = nullptr;  // weight blocks in consumption order, 64-byte swizzled
@@ -629,7 +889,7 @@ struct TcForm {
 };
 
 struct TcState {
-    TcForm bf16, fp8;
+    TcForm bf16, fp8, bf16_split;
     float* aux = nullptr;      // fp32 biases, scales and small heads
     float* ray_bias = nullptr; // [max_rays][128]
     int* abort_flag = nullptr;
@@ -854,9 +1114,35 @@ int mlp_tc_prepare(mcl_map* m, const float* blob) {
         return out;
     };
     const std::vector<uint8_t> sw16 = swizzle(reinterpret_cast<const uint8_t*>(blk.data()), nb16);
+    // split-schedule BF16 blocks: [128 output rows x 64 k] per (layer, half,
+    // K chunk), 128-byte rows in the 128-byte swizzle; the last layer's half
+    // 1 holds the density head in its row 0
+    std::vector<uint8_t> spl((size_t)nb16 * kStageBytes, 0);
+    {
+        size_t bi = 0;
+        for (int l = 0; l < kLayers; ++l)
+            for (int h = 0; h < 2; ++h)
+                for (int k0 = 0; k0 < padded_k(l); k0 += 64, ++bi)
+                    for (int n = 0; n < 128; ++n) {
+                        const int row = h * 128 + n;
+                        if (l == 8 && h == 1 && n > 0) continue;
+                        for (int k = 0; k < 64; ++k) {
+                            const uint16_t w = f2bf((float)weight(l, row, k0 + k));
+                            const uint32_t byte = (uint32_t)n * 128u + (uint32_t)k * 2u;
+                            const uint32_t off = byte ^ (((byte >> 7) & 7u) << 4);
+                            spl[bi * kStageBytes + off] = (uint8_t)(w & 0xFF);
+                            spl[bi * kStageBytes + off + 1] = (uint8_t)(w >> 8);
+                        }
+                    }
+        if (bi != (size_t)nb16) return fail(MCL_ERR_UNSUPPORTED, "internal: split block count %zu", bi);
+    }
     const std::vector<uint8_t> sw8 = swizzle(blk8.data(), nb8);
     int rc;
-    if ((rc = cuda_check(cudaMalloc(&st->bf16.wblocks, sw16.size()), "cudaMalloc(tc weights)")) ||
+    if ((rc = cuda_check(cudaMalloc(&st->bf16_split.wblocks, spl.size()), "cudaMalloc(split weights)")) ||
+        (rc = cuda_check(cudaMemcpy(st->bf16_split.wblocks, spl.data(), spl.size(),
+                                    cudaMemcpyHostToDevice),
+                         "upload split weights")) ||
+        (rc = cuda_check(cudaMalloc(&st->bf16.wblocks, sw16.size()), "cudaMalloc(tc weights)")) ||
         (rc = cuda_check(cudaMemcpy(st->bf16.wblocks, sw16.data(), sw16.size(), cudaMemcpyHostToDevice),
                          "upload tc weights")) ||
         (rc = cuda_check(cudaMalloc(&st->fp8.wblocks, sw8.size()), "cudaMalloc(fp8 weights)")) ||
@@ -887,7 +1173,7 @@ int mlp_tc_prepare(mcl_map* m, const float* blob) {
                                                   (int)v.smem),
                              "smem attribute")))
             return rc;
-    st->bf16.ready = st->fp8.ready = true;
+    st->bf16.ready = st->fp8.ready = st->bf16_split.ready = true;
     return MCL_OK;
 }
 
@@ -896,6 +1182,7 @@ void mlp_tc_free(mcl_map* m) {
     if (!st) return;
     if (st->bf16.wblocks) cudaFree(st->bf16.wblocks);
     if (st->fp8.wblocks) cudaFree(st->fp8.wblocks);
+    if (st->bf16_split.wblocks) cudaFree(st->bf16_split.wblocks);
     if (st->aux) cudaFree(st->aux);
     if (st->ray_bias) cudaFree(st->ray_bias);
     if (st->abort_flag) cudaFree(st->abort_flag);
@@ -937,7 +1224,10 @@ static cudaError_t mlp_tc_variant(mcl_map* m, int precision, int variant, const 
     TcState* st = (TcState*)m->tc_aux;
     if (!mlp_tc_available(m, precision)) return cudaErrorNotSupported;
     Params p;
-    p.wblocks = precision == MCL_PREC_FP8 ? st->fp8.wblocks : st->bf16.wblocks;
+    const int vi = variant >= 0 ? variant : st->variant[precision];
+    p.wblocks = precision == MCL_PREC_FP8 ? st->fp8.wblocks
+                : kVariants[vi].fn == &k_mlp_tc_split ? st->bf16_split.wblocks
+                                                      : st->bf16.wblocks;
     p.rays = rays;
     p.z = z;
     p.S = S;
@@ -962,7 +1252,7 @@ static cudaError_t mlp_tc_variant(mcl_map* m, int precision, int variant, const 
     cudaError_t e = cudaMemsetAsync(st->abort_flag, 0, sizeof(int), s);
     if (e) return e;
     const long long grid = p.n_pairs < st->n_sm ? p.n_pairs : st->n_sm;
-    const TcVariant& v = kVariants[variant >= 0 ? variant : st->variant[precision]];
+    const TcVariant& v = kVariants[vi];
     note_launch();
     v.fn<<<(unsigned)grid, v.threads, v.smem, s>>>(p);
     return cudaGetLastError();
