@@ -210,6 +210,13 @@ int mcl_predict(const float* d_in, int N_in, const int32_t* d_idx, int N_out,
                 float sigma_t, float sigma_yaw, uint64_t seed,
                 uint64_t counter, float* d_out, void* stream);
 
+/* Prediction with odometry (Sec. III-A motion model x_t = x_{t-1} O_t
+ * Exp(delta)): as mcl_predict, with d_odom the device 3x4 row-major relative
+ * motion O_t between the two observations (NULL: O_t = I, mcl_predict). */
+int mcl_predict_odom(const float* d_in, int N_in, const int32_t* d_idx, int N_out,
+                     const float* d_odom, float sigma_t, float sigma_yaw, uint64_t seed,
+                     uint64_t counter, float* d_out, void* stream);
+
 /* Box downscale of Alg. 1 ("downscale(I_t, R_t)"): d_out[v][u] = mean of the
  * factor x factor block of d_image.  d_image [H,W,3] f32, d_out
  * [H/factor, W/factor, 3]. */

@@ -87,6 +87,7 @@ def lib():
             L.orc_normal.argtypes = [C.c_uint64] * 3
             L.orc_se3_exp.argtypes = [dp, dp, dp]
             L.orc_predict.argtypes = [C.c_int, dp, dp, dp]
+            L.orc_predict_odom.argtypes = [C.c_int, dp, dp, dp, dp]
             L.orc_motion_noise.argtypes = [C.c_int, C.c_uint64, C.c_uint64,
                                            C.c_double, C.c_double, dp]
             L.orc_position_spread.argtypes = [C.c_int, dp, dp]
@@ -393,11 +394,16 @@ def se3_exp(rho, omega):
     return M.reshape(3, 4)
 
 
-def predict(poses, noise):
+def predict(poses, noise, odom=None):
+    """x_t = x_{t-1} O_t Exp(delta) (odom: 3x4 O_t, default identity)."""
     P, pp = _d(np.reshape(poses, (-1, 12)))
     q, qp = _d(np.reshape(noise, (-1, 4)))
     out = np.zeros_like(P)
-    lib().orc_predict(P.shape[0], pp, qp, out.ctypes.data_as(C.POINTER(C.c_double)))
+    if odom is None:
+        lib().orc_predict(P.shape[0], pp, qp, out.ctypes.data_as(C.POINTER(C.c_double)))
+    else:
+        o, op_ = _d(np.reshape(odom, (12,)))
+        lib().orc_predict_odom(P.shape[0], pp, op_, qp, out.ctypes.data_as(C.POINTER(C.c_double)))
     return out
 
 

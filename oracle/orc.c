@@ -662,9 +662,24 @@ void orc_se3_exp(const double* rho, const double* om, double* M /*3x4*/) {
 
 /* out = pose * Exp(rho, (0, yaw, 0)) for n poses [n,12]; noise [n,4] =
  * (rho_x, rho_y, rho_z, yaw) in the body frame. */
-void orc_predict(int n, const double* pose, const double* noise, double* out) {
+/* Prediction with odometry (Sec. III-A motion model x_t = x_{t-1} O_t
+ * Exp(delta)): odom is the 3x4 relative motion O_t, or NULL for O_t = I. */
+void orc_predict_odom(int n, const double* pose, const double* odom, const double* noise,
+                      double* out) {
     for (int i = 0; i < n; ++i) {
-        const double* P = pose + 12 * (long)i;
+        const double* P0 = pose + 12 * (long)i;
+        double PO[12];
+        if (odom) {
+            for (int r = 0; r < 3; ++r)
+                for (int c = 0; c < 4; ++c) {
+                    double s = (c == 3) ? P0[4 * r + 3] : 0.0;
+                    for (int m = 0; m < 3; ++m) s += P0[4 * r + m] * odom[4 * m + c];
+                    PO[4 * r + c] = s;
+                }
+        } else {
+            for (int k = 0; k < 12; ++k) PO[k] = P0[k];
+        }
+        const double* P = PO;
         const double* q = noise + 4 * (long)i;
         double om[3] = {0.0, q[3], 0.0}, E[12];
         orc_se3_exp(q, om, E);
@@ -678,6 +693,10 @@ void orc_predict(int n, const double* pose, const double* noise, double* out) {
             }
         }
     }
+}
+
+void orc_predict(int n, const double* pose, const double* noise, double* out) {
+    orc_predict_odom(n, pose, NULL, noise, out);
 }
 
 /* Motion noise of particle k drawn from stream (seed, ctr): normals 4k..4k+3

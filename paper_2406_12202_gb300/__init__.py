@@ -126,6 +126,7 @@ def lib():
                                      C.POINTER(Opts), vp, vp, vp]
             L.mcl_resample.argtypes = [vp, vp, i32, i32, f64, vp, vp]
             L.mcl_predict.argtypes = [vp, i32, vp, i32, f32, f32, u64, u64, vp, vp]
+            L.mcl_predict_odom.argtypes = [vp, i32, vp, i32, vp, f32, f32, u64, u64, vp, vp]
             L.mcl_downscale.argtypes = [vp, i32, i32, i32, vp, vp]
             L.mcl_position_spread.argtypes = [vp, i32, vp, vp]
             L.mcl_read_status.argtypes = [vp, C.POINTER(C.c_int), vp]
@@ -473,14 +474,20 @@ def draw_pixels(W: int, H: int, B: int, seed: int, counter: int, out=None):
 
 
 def predict(poses, idx, n_out: int, sigma_t: float, sigma_yaw: float, seed: int, counter: int,
-            out=None):
+            out=None, odom=None):
+    """x_t = x_{t-1} (O_t) Exp(delta) (mcl_predict / mcl_predict_odom; odom:
+    a [12] f32 CUDA tensor, the 3x4 relative motion, or None)."""
     torch = _torch()
     if out is None:
         out = torch.empty(n_out, 12, dtype=torch.float32, device=poses.device)
-    _check(lib().mcl_predict(_ptr(poses, torch.float32, (poses.shape[0], 12), "poses"),
-                             poses.shape[0], _ptr(idx, torch.int32, (n_out,), "idx") if idx is not None else None,
-                             int(n_out), float(sigma_t), float(sigma_yaw), int(seed), int(counter),
-                             _ptr(out, torch.float32, (n_out, 12), "out"), _stream()))
+    args = (_ptr(poses, torch.float32, (poses.shape[0], 12), "poses"), poses.shape[0],
+            _ptr(idx, torch.int32, (n_out,), "idx") if idx is not None else None, int(n_out))
+    tail = (float(sigma_t), float(sigma_yaw), int(seed), int(counter),
+            _ptr(out, torch.float32, (n_out, 12), "out"), _stream())
+    if odom is None:
+        _check(lib().mcl_predict(*args, *tail))
+    else:
+        _check(lib().mcl_predict_odom(*args, _ptr(odom, torch.float32, (12,), "odom"), *tail))
     return out
 
 
@@ -510,6 +517,7 @@ EXPORTED = ("mcl_init_map", "mcl_destroy_map", "mcl_update", "mcl_render", "mcl_
             "mcl_resample_noalloc", "mcl_query", "mcl_draw_pixels", "mcl_localize",
             "mcl_proposal_set", "mcl_proposal_get", "mcl_render_histogram",
             "mcl_proposal_loss_grad", "mcl_proposal_train", "mcl_proposal_query", "mcl_autotune",
+            "mcl_predict_odom",
             "mcl_set_mlp_variant")
 
 # Kernel variants of the tensor-core MLP (include/mcl.h, MCL_MLP_VARIANTS):

@@ -485,17 +485,24 @@ extern "C" int mcl_resample(mcl_map* m, const double* d_w, int N_in, int N_out, 
                       "resample");
 }
 
-extern "C" int mcl_predict(const float* d_in, int N_in, const int32_t* d_idx, int N_out,
-                           float sigma_t, float sigma_yaw, uint64_t seed, uint64_t counter,
-                           float* d_out, void* stream) {
+extern "C" int mcl_predict_odom(const float* d_in, int N_in, const int32_t* d_idx, int N_out,
+                                const float* d_odom, float sigma_t, float sigma_yaw, uint64_t seed,
+                                uint64_t counter, float* d_out, void* stream) {
     g_err[0] = 0;
     if (!d_in || !d_out || N_out < 1 || N_in < 1) return fail(MCL_ERR_ARG, "mcl_predict: bad argument");
     if (!d_idx && N_out > N_in) return fail(MCL_ERR_ARG, "mcl_predict: N_out > N_in without an index");
     if (!(sigma_t >= 0.f) || !(sigma_yaw >= 0.f)) return fail(MCL_ERR_ARG, "mcl_predict: negative sigma");
     if (d_in == d_out && d_idx) return fail(MCL_ERR_ARG, "mcl_predict: in-place gather is not allowed");
-    return cuda_check(launch_predict(d_in, N_in, d_idx, N_out, sigma_t, sigma_yaw, seed, counter, d_out,
-                                     (cudaStream_t)stream),
+    return cuda_check(launch_predict(d_in, N_in, d_idx, N_out, d_odom, sigma_t, sigma_yaw, seed, counter,
+                                     d_out, (cudaStream_t)stream),
                       "predict");
+}
+
+extern "C" int mcl_predict(const float* d_in, int N_in, const int32_t* d_idx, int N_out,
+                           float sigma_t, float sigma_yaw, uint64_t seed, uint64_t counter,
+                           float* d_out, void* stream) {
+    return mcl_predict_odom(d_in, N_in, d_idx, N_out, nullptr, sigma_t, sigma_yaw, seed, counter,
+                            d_out, stream);
 }
 
 extern "C" int mcl_downscale(const float* d_image, int W, int H, int factor, float* d_out,

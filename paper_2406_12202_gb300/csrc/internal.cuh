@@ -177,9 +177,9 @@ cudaError_t mlp_tc(mcl_map* m, int precision, const Ray* rays, const float* gd, 
 // resample.cu
 cudaError_t launch_resample(const double* w, int n_in, int n_out, double u0, int32_t* idx,
                             unsigned long long* cdf, Status* status, cudaStream_t s);
-cudaError_t launch_predict(const float* in, int n_in, const int32_t* idx, int n_out, float sigma_t,
-                           float sigma_yaw, uint64_t seed, uint64_t counter, float* out,
-                           cudaStream_t s);
+cudaError_t launch_predict(const float* in, int n_in, const int32_t* idx, int n_out,
+                           const float* odom, float sigma_t, float sigma_yaw, uint64_t seed,
+                           uint64_t counter, float* out, cudaStream_t s);
 cudaError_t launch_downscale(const float* img, int W, int H, int f, float* out, cudaStream_t s);
 cudaError_t launch_position_spread(const float* poses, int N, double* out, cudaStream_t s);
 

@@ -26,8 +26,8 @@ cudaError_t launch_resample(const double* w, int n_in, int n_out, double u0, int
 
 // Prediction: out_k = in_{idx_k} * Exp(rho, (0, yaw, 0)) (stages.cuh).
 __global__ void k_predict(const float* __restrict__ in, int n_in, const int32_t* __restrict__ idx,
-                          int n, float sigma_t, float sigma_yaw, uint64_t seed, uint64_t ctr,
-                          float* __restrict__ out) {
+                          int n, const float* __restrict__ odom, float sigma_t, float sigma_yaw,
+                          uint64_t seed, uint64_t ctr, float* __restrict__ out) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
     const int src = idx ? idx[k] : k;
@@ -38,15 +38,15 @@ __global__ void k_predict(const float* __restrict__ in, int n_in, const int32_t*
     }
     double q[4];
     motion_noise(seed, ctr, k, sigma_t, sigma_yaw, q);
-    predict_pose(in + 12 * (size_t)src, q, O);
+    predict_pose(in + 12 * (size_t)src, q, O, odom);
 }
 
-cudaError_t launch_predict(const float* in, int n_in, const int32_t* idx, int n_out, float sigma_t,
-                           float sigma_yaw, uint64_t seed, uint64_t counter, float* out,
-                           cudaStream_t s) {
+cudaError_t launch_predict(const float* in, int n_in, const int32_t* idx, int n_out,
+                           const float* odom, float sigma_t, float sigma_yaw, uint64_t seed,
+                           uint64_t counter, float* out, cudaStream_t s) {
     note_launch();
-    k_predict<<<(n_out + 127) / 128, 128, 0, s>>>(in, n_in, idx, n_out, sigma_t, sigma_yaw, seed, counter,
-                                                   out);
+    k_predict<<<(n_out + 127) / 128, 128, 0, s>>>(in, n_in, idx, n_out, odom, sigma_t, sigma_yaw, seed,
+                                                   counter, out);
     return cudaGetLastError();
 }
 

@@ -379,8 +379,26 @@ __device__ __forceinline__ bool resample_block(const double* __restrict__ w, int
 // K = [omega]x, th = |omega|, a = sin th / th, b = (1 - cos th)/th^2,
 // c = (th - sin th)/th^3 (series values below th = 1e-8).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void predict_pose(const float* __restrict__ P, const double q[4],
-                                             float* __restrict__ O) {
+// x Exp(delta) for the pose P (optionally x O_t Exp(delta): odom is the 3x4
+// relative motion O_t, NULL for the identity), FP64 arithmetic.
+__device__ __forceinline__ void predict_pose(const float* __restrict__ P0, const double q[4],
+                                             float* __restrict__ O,
+                                             const float* __restrict__ odom = nullptr) {
+    double P[12];
+    if (odom) {
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                double s = (c == 3) ? (double)P0[4 * r + 3] : 0.0;
+#pragma unroll
+                for (int m = 0; m < 3; ++m) s += (double)P0[4 * r + m] * (double)odom[4 * m + c];
+                P[4 * r + c] = s;
+            }
+    } else {
+#pragma unroll
+        for (int k = 0; k < 12; ++k) P[k] = (double)P0[k];
+    }
     const double om[3] = {0.0, q[3], 0.0};
     const double th2 = om[0] * om[0] + om[1] * om[1] + om[2] * om[2];
     const double th = sqrt(th2);
@@ -415,9 +433,9 @@ __device__ __forceinline__ void predict_pose(const float* __restrict__ P, const 
     for (int r = 0; r < 3; ++r)
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
-            double s = (c == 3) ? (double)P[4 * r + 3] : 0.0;
+            double s = (c == 3) ? P[4 * r + 3] : 0.0;
 #pragma unroll
-            for (int m = 0; m < 3; ++m) s += (double)P[4 * r + m] * E[4 * m + c];
+            for (int m = 0; m < 3; ++m) s += P[4 * r + m] * E[4 * m + c];
             O[4 * r + c] = (float)s;
         }
 }

@@ -172,6 +172,21 @@ def test_predict_matches_oracle(M):
     assert np.allclose(out, ref, rtol=0, atol=3e-6)
 
 
+def test_predict_with_odometry_matches_oracle(M):
+    """x_t = x_{t-1} O_t Exp(delta) (Sec. III-A) through mcl_predict_odom;
+    FP64 arithmetic on both sides, FP32 results: 3e-6 absolute."""
+    import torch
+    P = synth.random_particles(13, 200)[0].astype(np.float32)
+    idx = np.random.default_rng(13).integers(0, 200, size=256).astype(np.int32)
+    O = synth.pose_from_xyz_yaw([[0.05, 0.0, -0.1]], [0.03])[0].astype(np.float32)
+    seed, ctr, st, sy = 78, 5, 0.02, 0.01
+    out = M.predict(torch.tensor(P, device="cuda"), torch.tensor(idx, device="cuda"), 256, st, sy,
+                    seed, ctr, odom=torch.tensor(O, device="cuda")).cpu().numpy()
+    noise = oracle.motion_noise(256, seed, ctr, float(np.float32(st)), float(np.float32(sy)))
+    ref = oracle.predict(P.astype(np.float64)[idx], noise, odom=O.astype(np.float64))
+    assert np.allclose(out, ref, rtol=0, atol=3e-6)
+
+
 def test_downscale_and_spread(M):
     import torch
     img = synth.smooth_image(11, 400, 400)

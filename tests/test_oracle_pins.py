@@ -513,6 +513,25 @@ def test_predict_identity_and_inverse():
     assert np.allclose(Q[:, :, 3], R0[:, :, 3], atol=1e-15)
 
 
+def test_predict_with_odometry_matrix_product():
+    """x_t = x_{t-1} O_t Exp(delta) (Sec. III-A): against 4x4 homogeneous
+    products with scipy's matrix exponential of the noise twist."""
+    from scipy.linalg import expm
+    rng = np.random.default_rng(21)
+    P, _, _ = synth.random_particles(21, 12)
+    O = synth.pose_from_xyz_yaw([[0.3, -0.1, 0.2]], [0.4])[0]
+    q = rng.normal(0, 0.1, (12, 4))
+    out = oracle.predict(P, q, odom=O)
+    h = lambda m: np.vstack([np.reshape(m, (3, 4)), [0, 0, 0, 1]])
+    for i in range(12):
+        ref = h(P[i]) @ h(O) @ expm(_twist(q[i, :3], np.array([0.0, q[i, 3], 0.0])))
+        assert np.allclose(out[i], ref[:3].reshape(12), atol=1e-13)
+    # zero noise: the pure odometry step, and the identity odometry is the default
+    assert np.allclose(oracle.predict(P, np.zeros((12, 4)), odom=O),
+                       np.stack([(h(P[i]) @ h(O))[:3].reshape(12) for i in range(12)]), atol=1e-14)
+    assert np.array_equal(oracle.predict(P, q, odom=np.eye(4)[:3].reshape(12)), oracle.predict(P, q))
+
+
 def test_position_spread_closed_form():
     P = synth.pose_from_xyz_yaw([[0, 0, 0], [2, 0, 0], [0, 4, 0]], [0, 1, 2])
     s = oracle.position_spread(P)
