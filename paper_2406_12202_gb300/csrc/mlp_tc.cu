@@ -843,6 +843,244 @@ __global__ void __launch_bounds__(kSplitThreads, 1) k_mlp_tc_split(const __grid_
     }
 }
 
+// ---------------------------------------------------------------------------
+// BF16, pipelined single tile: one 128-row tile per CTA at a time, its
+// accumulators double-buffered in TMEM (layer l in columns 256 (l & 1) ..
+// +255), and the activation columns handed to the next layer 64 at a time:
+// the epilogue of layer l releases K chunks 2q, 2q + 1 of layer l + 1 as
+// soon as it has written columns 64q .. 64q + 63, so the MMAs of layer l + 1
+// run under the rest of layer l's epilogue.  Nine-stage weight ring (more
+// than a layer), same weight blocks and arithmetic as the lockstep kernel.
+struct __align__(8) PipeBars {
+    uint64_t full[9];
+    uint64_t empty[9];
+    uint64_t acc_full[2];
+    uint64_t q_ready[4];
+    uint64_t gx_ready;
+    uint64_t drain;
+    uint32_t tmem_base;
+};
+constexpr int kPipeStages = 9;
+constexpr int kPipeThreads = 64 + 128;
+constexpr uint32_t kPipeSmem = 1024 + Form<false>::kActBytes + kGxBytes + kPipeStages * kStageBytes;
+static_assert(kPipeSmem <= 232448, "pipelined kernel shared memory");
+
+__global__ void __launch_bounds__(kPipeThreads, 1) k_mlp_tc_pipe(const __grid_constant__ Params p) {
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ PipeBars bars;
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const uint32_t s_act = smem_u32(smem);
+    const uint32_t s_gx = s_act + Form<false>::kActBytes;
+    const uint32_t s_ring = s_gx + kGxBytes;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    volatile int* abort_flag = p.abort_flag;
+    const long long M = p.M_dev ? min(p.M, (long long)*p.M_dev) : p.M;
+    const long long n_tiles = (M + 127) / 128;
+    if (tid == 0) {
+        for (int i = 0; i < kPipeStages; ++i) {
+            mbar_init(smem_u32(&bars.full[i]), 1);
+            mbar_init(smem_u32(&bars.empty[i]), 1);
+        }
+        for (int b = 0; b < 2; ++b) mbar_init(smem_u32(&bars.acc_full[b]), 1);
+        for (int q = 0; q < 4; ++q) mbar_init(smem_u32(&bars.q_ready[q]), 128);
+        mbar_init(smem_u32(&bars.gx_ready), 128);
+        mbar_init(smem_u32(&bars.drain), 1);
+        fence_mbar_init();
+    }
+    if (warp == 1) {
+        tmem_alloc(smem_u32(&bars.tmem_base), 512);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = bars.tmem_base;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            uint32_t g = 0;
+            bool ok = true;
+            for (long long t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
+                for (int b = 0; b < Form<false>::kBlocks; ++b, ++g) {
+                    const uint32_t st = g % kPipeStages, ph = (g / kPipeStages) & 1u;
+                    if (!mbar_wait(smem_u32(&bars.empty[st]), ph ^ 1u, abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_arrive_expect_tx(smem_u32(&bars.full[st]), kStageBytes);
+                    bulk_load(s_ring + st * kStageBytes, p.wblocks + (size_t)b * kStageBytes,
+                              kStageBytes, smem_u32(&bars.full[st]));
+                }
+            }
+            if (!ok) record_abort(p);
+            for (uint32_t k = 0; k < (uint32_t)kPipeStages && k < g; ++k) {
+                const uint32_t gl = g - 1 - k;
+                mbar_wait(smem_u32(&bars.full[gl % kPipeStages]), (gl / kPipeStages) & 1u, nullptr);
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            uint32_t g = 0, ph_bits = 0;   // bit q: parity of q_ready[q]; bit 4: gx_ready
+            bool ok = true;
+            const uint32_t id256 = idesc_bf16(128, 256), id144 = idesc_bf16(128, 144);
+            for (long long t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
+                for (int l = 0; l < kLayers && ok; ++l) {
+                    const int nch = c_chunks[0][l];
+                    const uint32_t idesc = (l == 8) ? id144 : id256;
+                    const uint32_t d = tmem + (l & 1) * 256;
+                    for (int c = 0; c < nch && ok; ++c) {
+                        const uint32_t st = g % kPipeStages, ph = (g / kPipeStages) & 1u;
+                        if (!mbar_wait(smem_u32(&bars.full[st]), ph, abort_flag)) {
+                            ok = false;
+                            break;
+                        }
+                        // A chunk written: gamma(x) (layer 0) or columns 64q .. +63
+                        // of the previous layer's output (chunks 2q, 2q + 1);
+                        // phase parities kept as bits of one register
+                        int wsel = -1;
+                        if (l == 0 && c == 0) wsel = 4;
+                        else if (l > 0 && c < 8 && (c & 1) == 0) wsel = c >> 1;
+                        if (wsel >= 0) {
+                            const uint32_t wb = wsel == 4 ? smem_u32(&bars.gx_ready)
+                                                          : smem_u32(&bars.q_ready[wsel]);
+                            const uint32_t wp = (ph_bits >> wsel) & 1u;
+                            if (!mbar_wait(wb, wp, abort_flag)) {
+                                ok = false;
+                                break;
+                            }
+                            ph_bits ^= 1u << wsel;
+                            tc_fence_after();
+                        }
+#pragma unroll
+                        for (int kk = 0; kk < 2; ++kk) {
+                            uint32_t a_addr;
+                            if (l == 0) a_addr = s_gx + (c * 2 + kk) * 32;
+                            else if (l == 5 && c >= 8) a_addr = s_gx + ((c - 8) * 2 + kk) * 32;
+                            else {
+                                const int ks = c * 2 + kk;
+                                a_addr = s_act + (ks >> 2) * 16384 + (ks & 3) * 32;
+                            }
+                            const uint64_t ad = smem_desc(a_addr, 1024, kLayoutSw128);
+                            const uint64_t bd = smem_desc(s_ring + st * kStageBytes + kk * 32, 512, kLayoutSw64);
+                            mma_bf16(d, ad, bd, idesc, (c | kk) ? 1u : 0u);
+                        }
+                        mma_commit(smem_u32(&bars.empty[st]));
+                        ++g;
+                    }
+                    if (ok) mma_commit(smem_u32(&bars.acc_full[l & 1]));
+                }
+            }
+            if (!ok) record_abort(p);
+            mma_commit(smem_u32(&bars.drain));
+            mbar_wait(smem_u32(&bars.drain), 0, nullptr);
+        }
+    } else {
+        const int quad = warp & 3;
+        const uint32_t r = quad * 32 + lane;
+        const uint32_t t_lane = tmem + ((uint32_t)(quad * 32) << 16);
+        uint32_t ph_acc[2] = {0, 0};
+        bool ok = true;
+        for (long long t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
+            const long long grow = t * 128 + r;
+            const bool valid = grow < M;
+            const long long ray = valid ? grow / p.S : 0;
+            {
+                float x[3] = {0.f, 0.f, 0.f};
+                if (valid) {
+                    const Ray R = p.rays[ray];
+                    const float zz = p.z[grow];
+                    x[0] = fmaf(zz, R.dx, R.ox);
+                    x[1] = fmaf(zz, R.dy, R.oy);
+                    x[2] = fmaf(zz, R.dz, R.oz);
+                }
+                for (int half = 0; half < 2; ++half) {
+                    float v[32];
+                    if (valid) {
+                        if (half == 0) pe_half<0>(x, v);
+                        else pe_half<1>(x, v);
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < 32; ++i) v[i] = 0.0f;
+                    }
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        st_shared_v4(s_gx + sw128_offset(r, 4 * half + j), pack_bf16x2(v[8 * j], v[8 * j + 1]),
+                                     pack_bf16x2(v[8 * j + 2], v[8 * j + 3]),
+                                     pack_bf16x2(v[8 * j + 4], v[8 * j + 5]),
+                                     pack_bf16x2(v[8 * j + 6], v[8 * j + 7]));
+                }
+                fence_proxy_async_smem();
+                tc_fence_before();
+                mbar_arrive(smem_u32(&bars.gx_ready));
+            }
+            for (int l = 0; l < kLayers && ok; ++l) {
+                const int b = l & 1;
+                if (!mbar_wait(smem_u32(&bars.acc_full[b]), ph_acc[b], abort_flag)) {
+                    ok = false;
+                    break;
+                }
+                ph_acc[b] ^= 1u;
+                tc_fence_after();
+                const uint32_t t_acc = t_lane + b * 256;
+                if (l < 8) {
+                    // 64 columns at a time (one 128-byte K block of the next
+                    // layer), each released to the MMAs as soon as it is stored
+                    const uint4* b4 = reinterpret_cast<const uint4*>(p.bias2 + l * 128);
+                    uint32_t va[32], vb[32];
+                    tmem_ld32(t_acc, va);
+#pragma unroll 1
+                    for (int q = 0; q < 4; ++q) {
+                        tmem_ld_wait();
+                        tmem_ld32(t_acc + (2 * q + 1) * 32, vb);
+                        const uint32_t blk = s_act + q * 16384;
+                        epi_chunk_store(va, b4 + (2 * q) * 4, blk, r, 0);
+                        tmem_ld_wait();
+                        if (q + 1 < 4) tmem_ld32(t_acc + (2 * q + 2) * 32, va);
+                        epi_chunk_store(vb, b4 + (2 * q + 1) * 4, blk, r, 4);
+                        fence_proxy_async_smem();
+                        tc_fence_before();
+                        mbar_arrive(smem_u32(&bars.q_ready[q]));
+                    }
+                } else {
+                    const float4* rb4 = reinterpret_cast<const float4*>(p.ray_bias + ray * 128);
+                    const float4* wo4 = reinterpret_cast<const float4*>(p.w_out);
+                    float o0 = 0.f, o1 = 0.f, o2 = 0.f;
+                    uint32_t va[32], vb[32];
+                    tmem_ld32(t_acc, va);
+#pragma unroll 1
+                    for (int c32 = 0; c32 < 4; c32 += 2) {
+                        tmem_ld_wait();
+                        tmem_ld32(t_acc + (c32 + 1) * 32, vb);
+                        rgb_group<false>(va, rb4, wo4, nullptr, c32, o0, o1, o2);
+                        tmem_ld_wait();
+                        if (c32 + 2 < 4) tmem_ld32(t_acc + (c32 + 2) * 32, va);
+                        rgb_group<false>(vb, rb4, wo4, nullptr, c32 + 1, o0, o1, o2);
+                    }
+                    uint32_t vs[32];
+                    tmem_ld32(t_acc + 128, vs);
+                    tmem_ld_wait();
+                    tc_fence_before();
+                    if (valid) {
+                        float4 res;
+                        res.x = __uint_as_float(vs[0]) + p.b_sigma;
+                        res.y = 1.0f / (1.0f + __expf(-(o0 + p.b_out0)));
+                        res.z = 1.0f / (1.0f + __expf(-(o1 + p.b_out1)));
+                        res.w = 1.0f / (1.0f + __expf(-(o2 + p.b_out2)));
+                        p.out[grow] = res;
+                    }
+                }
+            }
+        }
+        if (!ok) record_abort(p);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem, 512);
+    }
+}
+
 // Per-ray bias of the RGB hidden layer: b'_ray = b' + W_rgb_hidden[:, 256:283] gamma(d).
 __global__ void k_ray_bias(const float* __restrict__ gd, int n_rays, const int* __restrict__ n_dev,
                            const float* __restrict__ Wd, const float* __restrict__ bprime,
@@ -877,6 +1115,7 @@ const TcVariant kVariants[] = {
     make_variant<true, 4, false>(),  make_variant<true, 8, false>(),
     make_variant<true, 4, true>(),   make_variant<true, 8, true>(),
     TcVariant{MCL_PREC_BF16, 4, true, &k_mlp_tc_split, kSplitThreads, kSplitSmem},
+    TcVariant{MCL_PREC_BF16, 4, false, &k_mlp_tc_pipe, kPipeThreads, kPipeSmem},
 };
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 // untuned choice per precision (fastest measured at all sizes on GB300):
@@ -1251,7 +1490,10 @@ static cudaError_t mlp_tc_variant(mcl_map* m, int precision, int variant, const 
     p.status_code = &m->status->code;
     cudaError_t e = cudaMemsetAsync(st->abort_flag, 0, sizeof(int), s);
     if (e) return e;
-    const long long grid = p.n_pairs < st->n_sm ? p.n_pairs : st->n_sm;
+    // persistent grid: one CTA per SM at most, one per work unit (a pair of
+    // tiles, or a single tile for the pipelined kernel)
+    const long long units = kVariants[vi].fn == &k_mlp_tc_pipe ? (p.M + 127) / 128 : p.n_pairs;
+    const long long grid = units < st->n_sm ? units : st->n_sm;
     const TcVariant& v = kVariants[vi];
     note_launch();
     v.fn<<<(unsigned)grid, v.threads, v.smem, s>>>(p);
