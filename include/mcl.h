@@ -368,6 +368,8 @@ int mcl_proposal_train(mcl_map* map, const float* d_poses, int n_poses,
  *   0 BF16 4 lockstep   1 BF16 8 lockstep   2 FP8 4 lockstep
  *   3 FP8 8 lockstep    4 FP8 4 staggered   5 FP8 8 staggered
  *   6 BF16 4 split      7 BF16 4 pipelined (one tile per CTA)
+ *   8 BF16 4 lockstep, CTA pair   9 FP8 4 lockstep, CTA pair
+ *  10 FP8 4 staggered, CTA pair
  * Lockstep: each streamed weight block serves both tiles of a pair at once;
  * staggered: the second tile runs each layer after the first on the resident
  * blocks, so one tile's epilogue overlaps the other's MMAs (FP8 only: a BF16
@@ -375,9 +377,11 @@ int mcl_proposal_train(mcl_map* map, const float* d_poses, int n_poses,
  * 128-column halves whose epilogues overlap the MMAs of the other half and
  * of the next layer; pipelined: one tile per CTA with double-buffered
  * accumulators, the next layer's MMAs consuming the activations 64 columns
- * at a time as the epilogue writes them.  All variants of a precision give bit-identical
- * results.  Untuned defaults: 0 (BF16) and 4 (FP8). */
-#define MCL_MLP_VARIANTS 8
+ * at a time as the epilogue writes them; CTA pair: clusters of two CTAs on
+ * the two SMs of a TPC issue 256-row MMAs (tcgen05 cta_group::2), each CTA
+ * streaming half of every weight block.  All variants of a precision give
+ * bit-identical results.  Untuned defaults: 0 (BF16) and 4 (FP8). */
+#define MCL_MLP_VARIANTS 11
 
 /* Autotuner: time every variant of `precision` (MCL_PREC_BF16 or _FP8) on
  * `rows` synthetic samples (256 <= rows <= max_rays * min(64, max_samples);

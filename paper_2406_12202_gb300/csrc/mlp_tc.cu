@@ -42,19 +42,21 @@
 // epilogue and the TMA producer for the first two tile pairs.
 constexpr int kTraceSlots = 16, kTraceLen = 128;
 __device__ unsigned long long g_tc_trace[kTraceSlots * kTraceLen];
-#define TC_TRACE(slot, idx)                                                           \
+#define TC_TRACE_CTA(cta, slot, idx)                                                  \
     do {                                                                              \
-        if (blockIdx.x == 0 && (slot) < kTraceSlots && (idx) < kTraceLen)             \
+        if (blockIdx.x == (cta) && (slot) < kTraceSlots && (idx) < kTraceLen)         \
             g_tc_trace[(slot) * kTraceLen + (idx)] = mcl::tc::globaltimer();          \
     } while (0)
+#define TC_TRACE(slot, idx) TC_TRACE_CTA(0, slot, idx)
 extern "C" int mcl_tc_trace_read(unsigned long long* out, int n) {
     const int m = n < kTraceSlots * kTraceLen ? n : kTraceSlots * kTraceLen;
     return (int)cudaMemcpyFromSymbol(out, g_tc_trace, sizeof(unsigned long long) * m);
 }
 #else
-#define TC_TRACE(slot, idx) \
-    do {                    \
+#define TC_TRACE_CTA(cta, slot, idx) \
+    do {                             \
     } while (0)
+#define TC_TRACE(slot, idx) TC_TRACE_CTA(0, slot, idx)
 #endif
 
 namespace mcl {
@@ -93,10 +95,8 @@ template <bool F8, int EPIW, bool STAG>
 struct Variant {
     static_assert(EPIW == 4 || EPIW == 8, "epilogue warps");
     static_assert(!STAG || F8, "a BF16 layer does not fit in the weight ring");
-    static constexpr int kEpiWarps = EPIW;
-    static constexpr int kHalves = EPIW / 4;          // column groups per TMEM lane quadrant
     static constexpr int kEpiThreads = 32 * EPIW;
-    static constexpr int kThreads = 64 + 2 * kEpiThreads;   // + TMA warp + MMA warp
+    static constexpr int kThreads = 96 + 2 * kEpiThreads;   // + TMA, MMA and gate warps
 };
 
 // K chunks (one weight block each) per layer: trunk1 reads gamma(x) (64),
@@ -241,6 +241,200 @@ __device__ __forceinline__ void rgb_group(const uint32_t (&v)[32], const float4*
     }
 }
 
+// Operand writes of one thread (activations or gamma(x)) and its TMEM reads
+// are done: make the writes visible to the tensor core and signal the MMA
+// issuer.  Single CTA: every epilogue thread arrives on the local barrier.
+// CTA pair: the MMAs are issued by the even CTA, whose barrier counts one
+// arrival per epilogue warp of both CTAs (cluster scope).
+template <bool PAIR>
+__device__ __forceinline__ void signal_ready(uint32_t bar, int lane) {
+    fence_proxy_async_smem();
+    tc_fence_before();
+    if constexpr (PAIR) {
+        __syncwarp();
+        if (lane == 0) mbar_arrive_cluster(bar);
+    } else {
+        mbar_arrive(bar);
+    }
+}
+
+// Prologue and epilogues of the epilogue warps (warps warp0 .. warp0 + 2 EPIW - 1)
+// over the CTA's work units: unit u holds rows u unit_rows + row_base ..
+// +255 of the pass, tile slot s its rows + 128 s .. +127.  Per unit: gamma(x)
+// into the slot's buffer, then per layer TMEM -> bias + ReLU (and the FP8
+// scales) -> the next layer's A operand, and after the last layer the RGB
+// output layer and the density.  PAIR: bar_ready* are shared::cluster
+// addresses of the even CTA's barriers.
+template <bool F8, int EPIW, bool PAIR>
+__device__ __forceinline__ void epilogue_warps(const Params& p, int warp, int warp0, int lane, uint32_t tmem,
+                                               uint32_t s_act, uint32_t s_gx, uint32_t bar_ready0,
+                                               uint32_t bar_ready1, uint32_t bar_acc0,
+                                               uint32_t bar_acc1, long long M, long long u0,
+                                               long long du, long long n_units, long long unit_rows,
+                                               long long row_base) {
+    volatile int* abort_flag = p.abort_flag;
+    // EPIW warps per tile: warp w covers TMEM lane quadrant (w % 4), i.e.
+    // rows 32 (w % 4) .. +31; with 8 warps the first four take accumulator
+    // columns 0..127 and the other four 128..255 (column halves h0 .. h1 - 1
+    // of 128); one thread owns one row.
+    constexpr int kH = EPIW / 4;
+    constexpr uint32_t kActBytes = Form<F8>::kActBytes;
+    const int slot = (warp - warp0) / EPIW;
+    const int h0 = kH == 2 ? (((warp - warp0) >> 2) & 1) : 0;
+    const int h1 = h0 + 3 - kH;                       // one half, or both
+    const int quad = warp & 3;
+    const uint32_t r = quad * 32 + lane;              // row within the tile
+    const uint32_t t_row = tmem + ((uint32_t)(quad * 32) << 16) + slot * 256;
+    const uint32_t a_base = s_act + slot * kActBytes;
+    const uint32_t g_base = s_gx + slot * kGxBytes;
+    const uint32_t bar_ready = slot ? bar_ready1 : bar_ready0;
+    const uint32_t bar_acc = slot ? bar_acc1 : bar_acc0;
+    uint32_t acc_ph = 0;
+    bool ok = true;
+    const bool tracer = (r == 0 && h0 == 0);
+    int tl = 0;
+    for (long long pr = u0; pr < n_units && ok; pr += du) {
+        const long long grow = pr * unit_rows + row_base + slot * 128 + r;
+        const bool valid = grow < M;
+        const long long ray = valid ? grow / p.S : 0;
+        // ---- prologue: this thread's halves of gamma(x) into the tile's
+        //      gamma(x) buffer
+        {
+            float x[3] = {0.f, 0.f, 0.f};
+            if (valid) {
+                const Ray R = p.rays[ray];
+                const float zz = p.z[grow];
+                x[0] = fmaf(zz, R.dx, R.ox);
+                x[1] = fmaf(zz, R.dy, R.oy);
+                x[2] = fmaf(zz, R.dz, R.oz);
+            }
+            for (int half = h0; half < h1; ++half) {
+                float v[32];
+                if (valid) {
+                    if (half == 0) pe_half<0>(x, v);
+                    else pe_half<1>(x, v);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) v[i] = 0.0f;
+                }
+                if constexpr (F8) {
+                    const float sg = p.s_gx;
+#pragma unroll
+                    for (int j = 0; j < 2; ++j) {
+                        uint32_t w[4];
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const int i = 16 * j + 4 * e;
+                            w[e] = pack_e4m3x4(v[i] * sg, v[i + 1] * sg, v[i + 2] * sg,
+                                               v[i + 3] * sg);
+                        }
+                        st_shared_v4(g_base + sw128_offset(r, 2 * half + j), w[0], w[1], w[2], w[3]);
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        st_shared_v4(g_base + sw128_offset(r, 4 * half + j),
+                                     pack_bf16x2(v[8 * j], v[8 * j + 1]),
+                                     pack_bf16x2(v[8 * j + 2], v[8 * j + 3]),
+                                     pack_bf16x2(v[8 * j + 4], v[8 * j + 5]),
+                                     pack_bf16x2(v[8 * j + 6], v[8 * j + 7]));
+                }
+            }
+            signal_ready<PAIR>(bar_ready, lane);
+        }
+        float sigma = 0.0f;
+        for (int l = 0; l < kLayers && ok; ++l, ++tl) {
+            if (!(PAIR ? mbar_wait_cluster<true>(bar_acc, acc_ph, abort_flag)
+                       : mbar_wait_sleep(bar_acc, acc_ph, abort_flag))) {
+                ok = false;
+                break;
+            }
+            if (tracer) TC_TRACE(6 + 2 * slot, tl);
+            acc_ph ^= 1u;
+            tc_fence_after();
+            if (l < 8) {
+                // this thread's columns, 32 at a time, the next TMEM load
+                // in flight while the current group is stored
+                for (int half = h0; half < h1; ++half) {
+                    const uint32_t t_acc = t_row + half * 128;
+                    uint32_t va[32], vb[32];
+                    tmem_ld32(t_acc, va);
+                    if constexpr (F8) {
+                        // h = relu(acc alpha + beta) in FP32, stored as E4M3:
+                        // columns 128 half .. +127 are K-block `half`, chunks 0..7
+                        const float alpha = p.alpha[l];
+                        const float4* b4 =
+                            reinterpret_cast<const float4*>(p.beta + l * 256 + half * 128);
+                        const uint32_t blk = a_base + half * 16384;
+#pragma unroll 1
+                        for (int c32 = 0; c32 < 4; c32 += 2) {
+                            tmem_ld_wait();
+                            tmem_ld32(t_acc + (c32 + 1) * 32, vb);
+                            epi_chunk_store_f8(va, alpha, b4 + c32 * 8, blk, r, c32 * 2);
+                            tmem_ld_wait();
+                            if (c32 + 2 < 4) tmem_ld32(t_acc + (c32 + 2) * 32, va);
+                            epi_chunk_store_f8(vb, alpha, b4 + (c32 + 1) * 8, blk, r,
+                                               (c32 + 1) * 2);
+                        }
+                    } else {
+                        // h = relu(acc + b): accumulators rounded to BF16 pairs,
+                        // bias added and ReLU applied in packed BF16 arithmetic;
+                        // columns 128 half .. +127 are K-blocks 2 half, 2 half + 1
+                        const uint4* b4 =
+                            reinterpret_cast<const uint4*>(p.bias2 + l * 128 + half * 64);
+#pragma unroll 1
+                        for (int c32 = 0; c32 < 4; c32 += 2) {
+                            tmem_ld_wait();
+                            tmem_ld32(t_acc + (c32 + 1) * 32, vb);
+                            const uint32_t blk = a_base + (2 * half + (c32 >> 1)) * 16384;
+                            epi_chunk_store(va, b4 + c32 * 4, blk, r, 0);
+                            tmem_ld_wait();
+                            if (c32 + 2 < 4) tmem_ld32(t_acc + (c32 + 2) * 32, va);
+                            epi_chunk_store(vb, b4 + (c32 + 1) * 4, blk, r, 4);
+                        }
+                    }
+                }
+                if (tracer) TC_TRACE(7 + 2 * slot, tl);
+                signal_ready<PAIR>(bar_ready, lane);
+            } else if (h0 == 0) {
+                const float4* rb4 = reinterpret_cast<const float4*>(p.ray_bias + ray * 128);
+                const float4* wo4 = reinterpret_cast<const float4*>(p.w_out);
+                const float4* al4 = reinterpret_cast<const float4*>(p.alpha_last);
+                float o0 = 0.f, o1 = 0.f, o2 = 0.f;
+                uint32_t va[32], vb[32];
+                tmem_ld32(t_row, va);
+#pragma unroll 1
+                for (int c32 = 0; c32 < 4; c32 += 2) {
+                    tmem_ld_wait();
+                    tmem_ld32(t_row + (c32 + 1) * 32, vb);
+                    rgb_group<F8>(va, rb4, wo4, al4, c32, o0, o1, o2);
+                    tmem_ld_wait();
+                    if (c32 + 2 < 4) tmem_ld32(t_row + (c32 + 2) * 32, va);
+                    rgb_group<F8>(vb, rb4, wo4, al4, c32 + 1, o0, o1, o2);
+                }
+                {
+                    // density head: accumulator column 128 of the last MMA
+                    uint32_t vs[32];
+                    tmem_ld32(t_row + 128, vs);
+                    tmem_ld_wait();
+                    sigma = __uint_as_float(vs[0]);
+                    if constexpr (F8) sigma *= p.alpha_sigma;
+                }
+                tc_fence_before();
+                if (valid) {
+                    float4 res;
+                    res.x = sigma + p.b_sigma;
+                    res.y = 1.0f / (1.0f + __expf(-(o0 + p.b_out0)));
+                    res.z = 1.0f / (1.0f + __expf(-(o1 + p.b_out1)));
+                    res.w = 1.0f / (1.0f + __expf(-(o2 + p.b_out2)));
+                    p.out[grow] = res;
+                }
+            }
+        }
+    }
+    if (!ok) record_abort(p);
+}
+
 template <bool F8, int EPIW, bool STAG>
 __global__ void __launch_bounds__(Variant<F8, EPIW, STAG>::kThreads, 1)
     k_mlp_tc(const __grid_constant__ Params p) {
@@ -310,278 +504,469 @@ __global__ void __launch_bounds__(Variant<F8, EPIW, STAG>::kThreads, 1)
         }
     } else if (warp == 1) {
         // ------------------------------------------------ MMA issuer
-        if (lane == 0) {
-            uint32_t g = 0;
-            uint32_t rdy_ph[2] = {0, 0};
-            bool ok = true;
-            const uint32_t id256 = F8 ? idesc_e4m3(128, 256) : idesc_bf16(128, 256);
-            const uint32_t id144 = F8 ? idesc_e4m3(128, 144) : idesc_bf16(128, 144);
-            int tl = 0;
-            // A operand (shared-memory address) of tile s, chunk c, K step kk
-            // of layer l; K steps are 32 bytes (16 BF16 or 32 E4M3 values)
-            auto a_operand = [&](int l, int s, int c, int kk) -> uint32_t {
-                if (l == 0) return s_gx + s * kGxBytes + (c * 2 + kk) * 32;
-                if (l == 5 && c >= Fm::kActChunks)
-                    return s_gx + s * kGxBytes + ((c - Fm::kActChunks) * 2 + kk) * 32;
-                const int ks = c * 2 + kk;
-                return s_act + s * kActBytes + (ks >> 2) * 16384 + (ks & 3) * 32;
-            };
-            auto issue = [&](int l, int s, int c, uint32_t st, uint32_t idesc) {
-#pragma unroll
-                for (int kk = 0; kk < 2; ++kk) {
-                    const uint64_t ad = smem_desc(a_operand(l, s, c, kk), 1024, kLayoutSw128);
-                    const uint64_t bd =
-                        smem_desc(s_ring + st * kStageBytes + kk * 32, 512, kLayoutSw64);
-                    if constexpr (F8)
-                        mma_f8(tmem + s * 256, ad, bd, idesc, (c | kk) ? 1u : 0u);
-                    else
-                        mma_bf16(tmem + s * 256, ad, bd, idesc, (c | kk) ? 1u : 0u);
-                }
-            };
-            for (long long pr = blockIdx.x; pr < n_pairs && ok; pr += gridDim.x) {
-                for (int l = 0; l < kLayers && ok; ++l, ++tl) {
-                    const int nch = c_chunks[F8 ? 1 : 0][l];
-                    const uint32_t idesc = (l == 8) ? id144 : id256;
-                    TC_TRACE(2, tl);
-                    if constexpr (STAG) {
-                        // Staggered tiles: all of layer l for tile 0, then all
-                        // of it for tile 1 from the same resident weight
-                        // blocks (a layer is at most 5 of the 8 stages), so
-                        // tile 0's epilogue runs under tile 1's MMAs and vice
-                        // versa.  A stage is released after tile 1's MMAs.
-                        for (int s = 0; s < 2 && ok; ++s) {
-                            if (!mbar_wait(smem_u32(&bars.a_ready[s]), rdy_ph[s], abort_flag)) {
-                                ok = false;
-                                break;
-                            }
-                            TC_TRACE(3 + s, tl);
-                            rdy_ph[s] ^= 1u;
+        // The whole warp walks the schedule; before each group of MMAs it
+        // meets the gate warp at named barrier 1 (which has waited for the
+        // group's weight block and activations); lane 0 issues.
+        uint32_t g = 0;
+        bool ok = true;
+        const uint32_t id256 = F8 ? idesc_e4m3(128, 256) : idesc_bf16(128, 256);
+        const uint32_t id144 = F8 ? idesc_e4m3(128, 144) : idesc_bf16(128, 144);
+        int tl = 0;
+        // Operand descriptors: the bases are built once; an operand at byte
+        // offset o from a base is base + o / 16 (the 14-bit start-address
+        // field does not overflow: all of shared memory is below 256 KB), so
+        // the issuing lane does one add per operand between MMAs.
+        const uint64_t d_act[2] = {smem_desc(s_act, 1024, kLayoutSw128),
+                                   smem_desc(s_act + kActBytes, 1024, kLayoutSw128)};
+        const uint64_t d_gx[2] = {smem_desc(s_gx, 1024, kLayoutSw128),
+                                  smem_desc(s_gx + kGxBytes, 1024, kLayoutSw128)};
+        const uint64_t d_ring = smem_desc(s_ring, 512, kLayoutSw64);
+        // A operand of tile s, chunk c (two 32-byte K steps) of layer l:
+        // gamma(x) for layer 1 and the skip layer's last chunks, else the
+        // activation tile (K-blocks of 128-byte rows, 16 KB apart)
+        auto a_desc = [&](int l, int s, int c) -> uint64_t {
+            if (l == 0) return d_gx[s] + (uint64_t)(c * 4);
+            if (l == 5 && c >= Fm::kActChunks) return d_gx[s] + (uint64_t)((c - Fm::kActChunks) * 4);
+            return d_act[s] + (uint64_t)((c >> 1) * 1024 + (c & 1) * 4);
+        };
+        auto issue = [&](int l, int s, int c, uint32_t st, uint32_t idesc) {
+            const uint64_t ad = a_desc(l, s, c);
+            const uint64_t bd = d_ring + (uint64_t)(st * (kStageBytes >> 4));
+            const uint32_t d = tmem + s * 256;
+            if constexpr (F8) {
+                mma_f8(d, ad, bd, idesc, c ? 1u : 0u);
+                mma_f8(d, ad + 2, bd + 2, idesc, 1u);
+            } else {
+                mma_bf16(d, ad, bd, idesc, c ? 1u : 0u);
+                mma_bf16(d, ad + 2, bd + 2, idesc, 1u);
+            }
+        };
+        auto gate = [&]() -> bool { return !named_bar_or(1, 64, false); };
+        for (long long pr = blockIdx.x; pr < n_pairs && ok; pr += gridDim.x) {
+            for (int l = 0; l < kLayers && ok; ++l, ++tl) {
+                const int nch = c_chunks[F8 ? 1 : 0][l];
+                const uint32_t idesc = (l == 8) ? id144 : id256;
+                if (lane == 0) TC_TRACE(2, tl);
+                if constexpr (STAG) {
+                    // Staggered tiles: all of layer l for tile 0, then all of
+                    // it for tile 1 from the same resident weight blocks (a
+                    // layer is at most 5 of the 8 stages), so tile 0's
+                    // epilogue runs under tile 1's MMAs and vice versa.  A
+                    // stage is released after tile 1's MMAs.
+                    for (int c = 0; c < nch; ++c) {
+                        if (!gate()) { ok = false; break; }
+                        if (lane == 0) {
                             tc_fence_after();
-                            for (int c = 0; c < nch; ++c) {
-                                const uint32_t gc = g + c;
-                                const uint32_t st = gc % kStages, ph = (gc / kStages) & 1u;
-                                if (s == 0) {
-                                    TC_TRACE(15, gc);
-                                    if (!mbar_wait(smem_u32(&bars.full[st]), ph, abort_flag)) {
-                                        ok = false;
-                                        break;
-                                    }
-                                    TC_TRACE(13, gc);
-                                }
-                                issue(l, s, c, st, idesc);
-                                if (s == 1) mma_commit(smem_u32(&bars.empty[st]));
-                            }
-                            if (!ok) break;
-                            mma_commit(smem_u32(&bars.acc_full[s]));
+                            issue(l, 0, c, (g + c) % kStages, idesc);
+                            if (c == nch - 1) mma_commit(smem_u32(&bars.acc_full[0]));
                         }
-                        g += nch;
-                    } else {
-                        // Lockstep tiles: each weight block serves both tiles
-                        // at once.
-                        for (int c = 0; c < nch && ok; ++c) {
-                            const uint32_t st = g % kStages, ph = (g / kStages) & 1u;
-                            TC_TRACE(15, g);
-                            if (!mbar_wait(smem_u32(&bars.full[st]), ph, abort_flag)) {
-                                ok = false;
-                                break;
-                            }
-                            TC_TRACE(13, g);
-                            for (int s = 0; s < 2; ++s) {
-                                if (c == 0) {
-                                    if (!mbar_wait(smem_u32(&bars.a_ready[s]), rdy_ph[s], abort_flag)) {
-                                        ok = false;
-                                        break;
-                                    }
-                                    TC_TRACE(3 + s, tl);
-                                    rdy_ph[s] ^= 1u;
-                                    tc_fence_after();
-                                }
-                                issue(l, s, c, st, idesc);
-                                if (c == nch - 1) mma_commit(smem_u32(&bars.acc_full[s]));
-                            }
-                            if (!ok) break;
+                        __syncwarp();
+                    }
+                    if (!ok) break;
+                    if (!gate()) { ok = false; break; }
+                    if (lane == 0) {
+                        tc_fence_after();
+                        for (int c = 0; c < nch; ++c) {
+                            const uint32_t st = (g + c) % kStages;
+                            issue(l, 1, c, st, idesc);
                             mma_commit(smem_u32(&bars.empty[st]));
-                            ++g;
+                        }
+                        mma_commit(smem_u32(&bars.acc_full[1]));
+                    }
+                    __syncwarp();
+                    g += nch;
+                } else {
+                    // Lockstep tiles: each weight block serves both tiles at
+                    // once; the first block of a layer waits for each tile's
+                    // activations separately.
+                    for (int c = 0; c < nch; ++c, ++g) {
+                        const uint32_t st = g % kStages;
+                        if (!gate()) { ok = false; break; }
+                        if (lane == 0) {
+                            tc_fence_after();
+                            issue(l, 0, c, st, idesc);
+                            if (c == nch - 1) mma_commit(smem_u32(&bars.acc_full[0]));
+                            if (c > 0) {
+                                issue(l, 1, c, st, idesc);
+                                if (c == nch - 1) mma_commit(smem_u32(&bars.acc_full[1]));
+                                mma_commit(smem_u32(&bars.empty[st]));
+                            }
+                        }
+                        __syncwarp();
+                        if (c == 0) {
+                            if (!gate()) { ok = false; break; }
+                            if (lane == 0) {
+                                tc_fence_after();
+                                issue(l, 1, 0, st, idesc);
+                                if (nch == 1) mma_commit(smem_u32(&bars.acc_full[1]));
+                                mma_commit(smem_u32(&bars.empty[st]));
+                            }
+                            __syncwarp();
                         }
                     }
-                    TC_TRACE(5, tl);
                 }
+                if (lane == 0) TC_TRACE(5, tl);
             }
+        }
+        if (lane == 0) {
             if (!ok) record_abort(p);
             // all issued MMAs complete before TMEM is released
             mma_commit(smem_u32(&bars.drain));
             mbar_wait(smem_u32(&bars.drain), 0, nullptr);
         }
-    } else {
-        // ------------------------------------------------ prologue / epilogues
-        // kEpiWarps warps per tile: warp w covers TMEM lane quadrant (w % 4),
-        // i.e. rows 32 (w % 4) .. +31; with 8 warps the first four take
-        // accumulator columns 0..127 and the other four 128..255 (column
-        // halves h0 .. h1 - 1 of 128); one thread owns one row.
-        constexpr int kH = Vt::kHalves;
-        const int slot = (warp - 2) / Vt::kEpiWarps;
-        const int h0 = kH == 2 ? (((warp - 2) >> 2) & 1) : 0;
-        const int h1 = h0 + 3 - kH;                       // one half, or both
-        const int quad = warp & 3;
-        const uint32_t r = quad * 32 + lane;              // row within the tile
-        const uint32_t t_row = tmem + ((uint32_t)(quad * 32) << 16) + slot * 256;
-        const uint32_t a_base = s_act + slot * kActBytes;
-        const uint32_t g_base = s_gx + slot * kGxBytes;
-        const uint32_t bar_ready = smem_u32(&bars.a_ready[slot]);
-        const uint32_t bar_acc = smem_u32(&bars.acc_full[slot]);
-        uint32_t acc_ph = 0;
+        __syncwarp();
+    } else if (warp == 2) {
+        // ------------------------------------------------ gate
+        // Waits (all lanes) for what each MMA group of the schedule needs,
+        // then releases the MMA warp at named barrier 1, or stops it.
+        uint32_t g = 0;
+        uint32_t rdy_ph[2] = {0, 0};
         bool ok = true;
-        const bool tracer = (r == 0 && h0 == 0);
         int tl = 0;
+        auto wait_ready = [&](int s) -> bool {
+            const bool r = mbar_wait(smem_u32(&bars.a_ready[s]), rdy_ph[s], abort_flag);
+            rdy_ph[s] ^= 1u;
+            if (lane == 0) TC_TRACE(3 + s, tl);
+            return r;
+        };
+        auto wait_block = [&](uint32_t gi) -> bool {
+            if (lane == 0) TC_TRACE(15, gi);
+            const bool r = mbar_wait(smem_u32(&bars.full[gi % kStages]), (gi / kStages) & 1u, abort_flag);
+            if (lane == 0) TC_TRACE(13, gi);
+            return r;
+        };
+        auto release = [&](bool good) -> bool {
+            __syncwarp();
+            return !named_bar_or(1, 64, !good);
+        };
         for (long long pr = blockIdx.x; pr < n_pairs && ok; pr += gridDim.x) {
-            const long long grow = pr * 256 + slot * 128 + r;
-            const bool valid = grow < M;
-            const long long ray = valid ? grow / p.S : 0;
-            // ---- prologue: this thread's halves of gamma(x) into the tile's
-            //      gamma(x) buffer
-            {
-                float x[3] = {0.f, 0.f, 0.f};
-                if (valid) {
-                    const Ray R = p.rays[ray];
-                    const float zz = p.z[grow];
-                    x[0] = fmaf(zz, R.dx, R.ox);
-                    x[1] = fmaf(zz, R.dy, R.oy);
-                    x[2] = fmaf(zz, R.dz, R.oz);
-                }
-                for (int half = h0; half < h1; ++half) {
-                    float v[32];
-                    if (valid) {
-                        if (half == 0) pe_half<0>(x, v);
-                        else pe_half<1>(x, v);
-                    } else {
-#pragma unroll
-                        for (int i = 0; i < 32; ++i) v[i] = 0.0f;
-                    }
-                    if constexpr (F8) {
-                        const float sg = p.s_gx;
-#pragma unroll
-                        for (int j = 0; j < 2; ++j) {
-                            uint32_t w[4];
-#pragma unroll
-                            for (int e = 0; e < 4; ++e) {
-                                const int i = 16 * j + 4 * e;
-                                w[e] = pack_e4m3x4(v[i] * sg, v[i + 1] * sg, v[i + 2] * sg,
-                                                   v[i + 3] * sg);
-                            }
-                            st_shared_v4(g_base + sw128_offset(r, 2 * half + j), w[0], w[1], w[2], w[3]);
-                        }
-                    } else {
-#pragma unroll
-                        for (int j = 0; j < 4; ++j)
-                            st_shared_v4(g_base + sw128_offset(r, 4 * half + j),
-                                         pack_bf16x2(v[8 * j], v[8 * j + 1]),
-                                         pack_bf16x2(v[8 * j + 2], v[8 * j + 3]),
-                                         pack_bf16x2(v[8 * j + 4], v[8 * j + 5]),
-                                         pack_bf16x2(v[8 * j + 6], v[8 * j + 7]));
-                    }
-                }
-                fence_proxy_async_smem();
-                tc_fence_before();
-                mbar_arrive(bar_ready);
-            }
-            float sigma = 0.0f;
             for (int l = 0; l < kLayers && ok; ++l, ++tl) {
-                if (!mbar_wait_sleep(bar_acc, acc_ph, abort_flag)) {
-                    ok = false;
-                    break;
-                }
-                if (tracer) TC_TRACE(6 + 2 * slot, tl);
-                acc_ph ^= 1u;
-                tc_fence_after();
-                if (l < 8) {
-                    // this thread's columns, 32 at a time, the next TMEM load
-                    // in flight while the current group is stored
-                    for (int half = h0; half < h1; ++half) {
-                        const uint32_t t_acc = t_row + half * 128;
-                        uint32_t va[32], vb[32];
-                        tmem_ld32(t_acc, va);
-                        if constexpr (F8) {
-                            // h = relu(acc alpha + beta) in FP32, stored as E4M3:
-                            // columns 128 half .. +127 are K-block `half`, chunks 0..7
-                            const float alpha = p.alpha[l];
-                            const float4* b4 =
-                                reinterpret_cast<const float4*>(p.beta + l * 256 + half * 128);
-                            const uint32_t blk = a_base + half * 16384;
-#pragma unroll 1
-                            for (int c32 = 0; c32 < 4; c32 += 2) {
-                                tmem_ld_wait();
-                                tmem_ld32(t_acc + (c32 + 1) * 32, vb);
-                                epi_chunk_store_f8(va, alpha, b4 + c32 * 8, blk, r, c32 * 2);
-                                tmem_ld_wait();
-                                if (c32 + 2 < 4) tmem_ld32(t_acc + (c32 + 2) * 32, va);
-                                epi_chunk_store_f8(vb, alpha, b4 + (c32 + 1) * 8, blk, r,
-                                                   (c32 + 1) * 2);
-                            }
-                        } else {
-                            // h = relu(acc + b): accumulators rounded to BF16 pairs,
-                            // bias added and ReLU applied in packed BF16 arithmetic;
-                            // columns 128 half .. +127 are K-blocks 2 half, 2 half + 1
-                            const uint4* b4 =
-                                reinterpret_cast<const uint4*>(p.bias2 + l * 128 + half * 64);
-#pragma unroll 1
-                            for (int c32 = 0; c32 < 4; c32 += 2) {
-                                tmem_ld_wait();
-                                tmem_ld32(t_acc + (c32 + 1) * 32, vb);
-                                const uint32_t blk = a_base + (2 * half + (c32 >> 1)) * 16384;
-                                epi_chunk_store(va, b4 + c32 * 4, blk, r, 0);
-                                tmem_ld_wait();
-                                if (c32 + 2 < 4) tmem_ld32(t_acc + (c32 + 2) * 32, va);
-                                epi_chunk_store(vb, b4 + (c32 + 1) * 4, blk, r, 4);
-                            }
-                        }
+                const int nch = c_chunks[F8 ? 1 : 0][l];
+                if constexpr (STAG) {
+                    for (int c = 0; c < nch; ++c) {
+                        bool good = true;
+                        if (c == 0) good = wait_ready(0);
+                        good = good && wait_block(g + c);
+                        if (!release(good)) { ok = false; break; }
                     }
-                    fence_proxy_async_smem();
-                    tc_fence_before();
-                    if (tracer) TC_TRACE(7 + 2 * slot, tl);
-                    mbar_arrive(bar_ready);
-                } else if (h0 == 0) {
-                    const float4* rb4 = reinterpret_cast<const float4*>(p.ray_bias + ray * 128);
-                    const float4* wo4 = reinterpret_cast<const float4*>(p.w_out);
-                    const float4* al4 = reinterpret_cast<const float4*>(p.alpha_last);
-                    float o0 = 0.f, o1 = 0.f, o2 = 0.f;
-                    uint32_t va[32], vb[32];
-                    tmem_ld32(t_row, va);
-#pragma unroll 1
-                    for (int c32 = 0; c32 < 4; c32 += 2) {
-                        tmem_ld_wait();
-                        tmem_ld32(t_row + (c32 + 1) * 32, vb);
-                        rgb_group<F8>(va, rb4, wo4, al4, c32, o0, o1, o2);
-                        tmem_ld_wait();
-                        if (c32 + 2 < 4) tmem_ld32(t_row + (c32 + 2) * 32, va);
-                        rgb_group<F8>(vb, rb4, wo4, al4, c32 + 1, o0, o1, o2);
-                    }
-                    {
-                        // density head: accumulator column 128 of the last MMA
-                        uint32_t vs[32];
-                        tmem_ld32(t_row + 128, vs);
-                        tmem_ld_wait();
-                        sigma = __uint_as_float(vs[0]);
-                        if constexpr (F8) sigma *= p.alpha_sigma;
-                    }
-                    tc_fence_before();
-                    if (valid) {
-                        float4 res;
-                        res.x = sigma + p.b_sigma;
-                        res.y = 1.0f / (1.0f + __expf(-(o0 + p.b_out0)));
-                        res.z = 1.0f / (1.0f + __expf(-(o1 + p.b_out1)));
-                        res.w = 1.0f / (1.0f + __expf(-(o2 + p.b_out2)));
-                        p.out[grow] = res;
+                    if (!ok) break;
+                    if (!release(wait_ready(1))) { ok = false; break; }
+                    g += nch;
+                } else {
+                    for (int c = 0; c < nch; ++c, ++g) {
+                        bool good = wait_block(g);
+                        if (c == 0) good = good && wait_ready(0);
+                        if (!release(good)) { ok = false; break; }
+                        if (c == 0 && !release(wait_ready(1))) { ok = false; break; }
                     }
                 }
             }
         }
-        if (!ok) record_abort(p);
+        if (!ok && lane == 0) record_abort(p);
+    } else {
+        epilogue_warps<F8, EPIW, false>(p, warp, 3, lane, tmem, s_act, s_gx,
+                                        smem_u32(&bars.a_ready[0]), smem_u32(&bars.a_ready[1]),
+                                        smem_u32(&bars.acc_full[0]), smem_u32(&bars.acc_full[1]),
+                                        M, blockIdx.x, gridDim.x, n_pairs, 256, 0);
     }
     tc_fence_before();
     __syncthreads();
     if (warp == 1) {
         tc_fence_after();
         tmem_dealloc(tmem, 512);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// CTA-pair form (cluster of 2 CTAs on the two SMs of a TPC, tcgen05
+// cta_group::2).  Work unit: 512 rows; CTA rank r holds rows 256 r .. +255 as
+// its two 128-row tiles, exactly as the single-CTA kernel holds a tile pair.
+// Each MMA is M = 256 (tile s of both CTAs), N = 256 (144 for the last
+// layer), so each CTA stores and streams only its half of every weight block
+// (output rows N/2 r .. +N/2 - 1: 8 KB, or 4,608 bytes of the last layer's
+// 144 rows): twice the ring depth in blocks, half the weight bytes per SM.
+// The even CTA's warp 1 issues all MMAs once its own copy of a block has
+// landed (full[]) and the odd CTA's warp 1 has relayed that the odd CTA's
+// copy has (the even CTA's pfull[]); the epilogue warps of both CTAs signal
+// the even CTA's a_ready[] barriers; the MMA commits arrive on the barriers
+// of both CTAs (multicast).  Same arithmetic per row as the single-CTA
+// kernel.
+template <bool F8>
+struct PairForm {
+    static constexpr int kStages = 2 * Form<F8>::kStages;     // half-blocks
+    static constexpr uint32_t kHalf = kStageBytes / 2;       // 128 rows x 64 bytes
+    static constexpr uint32_t kHalfLast = 72 * 64;           // 144 / 2 rows
+    static constexpr uint32_t kSmemBytes = 1024 + 2 * Form<F8>::kActBytes + 2 * kGxBytes + kStages * kHalf;
+};
+static_assert(PairForm<false>::kSmemBytes <= 232448 && PairForm<true>::kSmemBytes <= 232448, "smem");
+constexpr int kPairMaxStages = 16;
+constexpr int kPairThreads = 96 + 2 * 128;
+
+struct __align__(8) PairBars {
+    uint64_t full[kPairMaxStages];
+    uint64_t pfull[kPairMaxStages];   // even CTA: the odd CTA's copy has landed
+    uint64_t empty[kPairMaxStages];
+    uint64_t acc_full[2];
+    uint64_t a_ready[2];
+    uint64_t drain;
+    uint32_t tmem_base;
+};
+
+template <bool F8, bool STAG>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kPairThreads, 1)
+    k_mlp_tc2(const __grid_constant__ Params p) {
+    static_assert(!STAG || F8, "a BF16 layer does not fit in the weight ring");
+    using Fm = Form<F8>;
+    using Pf = PairForm<F8>;
+    constexpr int kStages = Pf::kStages;
+    constexpr uint32_t kActBytes = Fm::kActBytes;
+    constexpr int kLastBlock0 = F8 ? 30 : 60;                 // first block of layer 9
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ PairBars bars;
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const uint32_t s_act = smem_u32(smem);
+    const uint32_t s_gx = s_act + 2 * kActBytes;
+    const uint32_t s_ring = s_gx + 2 * kGxBytes;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t rank = cluster_ctarank();
+    volatile int* abort_flag = p.abort_flag;
+    const long long M = p.M_dev ? min(p.M, (long long)*p.M_dev) : p.M;
+    const long long n_units = (M + 511) / 512;
+    const long long u0 = blockIdx.x >> 1, du = gridDim.x >> 1;
+
+    if (tid == 0) {
+        for (int i = 0; i < kStages; ++i) {
+            mbar_init(smem_u32(&bars.full[i]), 1);
+            mbar_init(smem_u32(&bars.pfull[i]), 1);
+            mbar_init(smem_u32(&bars.empty[i]), 1);
+        }
+        for (int s = 0; s < 2; ++s) {
+            mbar_init(smem_u32(&bars.acc_full[s]), 1);
+            mbar_init(smem_u32(&bars.a_ready[s]), 8);   // 4 epilogue warps x 2 CTAs
+        }
+        mbar_init(smem_u32(&bars.drain), 1);
+        fence_mbar_init();
+    }
+    if (warp == 1) {
+        tmem_alloc2(smem_u32(&bars.tmem_base), 512);
+        tmem_relinquish2();
+    }
+    tc_fence_before();
+    cluster_sync_all();
+    tc_fence_after();
+    const uint32_t tmem = bars.tmem_base;
+
+    if (warp == 0) {
+        // ------------------------------------------------ weight stream (both CTAs)
+        if (lane == 0) {
+            uint32_t g = 0;
+            bool ok = true;
+            for (long long u = u0; u < n_units && ok; u += du) {
+                for (int b = 0; b < Fm::kBlocks; ++b, ++g) {
+                    const uint32_t st = g % kStages, ph = (g / kStages) & 1u;
+                    TC_TRACE(0, g);
+                    if (!mbar_wait_cluster<false>(smem_u32(&bars.empty[st]), ph ^ 1u, abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    TC_TRACE(1, g);
+                    TC_TRACE_CTA(1, 11, g);
+                    const uint32_t bytes = b >= kLastBlock0 ? Pf::kHalfLast : Pf::kHalf;
+                    mbar_arrive_expect_tx(smem_u32(&bars.full[st]), bytes);
+                    bulk_load(s_ring + st * Pf::kHalf, p.wblocks + (size_t)b * kStageBytes + rank * bytes,
+                              bytes, smem_u32(&bars.full[st]));
+                }
+            }
+            if (!ok) record_abort(p);
+            // every issued copy lands before the CTA may exit: the last copy
+            // of each stage (earlier ones were consumed before it was issued)
+            for (uint32_t k = 0; k < (uint32_t)kStages && k < g; ++k) {
+                const uint32_t gl = g - 1 - k;
+                mbar_wait(smem_u32(&bars.full[gl % kStages]), (gl / kStages) & 1u, nullptr);
+            }
+        }
+    } else if (warp == 1 && rank == 1) {
+        // ------------------------------------------------ relay (odd CTA)
+        if (lane == 0) {
+            uint32_t g = 0;
+            bool ok = true;
+            for (long long u = u0; u < n_units && ok; u += du)
+                for (int b = 0; b < Fm::kBlocks; ++b, ++g) {
+                    const uint32_t st = g % kStages, ph = (g / kStages) & 1u;
+                    if (!mbar_wait(smem_u32(&bars.full[st]), ph, abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    TC_TRACE_CTA(1, 10, g);
+                    mbar_arrive_cluster(mapa_shared(smem_u32(&bars.pfull[st]), 0));
+                }
+            if (!ok) record_abort(p);
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------ MMA issuer (even CTA)
+        // As in the single-CTA kernel: the whole warp walks the schedule and
+        // meets the gate warp at named barrier 1 before each group; lane 0
+        // issues the pair's MMAs and commits to the barriers of both CTAs.
+        uint32_t g = 0;
+        bool ok = true;
+        const uint32_t id256 = F8 ? idesc_e4m3(256, 256) : idesc_bf16(256, 256);
+        const uint32_t id144 = F8 ? idesc_e4m3(256, 144) : idesc_bf16(256, 144);
+        constexpr uint16_t kBoth = 3;
+        int tl = 0;
+        const uint64_t d_act[2] = {smem_desc(s_act, 1024, kLayoutSw128),
+                                   smem_desc(s_act + kActBytes, 1024, kLayoutSw128)};
+        const uint64_t d_gx[2] = {smem_desc(s_gx, 1024, kLayoutSw128),
+                                  smem_desc(s_gx + kGxBytes, 1024, kLayoutSw128)};
+        const uint64_t d_ring = smem_desc(s_ring, 512, kLayoutSw64);
+        auto a_desc = [&](int l, int s, int c) -> uint64_t {
+            if (l == 0) return d_gx[s] + (uint64_t)(c * 4);
+            if (l == 5 && c >= Fm::kActChunks) return d_gx[s] + (uint64_t)((c - Fm::kActChunks) * 4);
+            return d_act[s] + (uint64_t)((c >> 1) * 1024 + (c & 1) * 4);
+        };
+        auto issue = [&](int l, int s, int c, uint32_t st, uint32_t idesc) {
+            const uint64_t ad = a_desc(l, s, c);
+            const uint64_t bd = d_ring + (uint64_t)(st * (Pf::kHalf >> 4));
+            const uint32_t d = tmem + s * 256;
+            if constexpr (F8) {
+                mma2_f8(d, ad, bd, idesc, c ? 1u : 0u);
+                mma2_f8(d, ad + 2, bd + 2, idesc, 1u);
+            } else {
+                mma2_bf16(d, ad, bd, idesc, c ? 1u : 0u);
+                mma2_bf16(d, ad + 2, bd + 2, idesc, 1u);
+            }
+        };
+        auto gate = [&]() -> bool { return !named_bar_or(1, 64, false); };
+        for (long long u = u0; u < n_units && ok; u += du) {
+            for (int l = 0; l < kLayers && ok; ++l, ++tl) {
+                const int nch = c_chunks[F8 ? 1 : 0][l];
+                const uint32_t idesc = (l == 8) ? id144 : id256;
+                if (lane == 0) TC_TRACE(2, tl);
+                if constexpr (STAG) {
+                    for (int c = 0; c < nch; ++c) {
+                        if (!gate()) { ok = false; break; }
+                        if (lane == 0) {
+                            tc_fence_after();
+                            issue(l, 0, c, (g + c) % kStages, idesc);
+                            if (c == nch - 1) mma_commit2_mc(smem_u32(&bars.acc_full[0]), kBoth);
+                        }
+                        __syncwarp();
+                    }
+                    if (!ok) break;
+                    if (!gate()) { ok = false; break; }
+                    if (lane == 0) {
+                        tc_fence_after();
+                        for (int c = 0; c < nch; ++c) {
+                            const uint32_t st = (g + c) % kStages;
+                            issue(l, 1, c, st, idesc);
+                            mma_commit2_mc(smem_u32(&bars.empty[st]), kBoth);
+                        }
+                        mma_commit2_mc(smem_u32(&bars.acc_full[1]), kBoth);
+                    }
+                    __syncwarp();
+                    g += nch;
+                } else {
+                    for (int c = 0; c < nch; ++c, ++g) {
+                        const uint32_t st = g % kStages;
+                        if (!gate()) { ok = false; break; }
+                        if (lane == 0) {
+                            tc_fence_after();
+                            issue(l, 0, c, st, idesc);
+                            if (c == nch - 1) mma_commit2_mc(smem_u32(&bars.acc_full[0]), kBoth);
+                            if (c > 0) {
+                                issue(l, 1, c, st, idesc);
+                                if (c == nch - 1) mma_commit2_mc(smem_u32(&bars.acc_full[1]), kBoth);
+                                mma_commit2_mc(smem_u32(&bars.empty[st]), kBoth);
+                            }
+                        }
+                        __syncwarp();
+                        if (c == 0) {
+                            if (!gate()) { ok = false; break; }
+                            if (lane == 0) {
+                                tc_fence_after();
+                                issue(l, 1, 0, st, idesc);
+                                if (nch == 1) mma_commit2_mc(smem_u32(&bars.acc_full[1]), kBoth);
+                                mma_commit2_mc(smem_u32(&bars.empty[st]), kBoth);
+                            }
+                            __syncwarp();
+                        }
+                    }
+                }
+                if (lane == 0) TC_TRACE(5, tl);
+            }
+        }
+        if (lane == 0) {
+            if (!ok) record_abort(p);
+            // all issued MMAs (they write both CTAs' TMEM and read both CTAs'
+            // shared memory) complete before either CTA releases TMEM or exits
+            mma_commit2_mc(smem_u32(&bars.drain), 1);
+            mbar_wait(smem_u32(&bars.drain), 0, nullptr);
+        }
+        __syncwarp();
+    } else if (warp == 2) {
+        // ------------------------------------------------ gate (even CTA)
+        if (rank == 0) {
+            uint32_t g = 0;
+            uint32_t rdy_ph[2] = {0, 0};
+            bool ok = true;
+            int tl = 0;
+            auto wait_ready = [&](int s) -> bool {
+                const bool r = mbar_wait_cluster<false>(smem_u32(&bars.a_ready[s]), rdy_ph[s], abort_flag);
+                rdy_ph[s] ^= 1u;
+                if (lane == 0) TC_TRACE(3 + s, tl);
+                return r;
+            };
+            // block gi present in both CTAs
+            auto wait_block = [&](uint32_t gi) -> bool {
+                const uint32_t st = gi % kStages, ph = (gi / kStages) & 1u;
+                if (lane == 0) TC_TRACE(15, gi);
+                const bool r = mbar_wait(smem_u32(&bars.full[st]), ph, abort_flag);
+                if (lane == 0) TC_TRACE(12, gi);
+                const bool r2 = r && mbar_wait_cluster<false>(smem_u32(&bars.pfull[st]), ph, abort_flag);
+                if (lane == 0) TC_TRACE(13, gi);
+                return r2;
+            };
+            auto release = [&](bool good) -> bool {
+                __syncwarp();
+                return !named_bar_or(1, 64, !good);
+            };
+            for (long long u = u0; u < n_units && ok; u += du) {
+                for (int l = 0; l < kLayers && ok; ++l, ++tl) {
+                    const int nch = c_chunks[F8 ? 1 : 0][l];
+                    if constexpr (STAG) {
+                        for (int c = 0; c < nch; ++c) {
+                            bool good = true;
+                            if (c == 0) good = wait_ready(0);
+                            good = good && wait_block(g + c);
+                            if (!release(good)) { ok = false; break; }
+                        }
+                        if (!ok) break;
+                        if (!release(wait_ready(1))) { ok = false; break; }
+                        g += nch;
+                    } else {
+                        for (int c = 0; c < nch; ++c, ++g) {
+                            bool good = wait_block(g);
+                            if (c == 0) good = good && wait_ready(0);
+                            if (!release(good)) { ok = false; break; }
+                            if (c == 0 && !release(wait_ready(1))) { ok = false; break; }
+                        }
+                    }
+                }
+            }
+            if (!ok && lane == 0) record_abort(p);
+        }
+    } else {
+        const uint32_t rdy0 = mapa_shared(smem_u32(&bars.a_ready[0]), 0);
+        const uint32_t rdy1 = mapa_shared(smem_u32(&bars.a_ready[1]), 0);
+        epilogue_warps<F8, 4, true>(p, warp, 3, lane, tmem, s_act, s_gx, rdy0, rdy1,
+                                    smem_u32(&bars.acc_full[0]), smem_u32(&bars.acc_full[1]), M, u0, du,
+                                    n_units, 512, (long long)rank * 256);
+    }
+    __syncwarp();
+    tc_fence_before();
+    cluster_sync_all();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc2(tmem, 512);
     }
 }
 
@@ -1104,20 +1489,29 @@ struct TcVariant {
     void (*fn)(Params);
     int threads;
     uint32_t smem;
+    int cluster;                // 1, or 2: CTA pairs over 512-row units
 };
 template <bool F8, int W, bool S>
 constexpr TcVariant make_variant() {
     return TcVariant{F8 ? MCL_PREC_FP8 : MCL_PREC_BF16, W, S, &k_mlp_tc<F8, W, S>,
-                     Variant<F8, W, S>::kThreads, Form<F8>::kSmemBytes};
+                     Variant<F8, W, S>::kThreads, Form<F8>::kSmemBytes, 1};
+}
+template <bool F8, bool S>
+constexpr TcVariant make_pair_variant() {
+    return TcVariant{F8 ? MCL_PREC_FP8 : MCL_PREC_BF16, 4, S, &k_mlp_tc2<F8, S>, kPairThreads,
+                     PairForm<F8>::kSmemBytes, 2};
 }
 const TcVariant kVariants[] = {
     make_variant<false, 4, false>(), make_variant<false, 8, false>(),
     make_variant<true, 4, false>(),  make_variant<true, 8, false>(),
     make_variant<true, 4, true>(),   make_variant<true, 8, true>(),
-    TcVariant{MCL_PREC_BF16, 4, true, &k_mlp_tc_split, kSplitThreads, kSplitSmem},
-    TcVariant{MCL_PREC_BF16, 4, false, &k_mlp_tc_pipe, kPipeThreads, kPipeSmem},
+    TcVariant{MCL_PREC_BF16, 4, true, &k_mlp_tc_split, kSplitThreads, kSplitSmem, 1},
+    TcVariant{MCL_PREC_BF16, 4, false, &k_mlp_tc_pipe, kPipeThreads, kPipeSmem, 1},
+    make_pair_variant<false, false>(), make_pair_variant<true, false>(),
+    make_pair_variant<true, true>(),
 };
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
+static_assert(kNumVariants == MCL_MLP_VARIANTS, "variant table");
 // untuned choice per precision (fastest measured at all sizes on GB300):
 // BF16 4 warps lockstep, FP8 4 warps staggered
 constexpr int kDefaultVariant[3] = {-1, 0, 4};
@@ -1142,6 +1536,7 @@ struct TcState {
     float b_sigma = 0.f, b_out[3] = {0.f, 0.f, 0.f};
     float alpha_sigma = 1.f, s_gx = 1.f;
     int n_sm = 0;
+    int max_pairs = 0;         // co-resident CTA pairs of the pair kernels
     int variant[3] = {-1, kDefaultVariant[1], kDefaultVariant[2]};   // by precision
     float tuned_ms[kNumVariants] = {};                                // last autotune
     bool tuned[3] = {false, false, false};
@@ -1412,6 +1807,18 @@ int mlp_tc_prepare(mcl_map* m, const float* blob) {
                                                   (int)v.smem),
                              "smem attribute")))
             return rc;
+    {
+        // persistent grid of the pair kernels: every pair resident at once
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)(st->n_sm & ~1));
+        cfg.blockDim = dim3(kPairThreads);
+        cfg.dynamicSmemBytes = PairForm<false>::kSmemBytes;
+        if ((rc = cuda_check(cudaOccupancyMaxActiveClusters(&st->max_pairs, &k_mlp_tc2<false, false>, &cfg),
+                             "pair occupancy")))
+            return rc;
+        st->max_pairs = std::min(st->max_pairs, st->n_sm / 2);
+        if (st->max_pairs < 1) return fail(MCL_ERR_UNSUPPORTED, "no CTA pair fits on an SM pair");
+    }
     st->bf16.ready = st->fp8.ready = st->bf16_split.ready = true;
     return MCL_OK;
 }
@@ -1491,10 +1898,16 @@ static cudaError_t mlp_tc_variant(mcl_map* m, int precision, int variant, const 
     cudaError_t e = cudaMemsetAsync(st->abort_flag, 0, sizeof(int), s);
     if (e) return e;
     // persistent grid: one CTA per SM at most, one per work unit (a pair of
-    // tiles, or a single tile for the pipelined kernel)
-    const long long units = kVariants[vi].fn == &k_mlp_tc_pipe ? (p.M + 127) / 128 : p.n_pairs;
-    const long long grid = units < st->n_sm ? units : st->n_sm;
+    // tiles, a single tile for the pipelined kernel, 512 rows for a CTA pair)
     const TcVariant& v = kVariants[vi];
+    long long grid;
+    if (v.cluster == 2) {
+        const long long units = (p.M + 511) / 512;
+        grid = 2 * (units < st->max_pairs ? units : st->max_pairs);
+    } else {
+        const long long units = v.fn == &k_mlp_tc_pipe ? (p.M + 127) / 128 : p.n_pairs;
+        grid = units < st->n_sm ? units : st->n_sm;
+    }
     note_launch();
     v.fn<<<(unsigned)grid, v.threads, v.smem, s>>>(p);
     return cudaGetLastError();
