@@ -17,9 +17,12 @@
 // Warp roles: warp 0 streams weight blocks (256 rows x 64 bytes, stored in
 // global memory already in the 64-byte-swizzled shared-memory layout) with
 // contiguous bulk copies through a ring; warp 1 allocates TMEM and issues
-// the MMAs (M = 128, N = 256, 32 bytes of K per instruction); the other warps
-// run prologue and epilogues, 4 (BF16) or 8 (FP8) per tile, one warp per TMEM
-// lane quadrant and column half, one thread per row.  BF16 runs the two
+// the MMAs (M = 128, N = 256, 32 bytes of K per instruction); warp 2 (the
+// gate) waits on the ring and activation barriers and releases warp 1
+// through a named barrier, so that the issuing thread makes no shared-memory
+// access between MMAs; the other warps run prologue and epilogues, 4 or 8
+// per tile, one warp per TMEM lane quadrant and column half, one thread per
+// row.  BF16 runs the two
 // tiles in lockstep, each weight block serving both at once; FP8 staggers
 // them (tile 1 runs a layer on the resident blocks after tile 0), so each
 // tile's epilogue overlaps the other's MMAs.  Every wait is bounded (see
@@ -685,9 +688,10 @@ __global__ void __launch_bounds__(Variant<F8, EPIW, STAG>::kThreads, 1)
 // layer), so each CTA stores and streams only its half of every weight block
 // (output rows N/2 r .. +N/2 - 1: 8 KB, or 4,608 bytes of the last layer's
 // 144 rows): twice the ring depth in blocks, half the weight bytes per SM.
-// The even CTA's warp 1 issues all MMAs once its own copy of a block has
-// landed (full[]) and the odd CTA's warp 1 has relayed that the odd CTA's
-// copy has (the even CTA's pfull[]); the epilogue warps of both CTAs signal
+// The even CTA's warp 1 issues all MMAs, released by its gate warp once its
+// own copy of a block has landed (full[]) and the odd CTA's warp 1 has
+// relayed that the odd CTA's copy has (the even CTA's pfull[]); the
+// epilogue warps (3 .. 10) of both CTAs signal
 // the even CTA's a_ready[] barriers; the MMA commits arrive on the barriers
 // of both CTAs (multicast).  Same arithmetic per row as the single-CTA
 // kernel.
