@@ -49,3 +49,34 @@ def test_last_error_without_gpu(built_lib):
     lib = ctypes.CDLL(built_lib)
     lib.mcl_last_error.restype = ctypes.c_char_p
     assert lib.mcl_last_error() == b""
+
+
+def header_defines():
+    vals = {}
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        for m in re.finditer(r"^#define\s+(MCL_[A-Z0-9_]+)\s+\(?(-?\d+)\)?", src, flags=re.M):
+            vals[m.group(1)] = int(m.group(2))
+        for m in re.finditer(r"\b(MCL_PREC_[A-Z0-9]+)\s*=\s*(\d+)", src):
+            vals[m.group(1)] = int(m.group(2))
+    return vals
+
+
+def test_binding_constants_match_header():
+    """The binding's copies of the header's constants (error codes, sizes,
+    the number of MLP kernel variants, the profiled phases) are the
+    header's values."""
+    import paper_2406_12202_gb300 as M
+    d = header_defines()
+    for name in ("MCL_OK", "MCL_ERR_ARG", "MCL_ERR_CUDA", "MCL_ERR_NONFINITE", "MCL_ERR_TIMEOUT",
+                 "MCL_ERR_UNSUPPORTED", "MCL_ERR_DEGENERATE"):
+        assert getattr(M, name) == d[name], name
+    assert M.MAX_STAGES == d["MCL_MAX_STAGES"]
+    assert M.RESAMPLE_NOALLOC_MAX_IN == d["MCL_RESAMPLE_NOALLOC_MAX_IN"]
+    assert M.PROPOSAL_N_WEIGHTS == d["MCL_PROPOSAL_N_WEIGHTS"]
+    assert M.N_PHASES == d["MCL_N_PHASES"]
+    assert M.MLP_VARIANTS == d["MCL_MLP_VARIANTS"]
+    assert sorted(M.MLP_VARIANT_TABLE) == list(range(d["MCL_MLP_VARIANTS"]))
+    assert {v[0] for v in M.MLP_VARIANT_TABLE.values()} == {"bf16", "fp8"}
+    for prec, code in (("FP32", M.PREC_FP32), ("BF16", M.PREC_BF16), ("FP8", M.PREC_FP8)):
+        assert d["MCL_PREC_" + prec] == code
