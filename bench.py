@@ -439,6 +439,21 @@ def run_batched(M, seed, W, H, focal, use_proposal_blob=None):
 
 
 # --------------------------------------------------------------- GPU arm
+def job_rate(dist, seconds, units, device="cpu"):
+    """Whole-job throughput over the ranks of a run: the units every rank
+    processed, summed, over the slowest rank's time.  Returns (slowest
+    seconds, total units, units per second); dist is torch.distributed with
+    an initialised process group, or None for a single process."""
+    if dist is None:
+        return float(seconds), float(units), float(units) / float(seconds)
+    import torch
+    t = torch.tensor([float(seconds)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item()), float(u.item()) / float(t.item())
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -536,16 +551,7 @@ def run_ours(args):
     clk = clocks.stop() if clocks else None
     total_s = sum(ms) / 1e3
     units = N * Bpx * ns * args.steps
-    tmax = total_s
-    units_all = units
-    if dist is not None:
-        t = torch.tensor([total_s], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tmax = float(t.item())
-        u = torch.tensor([float(units)], dtype=torch.float64, device=dev)
-        dist.all_reduce(u, op=dist.ReduceOp.SUM)
-        units_all = float(u.item())
-    value = units_all / tmax
+    _, _, value = job_rate(dist, total_s, units, dev)
 
     # plain FP32 GPU form on the same box (comparison the metric names)
     fp32 = None
@@ -587,12 +593,7 @@ def run_ours(args):
         torch.cuda.synchronize()
         if k >= args.warmup:
             e2e_ms.append(a.elapsed_time(b))
-    e2e_t = sum(e2e_ms) / 1e3
-    if dist is not None:
-        t = torch.tensor([e2e_t], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_t = float(t.item())
-    e2e_value = units_all / e2e_t
+    e2e_t, _, e2e_value = job_rate(dist, sum(e2e_ms) / 1e3, units, dev)
 
     if rank != 0:
         if dist is not None:
