@@ -438,6 +438,66 @@ def run_batched(M, seed, W, H, focal, use_proposal_blob=None):
             "final_yaw_error_deg_median": float(np.median([e[1] for e in errs]))}
 
 
+def run_sweeps(M, prec, Q=4, iters=60):
+    """Fig. 6 / Fig. 7 analogue (Sec. IV-D): the ray-uncertainty floor tau of
+    Eq. 6 and the initial particle count, swept on the analytic room map
+    (synth.room_map_weights), whose pose landscape has a unique optimum.
+    Q queries from the global spread (+-1 m, +-180 deg), observations
+    rendered by the FP32 form at seeded ground-truth poses (100 x 100, f =
+    138.9), three levels x 64 px, 64 + 64 samples, device loop under a CUDA
+    graph; per point: ms per batched update, median final errors and the
+    fraction of queries within 5 cm and 5 deg."""
+    import numpy as np
+    import torch
+    import synth
+    W = H = 100
+    focal = 138.9
+    taus = (0.01, 0.05, 0.1, 0.5, 1.0, 4.0)
+    n0s = (250, 500, 1000, 1500, 3000)
+    nmax = max(n0s)
+    blob, _ = synth.room_map_weights(0)
+    gm = M.Map(blob, max_rays=Q * nmax * 64, max_samples=192, max_particles=Q * nmax,
+               max_queries=Q)
+    K = M.intrinsics(focal, focal, W / 2, H / 2, W, H)
+    o32 = M.UpdateOptions(n_coarse=64, n_fine=128, precision="fp32")
+    allpx = np.stack(np.meshgrid(np.arange(W), np.arange(H), indexing="xy"), -1).reshape(-1, 2)
+    px_all = torch.tensor(allpx, dtype=torch.int32, device="cuda")
+    gts, imgs = [], []
+    for q in range(Q):
+        g = synth.gt_pose(100 + q)
+        gts.append(g)
+        P = torch.tensor(g[0][None], dtype=torch.float32, device="cuda")
+        imgs.append(gm.render(P, K, 2, px_all, o32).reshape(H, W, 3).contiguous())
+
+    def point(n0, tau):
+        sch = M.schedule([0, 1, 2], [64, 64, 64], [n0, max(2 * n0 // 3, 64), max(n0 // 3, 64)],
+                         n_min=64, iter_caps=[iters // 3] * 3, refine=[0.02, 0.005, 0.0],
+                         iterations=iters, sigma_t=0.02, sigma_yaw=0.02)
+        opts = M.UpdateOptions(n_coarse=64, n_fine=64, precision=prec, seed=1, tau=tau)
+        parts = torch.tensor(np.stack([synth.random_particles(200 + q, n0)[0] for q in range(Q)]),
+                             dtype=torch.float32, device="cuda")
+        gm.localize(parts.clone(), [n0] * Q, imgs, K, sch, opts, use_graph=True)   # build + warm
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        log, _ = gm.localize(parts.clone(), [n0] * Q, imgs, K, sch, opts, use_graph=True)
+        b.record()
+        torch.cuda.synchronize()
+        recs = M.Map.decode_log(log, Q, iters)
+        errs = [_pose_error(recs[q][-1]["est"], gts[q][1], gts[q][2]) for q in range(Q)]
+        return {"ms_per_update": a.elapsed_time(b) / iters,
+                "position_error_median": float(np.median([e[0] for e in errs])),
+                "yaw_error_deg_median": float(np.median([e[1] for e in errs])),
+                "success_5cm_5deg": sum(e[0] < 0.05 and e[1] < 5.0 for e in errs) / Q}
+
+    out = {"workload": f"room map, {Q} queries, 100x100, 3 levels x 64 px, 64+64 samples, "
+                       f"{iters} iterations, {prec}",
+           "tau_sweep_n0_1500": {str(t): point(1500, t) for t in taus},
+           "n0_sweep_tau_0.1": {str(n): point(n, 0.1) for n in n0s}}
+    gm.close()
+    return out
+
+
 # --------------------------------------------------------------- GPU arm
 def job_rate(dist, seconds, units, device="cpu"):
     """Whole-job throughput over the ranks of a run: the units every rank
@@ -635,6 +695,11 @@ def run_ours(args):
             cpu = {"value": None, "unit": UNIT, "cores": None, "kind": "oracle",
                    "sample": f"failed: {e}"}
     extra = {}
+    if world == 1 and args.sweeps:
+        try:
+            extra["sweeps"] = run_sweeps(M, prec)
+        except Exception as e:  # an extra workload must never hide the main line
+            extra["sweeps"] = {"failed": f"{type(e).__name__}: {e}"}
     if world == 1 and not args.no_extra:
         for name, fn in (
                 ("coarse_to_fine", lambda: run_coarse_to_fine(M, img, K, seed, prec)),
@@ -685,6 +750,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the coarse-to-fine, proposal and batched-query workloads")
+    ap.add_argument("--sweeps", action="store_true",
+                    help="add the tau and initial-particle-count sweeps on the room map")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
