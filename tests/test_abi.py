@@ -80,3 +80,40 @@ def test_binding_constants_match_header():
     assert {v[0] for v in M.MLP_VARIANT_TABLE.values()} == {"bf16", "fp8"}
     for prec, code in (("FP32", M.PREC_FP32), ("BF16", M.PREC_BF16), ("FP8", M.PREC_FP8)):
         assert d["MCL_PREC_" + prec] == code
+
+
+STRUCTS = {"Arch": "mcl_arch", "MapConfig": "mcl_map_config", "Intrinsics": "mcl_intrinsics",
+           "Opts": "mcl_opts", "Debug": "mcl_debug", "Schedule": "mcl_schedule",
+           "IterRecord": "mcl_iter_record", "TrainCfg": "mcl_train_cfg"}
+
+
+def test_struct_layouts_match_binding(tmp_path):
+    """Every ctypes structure of the binding has the size, field names and
+    field offsets of its C struct in include/mcl.h, as the host C compiler
+    lays it out (a plain C program prints sizeof / offsetof)."""
+    import ctypes as C
+    import shutil
+    import subprocess
+    import paper_2406_12202_gb300 as M
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no host C compiler")
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "mcl.h"', "int main(void) {"]
+    for py, cs in STRUCTS.items():
+        lines.append(f'    printf("{py} sizeof %zu\\n", sizeof({cs}));')
+        for f in getattr(M, py)._fields_:
+            lines.append(f'    printf("{py} {f[0]} %zu\\n", offsetof({cs}, {f[0]}));')
+    lines += ["    return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.check_call([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    got = {}
+    for line in subprocess.check_output([str(exe)], text=True).splitlines():
+        py, field, val = line.split()
+        got[(py, field)] = int(val)
+    for py in STRUCTS:
+        cls = getattr(M, py)
+        assert got[(py, "sizeof")] == C.sizeof(cls), py
+        for f in cls._fields_:
+            assert got[(py, f[0])] == getattr(cls, f[0]).offset, (py, f[0])
