@@ -117,3 +117,34 @@ def test_struct_layouts_match_binding(tmp_path):
         assert got[(py, "sizeof")] == C.sizeof(cls), py
         for f in cls._fields_:
             assert got[(py, f[0])] == getattr(cls, f[0]).offset, (py, f[0])
+
+
+def test_decode_log_order_and_fields():
+    """mcl_localize writes record q * iterations + t for query q, iteration t;
+    the binding decodes it into per-query lists with every field."""
+    import ctypes as C
+    import numpy as np
+    import torch
+    import paper_2406_12202_gb300 as M
+    Q, T = 3, 4
+    recs = (M.IterRecord * (Q * T))()
+    for q in range(Q):
+        for t in range(T):
+            r = recs[q * T + t]
+            r.stage, r.level, r.n_particles, r.n_pixels = t % 3, (t + 1) % 3, 1000 + q, 16 << q
+            r.n_survivors, r.status, r.spread = 900 + t, q, 0.5 ** t
+            for i in range(4):
+                r.est[i] = q + 0.25 * i - t
+            r.t_start_ns = (1 << 40) + 1000 * q + t
+    log = torch.from_numpy(np.frombuffer(bytes(recs), dtype=np.uint8).copy())
+    out = M.Map.decode_log(log, Q, T)
+    assert len(out) == Q and all(len(rows) == T for rows in out)
+    for q in range(Q):
+        for t in range(T):
+            d = out[q][t]
+            assert (d["stage"], d["level"], d["n_particles"], d["n_pixels"]) == (t % 3, (t + 1) % 3,
+                                                                                  1000 + q, 16 << q)
+            assert (d["n_survivors"], d["status"], d["spread"]) == (900 + t, q, 0.5 ** t)
+            assert d["est"] == [q + 0.25 * i - t for i in range(4)]
+            assert d["t_start_ns"] == (1 << 40) + 1000 * q + t
+    assert C.sizeof(M.IterRecord) * Q * T == log.numel()
