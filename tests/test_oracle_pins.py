@@ -364,6 +364,19 @@ def test_weights_closed_form_and_permutation():
     assert np.allclose(rp["S"], S[perm], rtol=1e-13)
 
 
+def test_weights_invariant_to_repeating_the_pixel_set():
+    """Eq. 6: every pixel taken twice doubles B and every S_i, so the
+    log-weights 4 (log B - log S_i) and the normalised weights are unchanged
+    (scale invariance of the normalisation)."""
+    blob, P, img, K4, px, opts = _scene(16, 4, 8)
+    P = P[:-1]
+    r1 = oracle.update(blob, P, img, K4, 1, px, opts)
+    r2 = oracle.update(blob, P, img, K4, 1, np.concatenate([px, px]), opts)
+    assert np.allclose(r2["S"], 2 * r1["S"], rtol=1e-14)
+    assert np.allclose(r2["logw"], r1["logw"], rtol=1e-13, atol=1e-13)
+    assert np.allclose(r2["w"], r1["w"], rtol=1e-12, atol=1e-300)
+
+
 def test_update_matches_rendered_rays():
     """S_i is the sum over j of E_ij F_ij with E the squared RGB distance."""
     blob, P, img, K4, px, opts = _scene(14, 2, 4)
