@@ -185,17 +185,20 @@ int mcl_resample(mcl_map* map, const double* d_w, int N_in, int N_out,
  * executing while a stream is captured into a CUDA graph, or a filter that
  * has no map.  The paper has no counterpart; this entry point only changes
  * where the scratch lives.  It needs no map and allocates nothing: its
- * scratch (the integer CDF of up to MCL_RESAMPLE_NOALLOC_MAX_IN weights and a
- * status word, about 512 KB) is a fixed array in the library image, present
- * on every device that loads the library until the process exits.  The first
- * call on a device looks up that array's device address (with that device
- * current); make that first call before any stream capture.  Every call
- * shares the array: calls that overlap on the GPU (different streams, or
- * different host threads on one device) race and must be serialised by the
- * caller.  N_in > MCL_RESAMPLE_NOALLOC_MAX_IN is rejected with MCL_ERR_ARG.
- * Negative, non-finite or all-zero weights give d_idx[k] = -1 for every k.
- * d_w: [N_in] f64, d_idx: [N_out] int32, 1 <= N_out <= 65536,
- * 0 <= u0 < 1. */
+ * scratch (the integer CDF of up to MCL_RESAMPLE_NOALLOC_MAX_IN weights,
+ * 512 KB) is a fixed array in the library image, present on every device
+ * that loads the library until the process exits.  The first call on a
+ * device looks up that array's device address (with that device current)
+ * and caches it; make that first call before any stream capture, and do not
+ * call this entry point on a device after cudaDeviceReset() (the cached
+ * address would be stale).  Every call shares the array: calls that overlap
+ * on the GPU (different streams, or different host threads on one device)
+ * race and must be serialised by the caller.  d_w and d_idx must be device
+ * memory of the current device (MCL_ERR_ARG otherwise).  N_in >
+ * MCL_RESAMPLE_NOALLOC_MAX_IN is rejected with MCL_ERR_ARG.  Negative,
+ * non-finite or all-zero weights give d_idx[k] = -1 for every k (there is
+ * no status word).  d_w: [N_in] f64, d_idx: [N_out] int32, 1 <= N_out <=
+ * 65536, 0 <= u0 < 1. */
 int mcl_resample_noalloc(const double* d_w, int N_in, int N_out, double u0,
                          int32_t* d_idx, void* stream);
 

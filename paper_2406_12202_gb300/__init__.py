@@ -452,15 +452,22 @@ RESAMPLE_NOALLOC_MAX_IN = 65536
 def resample_noalloc(w, n_out: int, u0: float, idx=None):
     """Systematic resampling without a map and without any device allocation
     in the library (mcl_resample_noalloc).  Same indices as Map.resample for
-    the same weights and u0.  Calls that overlap on the GPU race on the
-    library's fixed scratch, so issue them from one stream."""
+    the same weights and u0.  The call runs on w's device (made current for
+    the call, on that device's current stream); idx must live there too.
+    Calls that overlap on the GPU race on the library's fixed scratch, so
+    issue them from one stream."""
     torch = _torch()
+    if not (isinstance(w, torch.Tensor) and w.is_cuda):
+        raise TypeError("w must be a CUDA tensor")
     n_in = w.shape[0]
-    if idx is None:
-        idx = torch.empty(n_out, dtype=torch.int32, device=w.device)
-    _check(lib().mcl_resample_noalloc(_ptr(w, torch.float64, (n_in,), "w"), n_in, int(n_out),
-                                      float(u0), _ptr(idx, torch.int32, (n_out,), "idx"),
-                                      _stream()))
+    with torch.cuda.device(w.device):
+        if idx is None:
+            idx = torch.empty(n_out, dtype=torch.int32, device=w.device)
+        elif not (isinstance(idx, torch.Tensor) and idx.device == w.device):
+            raise ValueError(f"idx must be on {w.device}")
+        _check(lib().mcl_resample_noalloc(_ptr(w, torch.float64, (n_in,), "w"), n_in, int(n_out),
+                                          float(u0), _ptr(idx, torch.int32, (n_out,), "idx"),
+                                          _stream()))
     return idx
 
 

@@ -24,6 +24,8 @@ int fail(int code, const char* fmt, ...) {
     return code;
 }
 
+void clear_error() { g_err[0] = 0; }
+
 int cuda_check(cudaError_t e, const char* what) {
     if (e == cudaSuccess) return MCL_OK;
     return fail(MCL_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));

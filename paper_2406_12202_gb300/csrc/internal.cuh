@@ -133,6 +133,7 @@ namespace mcl {
 
 // Thread-local error reporting (api.cu).
 int fail(int code, const char* fmt, ...);
+void clear_error();
 int cuda_check(cudaError_t e, const char* what);
 // Count of kernels launched by the library (api.cu).
 void note_launch(int n = 1);
@@ -175,6 +176,7 @@ cudaError_t mlp_tc(mcl_map* m, int precision, const Ray* rays, const float* gd, 
                    int S, int n_rays, const int* rows_dev, float4* out, cudaStream_t s);
 
 // resample.cu
+// status may be NULL (degenerate weights then show only as idx = -1)
 cudaError_t launch_resample(const double* w, int n_in, int n_out, double u0, int32_t* idx,
                             unsigned long long* cdf, Status* status, cudaStream_t s);
 cudaError_t launch_predict(const float* in, int n_in, const int32_t* idx, int n_out,

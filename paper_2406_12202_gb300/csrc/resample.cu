@@ -13,7 +13,7 @@ __global__ __launch_bounds__(kResThreads) void k_resample(const double* __restri
                                                           int n_out, double u0,
                                                           int32_t* __restrict__ idx,
                                                           u64* __restrict__ cdf, Status* status) {
-    if (!resample_block(w, n_in, n_out, u0, idx, cdf) && threadIdx.x == 0)
+    if (!resample_block(w, n_in, n_out, u0, idx, cdf) && threadIdx.x == 0 && status)
         atomicCAS(&status->code, 0, MCL_ERR_DEGENERATE);
 }
 
