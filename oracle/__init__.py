@@ -91,6 +91,9 @@ def lib():
             L.orc_motion_noise.argtypes = [C.c_int, C.c_uint64, C.c_uint64,
                                            C.c_double, C.c_double, dp]
             L.orc_position_spread.argtypes = [C.c_int, dp, dp]
+            L.orc_loop_statistics.argtypes = [C.c_int, dp, dp, C.POINTER(C.c_uint8), dp]
+            L.orc_loop_schedule.argtypes = [ip, C.c_int, dp, ip, ip, C.c_int, C.c_int,
+                                            C.c_double, C.c_int]
             L.orc_num_threads.restype = C.c_int
             L.orc_pixel_set.argtypes = [C.c_int, C.c_int, C.c_int, C.c_uint64, C.c_uint64,
                                         C.POINTER(C.c_int32)]
@@ -419,6 +422,37 @@ def position_spread(poses):
     out = np.zeros(4)
     lib().orc_position_spread(P.shape[0], pp, out.ctypes.data_as(C.POINTER(C.c_double)))
     return dict(mean=out[:3].copy(), trace=float(out[3]))
+
+
+def loop_statistics(poses, w, mask):
+    """Weighted mean position, circular weighted yaw, weighted position spread
+    and survivor count of one weighted particle set (orc_loop_statistics)."""
+    P, pp = _d(np.reshape(poses, (-1, 12)))
+    wv, wp = _d(np.reshape(w, -1))
+    mk = np.ascontiguousarray(np.reshape(mask, -1), dtype=np.uint8)
+    assert wv.shape[0] == P.shape[0] == mk.shape[0]
+    out = np.zeros(6)
+    lib().orc_loop_statistics(P.shape[0], pp, wp, mk.ctypes.data_as(C.POINTER(C.c_uint8)),
+                              out.ctypes.data_as(C.POINTER(C.c_double)))
+    return dict(mean=out[:3].copy(), yaw=float(out[3]), spread=float(out[4]),
+                n_survivors=int(out[5]))
+
+
+def loop_schedule(stage, iter_at_stage, n_survivors, spread, refine, iter_cap, n_cap, n_min,
+                  stride):
+    """Next (stage, iter_at_stage, N) of the coarse-to-fine schedule
+    (orc_loop_schedule)."""
+    st = np.array([stage, iter_at_stage, 0], dtype=np.int32)
+    ns = len(refine)
+    rf = np.ascontiguousarray(refine, dtype=np.float64)
+    ic = np.ascontiguousarray(iter_cap, dtype=np.int32)
+    nc = np.ascontiguousarray(n_cap, dtype=np.int32)
+    assert len(ic) == len(nc) == ns
+    ip = C.POINTER(C.c_int)
+    lib().orc_loop_schedule(st.ctypes.data_as(ip), ns, rf.ctypes.data_as(C.POINTER(C.c_double)),
+                            ic.ctypes.data_as(ip), nc.ctypes.data_as(ip), int(n_min), int(stride),
+                            float(spread), int(n_survivors))
+    return int(st[0]), int(st[1]), int(st[2])
 
 
 def level_intrinsics(K4, factor):

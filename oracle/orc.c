@@ -729,6 +729,81 @@ void orc_position_spread(int n, const double* pose, double* out) {
     out[3] = tr / n;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Statistics of one weighted particle set, as the coarse-to-fine loop uses */
+/* them after the weights of an iteration (Sec. III-C, "Detailed            */
+/* Structure"; Alg. 1).  The paper's refinement test compares Var({x_t})    */
+/* with a threshold; the set it states it on is the resampled one, whose    */
+/* expected spread is the weighted spread of the set before resampling.     */
+/* This reading evaluates it on the weighted set (no resampling noise):     */
+/*   mean      m = sum_i w_i t_i / sum_i w_i        (t_i = position of x_i) */
+/*   spread    V = sum_i w_i |t_i - m|^2 / sum_i w_i                        */
+/*   yaw       atan2(sum_i w_i sin(yaw_i), sum_i w_i cos(yaw_i)),           */
+/*             yaw_i = atan2(R_i[0][2], R_i[0][0]) (rotation about +y)      */
+/*   survivors n_s = number of particles with mask_i = 1                    */
+/* out[0..2] = m, out[3] = yaw, out[4] = V, out[5] = n_s.  Particles with   */
+/* w_i = 0 (or all weights zero: out[0..4] = NaN) take no part.             */
+/* ------------------------------------------------------------------------ */
+void orc_loop_statistics(int n, const double* pose, const double* w, const uint8_t* mask,
+                         double* out) {
+    double W = 0.0, m[3] = {0, 0, 0}, ys = 0.0, yc = 0.0;
+    long ns = 0;
+    for (int i = 0; i < n; ++i) {
+        const double* p = pose + 12 * (long)i;
+        if (mask[i]) ++ns;
+        if (!(w[i] > 0.0)) continue;
+        W += w[i];
+        for (int c = 0; c < 3; ++c) m[c] += w[i] * p[4 * c + 3];
+        double yaw = atan2(p[2], p[0]);
+        ys += w[i] * sin(yaw);
+        yc += w[i] * cos(yaw);
+    }
+    for (int c = 0; c < 3; ++c) m[c] /= W;
+    double V = 0.0;
+    for (int i = 0; i < n; ++i) {
+        const double* p = pose + 12 * (long)i;
+        if (!(w[i] > 0.0)) continue;
+        for (int c = 0; c < 3; ++c) {
+            double dd = p[4 * c + 3] - m[c];
+            V += w[i] * dd * dd;
+        }
+    }
+    out[0] = m[0]; out[1] = m[1]; out[2] = m[2];
+    out[3] = atan2(ys, yc);
+    out[4] = V / W;
+    out[5] = (double)ns;
+}
+
+/* ------------------------------------------------------------------------ */
+/* One step of the coarse-to-fine schedule (Sec. III-C): the paper moves to */
+/* the next resolution level when Var({x_t}) falls below delta_refine; this */
+/* reading also moves after a per-stage iteration cap, and sets the next    */
+/* particle count from the survivors of the rejection weighting:            */
+/*   refine  = stage < n_stages - 1 and (V < refine[stage] or               */
+/*             iter_at_stage + 1 >= iter_cap[stage])                        */
+/*   stage'  = stage + 1, iter' = 0   if refine                             */
+/*             stage,     iter + 1    otherwise                             */
+/*   N'      = min(max(n_s, n_min), n_cap[stage'], stride)                  */
+/* state[0..2] = (stage, iter_at_stage, N) in, (stage', iter', N') out.     */
+/* ------------------------------------------------------------------------ */
+void orc_loop_schedule(int* state, int n_stages, const double* refine, const int* iter_cap,
+                       const int* n_cap, int n_min, int stride, double V, int n_s) {
+    int stage = state[0], it = state[1];
+    if (stage < n_stages - 1 && (V < refine[stage] || it + 1 >= iter_cap[stage])) {
+        stage += 1;
+        it = 0;
+    } else {
+        it += 1;
+    }
+    int N = n_s;
+    if (N < n_min) N = n_min;
+    if (N > n_cap[stage]) N = n_cap[stage];
+    if (N > stride) N = stride;
+    state[0] = stage;
+    state[1] = it;
+    state[2] = N;
+}
+
 /* ======================================================================== */
 /* Learned proposal sampler (not in the paper; a project extension that     */
 /* replaces the coarse pass).  Network: gamma(x) with 6 frequencies (39     */

@@ -232,6 +232,43 @@ def proposal_init_weights(seed: int = 0, head_bias: float = 1.0) -> np.ndarray:
     return np.concatenate(parts).astype(np.float32)
 
 
+def room_proposal_weights(half: float = 3.0, eps: float = 0.015625,
+                          density: float = 64.0) -> np.ndarray:
+    """Hand-set proposal blob whose raw density is exactly the room map's
+    density, density * clamp((max_c |x_c| - half) / eps, 0, 1), built from
+    the proposal network's ReLU units on the identity part of its input
+    (gamma(x) entries 0..2 = x): |x_c| = relu(x_c) + relu(-x_c) (layer 1),
+    |x|, relu(|y| - |x|), |z| (layer 2), max(|x|, |y|) and
+    relu(|z| - max(|x|, |y|)) (layer 3), relu(t) and relu(t - 1) with
+    t = (m - half) / eps (layer 4), head density * (relu(t) - relu(t - 1))."""
+    L = {n: (np.zeros((fo, fi)), np.zeros(fo)) for n, fi, fo in PROPOSAL_SHAPES}
+    W1 = L["p1"][0]
+    for c in range(3):
+        W1[2 * c, c] = 1.0
+        W1[2 * c + 1, c] = -1.0
+    W2 = L["p2"][0]
+    W2[0, 0] = W2[0, 1] = 1.0                       # |x|
+    W2[1, 2] = W2[1, 3] = 1.0                       # relu(|y| - |x|)
+    W2[1, 0] = W2[1, 1] = -1.0
+    W2[2, 4] = W2[2, 5] = 1.0                       # |z|
+    W3 = L["p3"][0]
+    W3[0, 0] = W3[0, 1] = 1.0                       # max(|x|, |y|)
+    W3[1, 2] = 1.0                                  # relu(|z| - max(|x|, |y|))
+    W3[1, 0] = W3[1, 1] = -1.0
+    W4, b4 = L["p4"]
+    W4[0, 0] = W4[0, 1] = 1.0 / eps
+    W4[1, 0] = W4[1, 1] = 1.0 / eps
+    b4[0] = -half / eps
+    b4[1] = -half / eps - 1.0
+    Wh = L["head"][0]
+    Wh[0, 0], Wh[0, 1] = density, -density
+    parts = []
+    for name, fi, fo in PROPOSAL_SHAPES:
+        parts.append(L[name][0].reshape(-1))
+        parts.append(L[name][1])
+    return np.concatenate(parts).astype(np.float32)
+
+
 # --------------------------------------------------------------------------
 # Poses: particle = T(x, y, z) * R_y(yaw), stored as a row-major 3x4 [R | t].
 # --------------------------------------------------------------------------
