@@ -6,11 +6,14 @@ shared pixels of a 400x400 observation, focal 555.6, 64 stratified + 128
 importance samples per ray, Eq. 5 uncertainty, Eq. 6 rejection weights, FP64
 normalisation, systematic resampling, the motion model and the position
 spread of the refinement test).  The metric is ray-samples per second
-(rays x composited samples / time) with the MCL-update milliseconds, for the
-selected MLP precision, next to the plain FP32 GPU form on the same box.
+(rays x composited samples / time) with the MCL-update milliseconds.  The
+headline value is the plain FP32 form (the paper's precision); the BF16,
+FP8 and learned-proposal + FP8 forms are reported beside it (key "forms")
+with their speed-up, their roofline and their error against the FP64
+oracle, and the equal-pose-error comparison runs on the analytic room map.
 
-python bench.py [--gpus N] [--steps K] [--warmup W] [--precision P]
-                [--impl ours|reference]
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                [--no-extra] [--no-cpu-baseline] [--sweeps]
 Under torchrun every rank localises its own query (its own seed): weak
 scaling, no data-path collective.  Rank 0 prints one JSON line.
 """
@@ -46,30 +49,25 @@ def load_peaks():
             "sm_max_mhz": 2070.0}, "fallback"
 
 
-def profiled_traffic(kernel_file: str, sources):
+def profiled_traffic(name: str, sources):
     """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum)
-    from the committed ncu summary of a kernel, or None when the kernel's
-    sources have changed since the capture (the summary records their hash)."""
+    of a kernel from profiles/<name>.json (written beside the ncu summary
+    profiles/<name>.md), or None when that file is missing or the kernel's
+    sources have changed since the capture (the file records their hash)."""
     import hashlib
-    path = os.path.join(ROOT, "profiles", kernel_file)
+    path = os.path.join(ROOT, "profiles", name + ".json")
     if not os.path.exists(path):
         return None
     h = hashlib.sha256()
     for src in sources:
         with open(os.path.join(ROOT, "paper_2406_12202_gb300", "csrc", src), "rb") as f:
             h.update(f.read())
-    fields = {}
     with open(path) as f:
-        for line in f:
-            if ":" in line and not line.startswith(("#", "|", " ")):
-                k, v = line.split(":", 1)
-                fields[k.strip()] = v.strip().split()[0] if v.strip() else ""
-    if fields.get("source_sha16") != h.hexdigest()[:16]:
+        rec = json.load(f)
+    if rec.get("source_sha16") != h.hexdigest()[:16]:
         return None
-    try:
-        return float(fields["traffic_bytes_per_launch"])
-    except (KeyError, ValueError):
-        return None
+    v = rec.get("traffic_bytes_per_launch")
+    return float(v) if v is not None else None
 
 
 # ------------------------------------------------------------------ clocks
@@ -315,8 +313,8 @@ def run_proposal_fp8(M, gm, img, K, seed, steps, warmup, wl):
     (4 x 64, gamma with 6 frequencies) is distilled on the GPU from the
     64 + 128 FP32 sampler over 2000 seeded poses x 64 pixels (128,000 rays,
     64 bins); then 64 proposal samples -> 32 guided + 32 importance samples
-    per ray through the FP8 MLP.  Accuracy against the FP32 full sampler on
-    the same particles and pixels."""
+    per ray through the FP8 MLP.  Returns the timing and the trained proposal
+    weights."""
     import numpy as np
     import torch
     import synth
@@ -357,26 +355,17 @@ def run_proposal_fp8(M, gm, img, K, seed, steps, warmup, wl):
             ms.append(a.elapsed_time(b))
     phases, _ = gm.profile_read(reset=True)
     gm.profile(False)
-    # accuracy against the FP32 full sampler (same particles, pixel set 0)
-    g = gm.update(P, img, K, wl["level"], pxs[0], prop, debug=True)
-    r = gm.update(P, img, K, wl["level"], pxs[0], full32, debug=True)
-    torch.cuda.synchronize()
-    from scipy.stats import spearmanr
-    e = (g["rgb"] - r["rgb"]).abs()
-    lw_g, lw_r = g["logw"].cpu().numpy(), r["logw"].cpu().numpy()
-    fin = np.isfinite(lw_g) & np.isfinite(lw_r)
-    top = len(set(np.argsort(-lw_g)[:10]) & set(np.argsort(-lw_r)[:10]))
     mean_ms = sum(ms) / len(ms)
-    return {"workload": "learned proposal (64 -> 32 guided + 32 importance) + FP8 MLP, "
-                        "600 particles x 64 px of 400x400",
-            "ms_per_step": mean_ms, "ray_samples_per_s": N * Bpx * 64 / (mean_ms / 1e3),
-            "phases_ms_per_step": {k: v / steps for k, v in phases.items()},
-            "phase_note": "sample = proposal MLP + inverse-CDF sampling; mlp_coarse = NeRF MLP on "
-                          "the guided samples",
-            "train_s": train_s, "train_rays": 2000 * Bpx, "train_loss_first_last": [float(losses[0]), float(losses[-1])],
-            "vs_fp32_full_sampler": {"rgb_mean_abs": float(e.mean()), "rgb_max_abs": float(e.max()),
-                                     "spearman_logw": float(spearmanr(lw_g[fin], lw_r[fin]).correlation),
-                                     "top10_overlap": top}}
+    res = {"workload": "learned proposal (64 -> 32 guided + 32 importance) + FP8 MLP, "
+                       "600 particles x 64 px of 400x400",
+           "ms_per_step": mean_ms, "ray_samples_per_s": N * Bpx * 64 / (mean_ms / 1e3),
+           "ray_samples_note": "composited samples per ray: 32 guided + 32 importance",
+           "phases_ms_per_step": {k: v / steps for k, v in phases.items()},
+           "phase_note": "sample = proposal MLP + inverse-CDF sampling; mlp_coarse = NeRF MLP on "
+                         "the guided samples",
+           "train_s": train_s, "train_rays": 2000 * Bpx,
+           "train_loss_first_last": [float(losses[0]), float(losses[-1])]}
+    return res, gm.proposal_get()
 
 
 def run_batched(M, seed, W, H, focal, use_proposal_blob=None):
@@ -514,6 +503,131 @@ def job_rate(dist, seconds, units, device="cpu"):
     return float(t.item()), float(u.item()), float(u.item()) / float(t.item())
 
 
+def run_pose_error(M, Q=10, iters=30):
+    """Equal-pose-error comparison (Sec. IV-A accuracy definition: position
+    error < 5 cm and rotation error < 5 deg) on the analytic room map, whose
+    pose landscape has a unique optimum: Q queries from the global spread
+    (+-1 m, +-180 deg), each with its own seeded ground truth and the same
+    initial particles for every form, localised by the device loop (one CUDA
+    graph for all queries) with the plain FP32 form (64 + 64 samples), the
+    BF16 form (64 + 64) and the FP8 form with the learned proposal
+    (64 -> 32 guided + 32 importance) distilled on this map.  100 x 100
+    observations rendered by the FP32 form at the ground truths, three levels
+    x 64 px, 1000 / 500 / 250 particles."""
+    import numpy as np
+    import torch
+    import synth
+    W = H = 100
+    focal = 138.9
+    N0 = 1000
+    blob, _ = synth.room_map_weights(0)
+    gm = M.Map(blob, max_rays=Q * N0 * 64, max_samples=128, max_particles=Q * N0,
+               max_queries=Q)
+    K = M.intrinsics(focal, focal, W / 2, H / 2, W, H)
+    o32 = M.UpdateOptions(n_coarse=64, n_fine=64, precision="fp32")
+    allpx = np.stack(np.meshgrid(np.arange(W), np.arange(H), indexing="xy"), -1).reshape(-1, 2)
+    px_all = torch.tensor(allpx, dtype=torch.int32, device="cuda")
+    gts, imgs = [], []
+    for q in range(Q):
+        g = synth.gt_pose(100 + q)
+        gts.append(g)
+        imgs.append(gm.render(torch.tensor(g[0][None], dtype=torch.float32, device="cuda"), K, 2,
+                              px_all, o32).reshape(H, W, 3).contiguous())
+    # learned proposal distilled from the FP32 full sampler on this map
+    Ptr = torch.tensor(synth.random_particles(21, 256)[0], dtype=torch.float32, device="cuda")
+    pxtr = torch.tensor(synth.pixel_set(21, 25, 25, 64), dtype=torch.int32, device="cuda")
+    gm.proposal_set(synth.proposal_init_weights(0))
+    gm.proposal_train(Ptr, pxtr, K, 0, M.UpdateOptions(n_coarse=64, n_fine=128, precision="fp32"),
+                      epochs=40, batch_rays=2048, n_bins=64, lr=3e-3, lr_end=1e-4, seed=1)
+    sch = M.schedule([0, 1, 2], [64, 64, 64], [N0, N0 // 2, N0 // 4], n_min=100,
+                     iter_caps=[iters // 3] * 3, refine=[0.02, 0.005, 0.0], iterations=iters,
+                     sigma_t=0.02, sigma_yaw=0.02)
+    parts0 = torch.tensor(np.stack([synth.random_particles(200 + q, N0)[0] for q in range(Q)]),
+                          dtype=torch.float32, device="cuda")
+    forms = {
+        "fp32_full_64+64": M.UpdateOptions(n_coarse=64, n_fine=64, precision="fp32", seed=1),
+        "bf16_full_64+64": M.UpdateOptions(n_coarse=64, n_fine=64, precision="bf16", seed=1),
+        "fp8_proposal_64->32+32": M.UpdateOptions(n_coarse=64, n_fine=32, precision="fp8", seed=1,
+                                                   use_proposal=True, n_proposal=64,
+                                                   n_guided=32),
+    }
+    out = {"workload": f"room map, {Q} queries (seeds 100..{99 + Q}), 100x100, 3 levels x 64 px, "
+                       f"{N0}/{N0 // 2}/{N0 // 4} particles, {iters} iterations, one CUDA graph "
+                       "per form; accuracy = position < 5 cm and rotation < 5 deg (Sec. IV-A)"}
+    for name, opts in forms.items():
+        gm.localize(parts0.clone(), [N0] * Q, imgs, K, sch, opts, use_graph=True)   # build + warm
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        log, _ = gm.localize(parts0.clone(), [N0] * Q, imgs, K, sch, opts, use_graph=True)
+        b.record()
+        torch.cuda.synchronize()
+        recs = M.Map.decode_log(log, Q, iters)
+        errs = [_pose_error(recs[q][-1]["est"], gts[q][1], gts[q][2]) for q in range(Q)]
+        out[name] = {"ms_per_batched_update": a.elapsed_time(b) / iters,
+                     "position_error_median": float(np.median([e[0] for e in errs])),
+                     "yaw_error_deg_median": float(np.median([e[1] for e in errs])),
+                     "accuracy_5cm_5deg": sum(e[0] < 0.05 and e[1] < 5.0 for e in errs) / Q,
+                     "position_errors": [float(e[0]) for e in errs]}
+    base = out["fp32_full_64+64"]["ms_per_batched_update"]
+    for name in forms:
+        out[name]["speedup_vs_fp32_form"] = base / out[name]["ms_per_batched_update"]
+    gm.close()
+    return out
+
+
+def fp64_error_leg(M, gm, blob, P, img, K, K4, px, forms, prop_blob, n_sample=32):
+    """Error against the FP64 oracle, after the timed regions, on a sample of
+    the run's own inputs: n_sample particles (evenly spaced indices) x the
+    first pixel set of the full-update workload.  Per form: RGB max / mean
+    absolute error against the oracle of the same sampler, Spearman rank
+    correlation and top-10 overlap of the particles' log-weights against
+    the oracle's full sampler (the method's own sampler, the judge of weight
+    error)."""
+    import numpy as np
+    import torch
+    import oracle
+    from scipy.stats import spearmanr
+    wl = WL
+    sel = np.linspace(0, wl["N"] - 1, n_sample).round().astype(int)
+    Ps = P[sel].contiguous()
+    Ph = Ps.cpu().numpy().astype(np.float64)
+    imgh = img.cpu().numpy().astype(np.float64)
+    pxh = px.cpu().numpy()
+    t0 = time.perf_counter()
+    ref = oracle.update(blob, Ph, imgh, K4, 1, pxh,
+                        oracle.make_opts(n_coarse=wl["n_coarse"], n_fine=wl["n_fine"]))
+    ref_prop = None
+    if prop_blob is not None:
+        o, d = [], []
+        for i in range(n_sample):
+            for j in range(pxh.shape[0]):
+                oi, di = oracle.ray(Ph[i], *K4, int(pxh[j, 0]), int(pxh[j, 1]))
+                o.append(oi)
+                d.append(di)
+        ref_prop = oracle.render_rays_proposal(
+            blob, prop_blob, np.array(o), np.array(d),
+            oracle.make_opts(n_coarse=64, n_fine=32), n_p=64, n_g=32)
+    oracle_s = time.perf_counter() - t0
+    lw_ref = ref["logw"]
+    top_ref = set(np.argsort(-lw_ref)[:10])
+    res = {"sample": f"{n_sample} of {wl['N']} particles (evenly spaced) x {pxh.shape[0]} px, "
+                     f"oracle {oracle_s:.1f} s"}
+    for name, opts in forms.items():
+        g = gm.update(Ps, img, K, wl["level"], px, opts, debug=True)
+        torch.cuda.synchronize()
+        rgb = g["rgb"].cpu().numpy().astype(np.float64)
+        lw = g["logw"].cpu().numpy().astype(np.float64)
+        same = ref_prop["rgb"] if (opts.use_proposal and ref_prop is not None) else ref["rgb"]
+        e = np.abs(rgb - same)
+        fin = np.isfinite(lw) & np.isfinite(lw_ref)
+        res[name] = {"rgb_max_abs": float(e.max()), "rgb_mean_abs": float(e.mean()),
+                     "rgb_reference": "oracle, same sampler",
+                     "spearman_logw_vs_full_sampler": float(spearmanr(lw[fin], lw_ref[fin]).correlation),
+                     "top10_overlap_vs_full_sampler": len(set(np.argsort(-lw)[:10]) & top_ref)}
+    return res
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -537,11 +651,7 @@ def run_ours(args):
     ns = wl["n_coarse"] + wl["n_fine"]
     blob = synth.he_init_weights(wl["map_seed"])
     gm = M.Map(blob, max_rays=N * Bpx, max_samples=ns, max_particles=N)
-    prec = args.precision
-    if prec == "auto":
-        prec = "bf16" if gm.supports("bf16") else "fp32"
     K = M.intrinsics(wl["focal"], wl["focal"], W / 2, H / 2, W, H)
-    opts = M.UpdateOptions(n_coarse=wl["n_coarse"], n_fine=wl["n_fine"], precision=prec)
     opts32 = M.UpdateOptions(n_coarse=wl["n_coarse"], n_fine=wl["n_fine"], precision="fp32")
 
     # query of this rank: particles, ground truth, observation rendered at GT
@@ -605,23 +715,19 @@ def run_ours(args):
         gm.profile(False)
         return ms, phases, l1 - l0
 
+    peaks, peak_src = load_peaks()
+    rows = N * Bpx * ns
+
+    # ---- headline: the plain FP32 form (the paper's precision) ----------
     gpu_id = os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0] or str(local)
     clocks = ClockSampler(gpu_id) if rank == 0 else None
-    ms, phases, launches = timed(opts, args.steps, args.warmup, profile=True, clocks=clocks)
+    ms, phases, launches = timed(opts32, args.steps, args.warmup, profile=True, clocks=clocks)
     clk = clocks.stop() if clocks else None
     total_s = sum(ms) / 1e3
     units = N * Bpx * ns * args.steps
     _, _, value = job_rate(dist, total_s, units, dev)
 
-    # plain FP32 GPU form on the same box (comparison the metric names)
-    fp32 = None
-    if prec != "fp32":
-        ms32, ph32, _ = timed(opts32, max(2, min(args.steps, 5)), 1, profile=True)
-        fp32 = {"ms_per_step": sum(ms32) / len(ms32),
-                "ray_samples_per_s": N * Bpx * ns * len(ms32) / (sum(ms32) / 1e3),
-                "mlp_ms_per_step": (ph32["mlp_coarse"] + ph32["mlp_fine"]) / len(ms32)}
-
-    # end to end through the public API with host buffers (pinned)
+    # end to end through the public API with host buffers (pinned), FP32 form
     hP = P0.cpu().pin_memory()
     himg = img.cpu().pin_memory()
     hpx = pxs.cpu().pin_memory()
@@ -642,7 +748,7 @@ def run_ours(args):
         dP.copy_(hP, non_blocking=True)
         dimg.copy_(himg, non_blocking=True)
         dpx.copy_(hpx[k], non_blocking=True)
-        gm.update(dP, dimg, K, wl["level"], dpx, opts, out=out)
+        gm.update(dP, dimg, K, wl["level"], dpx, opts32, out=out)
         gm.resample(out["w"], N, u0s[k], idx=idx)
         M.predict(dP, idx, N, wl["sigma_t"], wl["sigma_yaw"], seed, k, out=P_next)
         hw.copy_(out["w"], non_blocking=True)
@@ -655,37 +761,78 @@ def run_ours(args):
             e2e_ms.append(a.elapsed_time(b))
     e2e_t, _, e2e_value = job_rate(dist, sum(e2e_ms) / 1e3, units, dev)
 
+    # ---- the optimised forms on the same workload -------------------------
+    forms = {}
+    form_opts = {}
+    tc = [p for p in ("bf16", "fp8") if gm.supports(p)]
+    for prec in tc:
+        o = M.UpdateOptions(n_coarse=wl["n_coarse"], n_fine=wl["n_fine"], precision=prec)
+        ms_p, ph_p, _ = timed(o, args.steps, args.warmup, profile=True)
+        mlp_ms = (ph_p["mlp_coarse"] + ph_p["mlp_fine"]) / args.steps
+        flops = 2.0 * M.TC_MAC_PER_SAMPLE * rows
+        peak = peaks["bf16_tflops"] * (2.0 if prec == "fp8" else 1.0)
+        roof = {"bound": "tensor", "achieved": flops / (mlp_ms / 1e3) / 1e12, "peak": peak,
+                "unit": "TFLOP/s", "peak_source": f"bf16_tflops burst ({peak_src})"
+                + (" x 2 nominal fp8/bf16 ratio" if prec == "fp8" else ""),
+                "kernel": "k_mlp_tc (coarse + fine passes)", "mlp_ms_per_step": mlp_ms}
+        roof["frac"] = roof["achieved"] / roof["peak"]
+        roof["achieved_survey_flops"] = 2.0 * MAC_PER_SAMPLE_FP32 * rows / (mlp_ms / 1e3) / 1e12
+        roof["traffic"] = profiled_traffic(f"k_mlp_tc_c2_{prec}",
+                                           ("mlp_tc.cu", "tc_ptx.cuh", "stages.cuh"))
+        m_ = sum(ms_p) / len(ms_p)
+        forms[prec] = {"ms_per_step": m_, "ray_samples_per_s": N * Bpx * ns / (m_ / 1e3),
+                       "speedup_vs_fp32_form": (sum(ms) / len(ms)) / m_,
+                       "phases_ms_per_step": {k: v / args.steps for k, v in ph_p.items()},
+                       "roofline": roof}
+        form_opts[prec] = o
+    prop_blob = None
+    if "fp8" in tc and world == 1 and not args.no_extra:
+        try:
+            forms["proposal_fp8"], prop_blob = run_proposal_fp8(M, gm, img, K, seed, args.steps,
+                                                                args.warmup, wl)
+            forms["proposal_fp8"]["speedup_vs_fp32_form"] = (sum(ms) / len(ms)) / \
+                forms["proposal_fp8"]["ms_per_step"]
+            form_opts["proposal_fp8"] = M.UpdateOptions(n_coarse=64, n_fine=32, precision="fp8",
+                                                        use_proposal=True, n_proposal=64,
+                                                        n_guided=32)
+        except Exception as e:  # an extra workload must never hide the main line
+            forms["proposal_fp8"] = {"failed": f"{type(e).__name__}: {e}"}
+
     if rank != 0:
         if dist is not None:
             dist.barrier()
             dist.destroy_process_group()
         return
 
-    # roofline of the dominant kernel (the NeRF MLP)
-    peaks, peak_src = load_peaks()
+    # roofline of the dominant kernel of the headline step: the FP32 SIMT
+    # GEMMs of the NeRF MLP (FP32 FMA lanes are the bound)
     mlp_ms = (phases["mlp_coarse"] + phases["mlp_fine"]) / args.steps
-    rows = N * Bpx * ns
-    if prec == "fp32":
-        flops = 2.0 * MAC_PER_SAMPLE_FP32 * rows
-        peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-        roof = {"bound": "alu", "achieved": flops / (mlp_ms / 1e3) / 1e12, "peak": peak,
-                "unit": "TFLOP/s", "peak_source": f"152 SMs x 128 FP32 lanes x 2 x "
-                f"{peaks.get('sm_max_mhz', 2070.0):.0f} MHz ({peak_src} clock)"}
-    else:
-        flops = 2.0 * M.TC_MAC_PER_SAMPLE * rows
-        peak = peaks["bf16_tflops"] * (2.0 if prec == "fp8" else 1.0)
-        roof = {"bound": "tensor", "achieved": flops / (mlp_ms / 1e3) / 1e12, "peak": peak,
-                "unit": "TFLOP/s", "peak_source": f"bf16_tflops burst ({peak_src})"
-                + (" x 2 nominal fp8/bf16 ratio" if prec == "fp8" else "")}
+    mhz = peaks.get("sm_max_mhz", 2070.0)
+    peak = 152 * 128 * 2 * mhz * 1e6 / 1e12
+    roof = {"bound": "alu", "achieved": 2.0 * MAC_PER_SAMPLE_FP32 * rows / (mlp_ms / 1e3) / 1e12,
+            "peak": peak, "unit": "TFLOP/s",
+            "peak_source": f"152 SMs x 128 FP32 lanes x 2 FLOP x {mhz:.0f} MHz ({peak_src} "
+                           "max SM clock)",
+            "kernel": "NeRF MLP, plain FP32 form (k_sgemm layers, PE, heads; coarse + fine)",
+            "mlp_ms_per_step": mlp_ms}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    prof_file = {"bf16": "k_mlp_tc_c2_bf16.md", "fp8": "k_mlp_tc_c2_fp8.md"}.get(prec)
-    roof["traffic"] = (profiled_traffic(prof_file, ("mlp_tc.cu", "tc_ptx.cuh"))
-                       if prof_file else None)
-    if roof["traffic"] is not None:
-        roof["traffic_note"] = ("DRAM bytes per k_mlp_tc launch (mean of the coarse and fine "
-                                f"pass), profiles/{prof_file}")
-    roof["kernel"] = "NeRF MLP (coarse + fine passes)"
-    roof["mlp_ms_per_step"] = mlp_ms
+    roof["traffic"] = profiled_traffic("k_sgemm_c2_fp32", ("mlp_fp32.cu",))
+
+    # FP64 error of every form on a sample of this run's inputs (oracle, after
+    # the timed regions)
+    err = None
+    if world == 1 and not args.no_cpu_baseline:
+        try:
+            import oracle
+            oracle.build()
+            K4 = (float(np.float32(wl["focal"])), float(np.float32(wl["focal"])), W / 2, H / 2)
+            all_forms = {"fp32": opts32, **form_opts}
+            err = fp64_error_leg(M, gm, blob, P0, img, K, K4, pxs[0], all_forms, prop_blob)
+        except Exception as e:  # the error report must never hide the GPU line
+            err = {"failed": f"{type(e).__name__}: {e}"}
+    for name, f in forms.items():
+        if err and name in err:
+            f["err_vs_fp64"] = err[name]
 
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
@@ -697,17 +844,15 @@ def run_ours(args):
     extra = {}
     if world == 1 and args.sweeps:
         try:
-            extra["sweeps"] = run_sweeps(M, prec)
+            extra["sweeps"] = run_sweeps(M, "bf16" if "bf16" in tc else "fp32")
         except Exception as e:  # an extra workload must never hide the main line
             extra["sweeps"] = {"failed": f"{type(e).__name__}: {e}"}
-    if world == 1 and not args.no_extra:
+    if world == 1 and not args.no_extra and "bf16" in tc:
         for name, fn in (
-                ("coarse_to_fine", lambda: run_coarse_to_fine(M, img, K, seed, prec)),
-                ("ablation", lambda: run_ablation(M, img, K, seed, prec)),
-                ("proposal_fp8", lambda: run_proposal_fp8(M, gm, img, K, seed, args.steps,
-                                                          args.warmup, wl)),
-                ("batched_queries", lambda: run_batched(M, seed, W, H, wl["focal"],
-                                                        gm.proposal_get()))):
+                ("equal_pose_error", lambda: run_pose_error(M)),
+                ("coarse_to_fine", lambda: run_coarse_to_fine(M, img, K, seed, "bf16")),
+                ("ablation", lambda: run_ablation(M, img, K, seed, "bf16")),
+                ("batched_queries", lambda: run_batched(M, seed, W, H, wl["focal"], prop_blob))):
             try:
                 extra[name] = fn()
             except Exception as e:  # an extra workload must never hide the main line
@@ -715,18 +860,19 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": sum(ms) / len(ms), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None,
-        "dtype": {"fp32": "f32", "bf16": "bf16", "fp8": "fp8"}[prec], "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": wl["workload"], "particles": N, "pixels": Bpx,
                    "image": f"{W}x{H}", "samples_per_ray": f"{wl['n_coarse']}+{wl['n_fine']}",
-                   "mlp_precision": prec, "l2": "flushed (256 MB write) between timed steps",
+                   "mlp_precision": "fp32 (plain form, the paper's precision)",
+                   "l2": "flushed (256 MB write) between timed steps",
                    "step": "update + resample + predict + position spread",
                    "parallelism": f"replicas x{world} (one query per GPU)"},
         "update_ms": sum(ms) / len(ms),
         "phases_ms_per_step": {k: v / args.steps for k, v in phases.items()},
-        "fp32_form": fp32,
-        "speedup_vs_fp32_form": (fp32["ms_per_step"] / (sum(ms) / len(ms))) if fp32 else 1.0,
+        "err_vs_fp64": err.get("fp32") if isinstance(err, dict) else None,
+        "err_sample": err.get("sample") if isinstance(err, dict) else None,
         "roofline": roof,
+        "forms": forms,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": bi,
                 "d2h_bytes_per_step": bo, "ms_per_step": 1e3 * e2e_t / args.steps},
@@ -746,10 +892,10 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--precision", choices=("auto", "fp32", "bf16", "fp8"), default="auto")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true",
-                    help="skip the coarse-to-fine, proposal and batched-query workloads")
+                    help="skip the proposal, pose-error, coarse-to-fine, ablation and "
+                         "batched-query workloads")
     ap.add_argument("--sweeps", action="store_true",
                     help="add the tau and initial-particle-count sweeps on the room map")
     args = ap.parse_args()

@@ -294,9 +294,9 @@ typedef struct {
  * stay on the device: with use_graph != 0 the run is captured into a CUDA
  * graph on the map's own stream (ordered after earlier work on `stream` and
  * before later work on it) and kept; later calls with the same shapes and
- * pointers relaunch it.  opts->precision must be a tensor-core form
- * (MCL_PREC_BF16 or MCL_PREC_FP8); opts->use_proposal selects the learned
- * sampler.  The map must hold the largest iteration: n_queries * max(max_q
+ * pointers relaunch it.  opts->precision selects the NeRF MLP's form (the
+ * plain FP32 form or a tensor-core form); opts->use_proposal selects the
+ * learned sampler.  The map must hold the largest iteration: n_queries * max(max_q
  * h_n0[q] * n_pixels[0], max_s min(n_cap[s], stride) * n_pixels[s]) <=
  * max_rays, and n_queries * stride <= max_particles. */
 int mcl_localize(mcl_map* map, int n_queries, float* d_particles, int stride,
@@ -395,6 +395,19 @@ int mcl_proposal_train(mcl_map* map, const float* d_poses, int n_poses,
  * mcl_localize runs it once per precision before its first graph capture. */
 int mcl_autotune(mcl_map* map, int precision, long long rows, int* chosen, float* ms,
                  void* stream);
+
+/* Failure detection test hook (no counterpart in the paper).  The next
+ * n_launches launches of the tensor-core NeRF MLP on this map (any entry
+ * point that runs it) use the untuned single-CTA kernel of their precision
+ * with its weight stream held back and every bounded wait of the kernel
+ * limited to wait_ms: the wait for the first weight block runs out, the
+ * kernel's warps stop, release their tensor memory and exit, and the map's
+ * status word records MCL_ERR_TIMEOUT (mcl_read_status).  The launching call
+ * itself returns MCL_OK (the device sees the failure after the call has
+ * returned); outputs of the stalled launches are undefined.  Later launches
+ * run normally.  No GPU fault, trap or endless wait is involved.
+ * 0 <= n_launches; 0.01 <= wait_ms <= 2000. */
+int mcl_inject_weight_stall(mcl_map* map, int n_launches, double wait_ms);
 
 /* Pin the MLP kernel variant of a precision (see MCL_MLP_VARIANTS). */
 int mcl_set_mlp_variant(mcl_map* map, int precision, int variant);

@@ -150,6 +150,7 @@ def lib():
             L.mcl_autotune.argtypes = [vp, i32, C.c_longlong, C.POINTER(C.c_int),
                                        C.POINTER(C.c_float), vp]
             L.mcl_set_mlp_variant.argtypes = [vp, i32, i32]
+            L.mcl_inject_weight_stall.argtypes = [vp, i32, f64]
             L.mcl_last_error.restype = C.c_char_p
             L.mcl_last_error.argtypes = []
             _lib = L
@@ -440,6 +441,13 @@ class Map:
     def set_mlp_variant(self, precision: str, variant: int):
         _check(lib().mcl_set_mlp_variant(self.handle, _PREC[precision], int(variant)))
 
+    def inject_weight_stall(self, n_launches: int, wait_ms: float):
+        """Failure-detection test hook (mcl_inject_weight_stall): the next
+        n_launches tensor-core MLP launches hold their weight stream, so their
+        bounded waits run out after wait_ms and the status word records
+        MCL_ERR_TIMEOUT."""
+        _check(lib().mcl_inject_weight_stall(self.handle, int(n_launches), float(wait_ms)))
+
     def read_status(self):
         n = C.c_int(0)
         rc = lib().mcl_read_status(self.handle, C.byref(n), _stream())
@@ -525,7 +533,7 @@ EXPORTED = ("mcl_init_map", "mcl_destroy_map", "mcl_update", "mcl_render", "mcl_
             "mcl_proposal_set", "mcl_proposal_get", "mcl_render_histogram",
             "mcl_proposal_loss_grad", "mcl_proposal_train", "mcl_proposal_query", "mcl_autotune",
             "mcl_predict_odom",
-            "mcl_set_mlp_variant")
+            "mcl_set_mlp_variant", "mcl_inject_weight_stall")
 
 # Kernel variants of the tensor-core MLP (include/mcl.h, MCL_MLP_VARIANTS):
 # (precision, epilogue warps per tile, staggered tiles)

@@ -58,13 +58,26 @@ def _compile(src: str, verbose_ptxas: bool) -> str:
     return obj
 
 
+def _obj_current(src: str) -> bool:
+    """The object of src is newer than src, every header and this file."""
+    obj = os.path.join(OUT_DIR, os.path.basename(src).replace(".cu", ".o"))
+    if not os.path.exists(obj):
+        return False
+    t = os.path.getmtime(obj)
+    heads = sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) + [
+        os.path.join(INCLUDE, "mcl.h"), os.path.abspath(__file__)]
+    return all(os.path.getmtime(p) <= t for p in [src] + heads)
+
+
 def build(force: bool = False, verbose_ptxas: bool = False) -> str:
     if not force and up_to_date():
         return LIB
     os.makedirs(OUT_DIR, exist_ok=True)
     srcs = _sources()
-    with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
-        objs = list(ex.map(lambda s: _compile(s, verbose_ptxas), srcs))
+    todo = [s for s in srcs if force or verbose_ptxas or not _obj_current(s)]
+    with cf.ThreadPoolExecutor(max_workers=max(1, min(8, len(todo)))) as ex:
+        list(ex.map(lambda s: _compile(s, verbose_ptxas), todo))
+    objs = [os.path.join(OUT_DIR, os.path.basename(s).replace(".cu", ".o")) for s in srcs]
     tmp = LIB + f".tmp{os.getpid()}"
     cmd = [nvcc(), *ARCH, "-shared", "-cudart=static", "-o", tmp, *objs]
     r = subprocess.run(cmd, capture_output=True, text=True)

@@ -596,8 +596,9 @@ extern "C" int mcl_localize(mcl_map* m, int nq, float* d_particles, int stride, 
     if (!m || !d_particles || !h_n0 || !h_images || !K || !sch || !o || !d_log || !d_final_n)
         return fail(MCL_ERR_ARG, "mcl_localize: NULL argument");
     if ((rc = check_opts(o))) return rc;
-    if (o->precision == MCL_PREC_FP32 || !mlp_tc_available(m, o->precision))
-        return fail(MCL_ERR_UNSUPPORTED, "mcl_localize: needs a tensor-core form (BF16 or FP8)");
+    if (o->precision != MCL_PREC_FP32 && !mlp_tc_available(m, o->precision))
+        return fail(MCL_ERR_UNSUPPORTED, "mcl_localize: precision %d is not available on this device",
+                    o->precision);
     if (nq < 1 || nq > m->cfg.max_queries) return fail(MCL_ERR_ARG, "mcl_localize: n_queries %d", nq);
     if (stride < 1 || (long)nq * stride > m->cfg.max_particles)
         return fail(MCL_ERR_ARG, "mcl_localize: n_queries * stride > max_particles");
@@ -640,7 +641,7 @@ extern "C" int mcl_localize(mcl_map* m, int nq, float* d_particles, int stride, 
     cudaStream_t caller = (cudaStream_t)stream;
     // the first graph-mode run of a precision picks the MLP kernel variant
     // (synchronous; never inside a capture)
-    if (use_graph && !mlp_tc_tuned(m, o->precision)) {
+    if (use_graph && o->precision != MCL_PREC_FP32 && !mlp_tc_tuned(m, o->precision)) {
         const int S = std::min(64, m->cfg.max_samples);
         const long long rows = std::min((long long)max_rays_run * S, (long long)m->cfg.max_rays * S);
         if (rows >= 256 && (rc = mlp_tc_autotune(m, o->precision, rows, nullptr, nullptr, caller)))
@@ -707,6 +708,14 @@ extern "C" int mcl_autotune(mcl_map* m, int precision, long long rows, int* chos
     if (precision != MCL_PREC_BF16 && precision != MCL_PREC_FP8)
         return fail(MCL_ERR_ARG, "mcl_autotune: precision %d has no kernel variants", precision);
     return mlp_tc_autotune(m, precision, rows, chosen, ms, (cudaStream_t)stream);
+}
+
+extern "C" int mcl_inject_weight_stall(mcl_map* m, int n_launches, double wait_ms) {
+    g_err[0] = 0;
+    if (!m) return fail(MCL_ERR_ARG, "mcl_inject_weight_stall: NULL map");
+    if (n_launches < 0 || !(wait_ms >= 0.01 && wait_ms <= 2000.0))
+        return fail(MCL_ERR_ARG, "mcl_inject_weight_stall: n_launches >= 0, 0.01 <= wait_ms <= 2000");
+    return mlp_tc_hold_weights(m, n_launches, (unsigned long long)(wait_ms * 1e6));
 }
 
 extern "C" int mcl_set_mlp_variant(mcl_map* m, int precision, int variant) {

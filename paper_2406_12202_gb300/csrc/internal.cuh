@@ -158,8 +158,9 @@ cudaError_t launch_weights(const float* e_ray, int N, int B, const mcl_opts& o, 
                            Status* status, cudaStream_t s);
 
 // mlp_fp32.cu: (sigma_raw, rgb) for rows r = ray*S + k of the pass.
+// rows_dev (optional): device-side row count (n_rays * S is the bound).
 cudaError_t mlp_fp32(mcl_map* m, const Ray* rays, const float* gd, const float* z, int S,
-                     int n_rays, float4* out, cudaStream_t s);
+                     int n_rays, float4* out, cudaStream_t s, const int* rows_dev = nullptr);
 
 // mlp_tc.cu
 int mlp_tc_prepare(mcl_map* m, const float* host_blob);
@@ -169,6 +170,7 @@ int mlp_tc_set_variant(mcl_map* m, int precision, int variant);
 int mlp_tc_autotune(mcl_map* m, int precision, long long rows, int* chosen, float* ms_out,
                     cudaStream_t s);
 bool mlp_tc_tuned(const mcl_map* m, int precision);
+int mlp_tc_hold_weights(mcl_map* m, int n_launches, unsigned long long wait_ns);
 cudaError_t mlp_tc_ray_bias(mcl_map* m, const float* gd, int n_rays, const int* n_rays_dev,
                             cudaStream_t s);
 // rows_dev (optional): device-side row count (rows = n_rays * S is the bound).

@@ -258,6 +258,12 @@ int enqueue_localize(mcl_map* m, int nq, float* P_user, int stride, const mcl_in
     float* const za = prop ? m->zf : m->zc;
     float* const zb = prop ? m->zc : m->zf;
     const int tb = 128;
+    // the NeRF MLP of the precision, rows from the plan in device memory
+    const bool fp32 = o.precision == MCL_PREC_FP32;
+    auto mlp = [&](const float* z, int S, const int* rows_dev, float4* dst) -> cudaError_t {
+        if (fp32) return mlp_fp32(m, m->rays, m->gd, z, S, max_rays_run, dst, s, rows_dev);
+        return mlp_tc(m, o.precision, m->rays, m->gd, z, S, max_rays_run, rows_dev, dst, s);
+    };
     float* Pc = P_user;
     float* Pn = L.P_next;
     note_launch();
@@ -269,8 +275,8 @@ int enqueue_localize(mcl_map* m, int nq, float* P_user, int stride, const mcl_in
         k_raygen_b<<<(max_rays_run + tb - 1) / tb, tb, 0, s>>>(
             L.plan, nq, Pc, stride, L.pix, K.fx, K.fy, K.cx, K.cy, np, o.near_z, o.far_z,
             prop ? 0 : o.jitter, o.seed, t, max_rays_run, m->rays, m->gd, m->zc);
-        if ((rc = cuda_check(mlp_tc_ray_bias(m, m->gd, max_rays_run, &L.plan->total_rays, s),
-                             "loop ray bias")))
+        if (!fp32 && (rc = cuda_check(mlp_tc_ray_bias(m, m->gd, max_rays_run, &L.plan->total_rays, s),
+                                      "loop ray bias")))
             return rc;
         if (prop) {
             if ((rc = cuda_check(launch_prop_infer(m, o.precision, m->rays, m->zc, np, max_rays_run,
@@ -281,18 +287,14 @@ int enqueue_localize(mcl_map* m, int nq, float* P_user, int stride, const mcl_in
                                  "loop proposal sampling")))
                 return rc;
         }
-        if ((rc = cuda_check(mlp_tc(m, o.precision, m->rays, m->gd, za, nc, max_rays_run,
-                                    &L.plan->rows_c, m->out_c, s),
-                             "loop mlp (coarse)")))
+        if ((rc = cuda_check(mlp(za, nc, &L.plan->rows_c, m->out_c), "loop mlp (coarse)")))
             return rc;
         if (nf > 0) {
             if ((rc = cuda_check(launch_coarse_to_fine(m->rays, max_rays_run, &L.plan->total_rays,
                                                        za, nc, m->out_c, nf, zb, s),
                                  "loop importance sampling")))
                 return rc;
-            if ((rc = cuda_check(mlp_tc(m, o.precision, m->rays, m->gd, zb, nf, max_rays_run,
-                                        &L.plan->rows_f, m->out_f, s),
-                                 "loop mlp (fine)")))
+            if ((rc = cuda_check(mlp(zb, nf, &L.plan->rows_f, m->out_f), "loop mlp (fine)")))
                 return rc;
         }
         note_launch(5);

@@ -12,10 +12,18 @@ namespace mcl {
 // ray: [x, sin(2^k x), cos(2^k x)]_{k<10}, padded with a zero to 64.  x and
 // the arguments 2^k x are formed in FP64 and reduced modulo 2 pi there, so the
 // sines carry FP32 error rather than FP32 error of x amplified by 2^9.
+// rows_dev (optional): rows of the pass in device memory; rows at or beyond
+// it are skipped (every kernel of this file).
+__device__ __forceinline__ int rows_in_chunk(int n, long r0, const int* rows_dev) {
+    if (!rows_dev) return n;
+    const long left = (long)*rows_dev - r0;
+    return left < 0 ? 0 : (left < n ? (int)left : n);
+}
+
 __global__ void k_pe_xyz(const Ray* __restrict__ rays, const float* __restrict__ z, int S, long r0,
-                         int n, float* __restrict__ gx) {
+                         int n, const int* __restrict__ rows_dev, float* __restrict__ gx) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n) return;
+    if (t >= rows_in_chunk(n, r0, rows_dev)) return;
     const long row = r0 + t;
     const Ray ray = rays[row / S];
     const double zz = (double)z[row];
@@ -50,12 +58,15 @@ __global__ __launch_bounds__(256, 2) void k_sgemm(const float* __restrict__ A1, 
                                                long a2_off, int a2_div,
                                                const float* __restrict__ W,
                                                const float* __restrict__ bias,
-                                               float* __restrict__ C, int ldc, int M) {
+                                               float* __restrict__ C, int ldc, int M,
+                                               const int* __restrict__ rows_dev, long r0) {
     constexpr int BM = 128, BN = 128, BK = 16, PAD = 4;
     __shared__ __align__(16) float As[BK][BM + PAD];
     __shared__ __align__(16) float Bs[BK][BN + PAD];
     const int tid = threadIdx.x;
     const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+    M = rows_in_chunk(M, r0, rows_dev);
+    if (m0 >= M) return;
     const int K = K1 + K2;
     const int lr = tid >> 2, lk = (tid & 3) << 2;
     const int tx = tid & 15, ty = tid >> 4;
@@ -141,10 +152,11 @@ __global__ __launch_bounds__(256, 2) void k_sgemm(const float* __restrict__ A1, 
 
 // sigma_raw = w_sigma . h + b_sigma, one warp per row.
 __global__ void k_sigma_head(const float* __restrict__ h, int ldh, const float* __restrict__ w,
-                             const float* __restrict__ b, int n, float4* __restrict__ out) {
+                             const float* __restrict__ b, int n, const int* __restrict__ rows_dev,
+                             long r0, float4* __restrict__ out) {
     const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    if (row >= n) return;
+    if (row >= rows_in_chunk(n, r0, rows_dev)) return;
     const float* x = h + (size_t)row * ldh;
     float s = 0.f;
     for (int k = lane; k < kWidth; k += 32) s = fmaf(w[k], x[k], s);
@@ -154,10 +166,11 @@ __global__ void k_sigma_head(const float* __restrict__ h, int ldh, const float* 
 
 // rgb = sigmoid(W_out h + b_out), one warp per row.
 __global__ void k_rgb_head(const float* __restrict__ h, int ldh, const float* __restrict__ W,
-                           const float* __restrict__ b, int n, float4* __restrict__ out) {
+                           const float* __restrict__ b, int n, const int* __restrict__ rows_dev,
+                           long r0, float4* __restrict__ out) {
     const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    if (row >= n) return;
+    if (row >= rows_in_chunk(n, r0, rows_dev)) return;
     const float* x = h + (size_t)row * ldh;
     float s[3] = {0.f, 0.f, 0.f};
     for (int k = lane; k < kRgbW; k += 32) {
@@ -177,38 +190,40 @@ __global__ void k_rgb_head(const float* __restrict__ h, int ldh, const float* __
 
 static cudaError_t gemm(const float* A1, int lda1, int K1, const float* A2, int lda2, int K2,
                         long a2_off, int a2_div, const LayerF32& L, float* C, int ldc, int M,
-                        bool relu, cudaStream_t s) {
+                        bool relu, const int* rows_dev, long r0, cudaStream_t s) {
     dim3 grid((M + 127) / 128, L.n / 128);
     note_launch();
     if (relu)
         k_sgemm<true><<<grid, 256, 0, s>>>(A1, lda1, K1, A2, lda2, K2, a2_off, a2_div, L.W, L.b, C,
-                                           ldc, M);
+                                           ldc, M, rows_dev, r0);
     else
         k_sgemm<false><<<grid, 256, 0, s>>>(A1, lda1, K1, A2, lda2, K2, a2_off, a2_div, L.W, L.b, C,
-                                            ldc, M);
+                                            ldc, M, rows_dev, r0);
     return cudaGetLastError();
 }
 
 cudaError_t mlp_fp32(mcl_map* m, const Ray* rays, const float* gd, const float* z, int S,
-                     int n_rays, float4* out, cudaStream_t s) {
+                     int n_rays, float4* out, cudaStream_t s, const int* rows_dev) {
     const long rows = (long)n_rays * S;
     cudaError_t e = cudaSuccess;
     for (long r0 = 0; r0 < rows; r0 += m->chunk_rows) {
         const int n = (int)((rows - r0) < m->chunk_rows ? (rows - r0) : m->chunk_rows);
         note_launch();
-        k_pe_xyz<<<(n + 127) / 128, 128, 0, s>>>(rays, z, S, r0, n, m->gxbuf);
+        k_pe_xyz<<<(n + 127) / 128, 128, 0, s>>>(rays, z, S, r0, n, rows_dev, m->gxbuf);
         float* a = m->act0;
         float* b = m->act1;
         // trunk layer 1 reads gamma(x)
-        if ((e = gemm(m->gxbuf, kGxPad, kGxPad, nullptr, 0, 0, 0, 1, m->L[0], a, kWidth, n, true, s)))
+        if ((e = gemm(m->gxbuf, kGxPad, kGxPad, nullptr, 0, 0, 0, 1, m->L[0], a, kWidth, n, true,
+                      rows_dev, r0, s)))
             return e;
         for (int l = 1; l < kDepth; ++l) {
             if (l == kSkip) {
                 // layer skip+1 reads [h_skip, gamma(x)]
                 e = gemm(a, kWidth, kWidth, m->gxbuf, kGxPad, kGxPad, 0, 1, m->L[l], b, kWidth, n,
-                         true, s);
+                         true, rows_dev, r0, s);
             } else {
-                e = gemm(a, kWidth, kWidth, nullptr, 0, 0, 0, 1, m->L[l], b, kWidth, n, true, s);
+                e = gemm(a, kWidth, kWidth, nullptr, 0, 0, 0, 1, m->L[l], b, kWidth, n, true,
+                         rows_dev, r0, s);
             }
             if (e) return e;
             float* t = a; a = b; b = t;
@@ -216,15 +231,17 @@ cudaError_t mlp_fp32(mcl_map* m, const Ray* rays, const float* gd, const float* 
         // a = trunk output
         note_launch();
         k_sigma_head<<<(n * 32 + 255) / 256, 256, 0, s>>>(a, kWidth, m->L[8].W, m->L[8].b, n,
-                                                          out + r0);
-        if ((e = gemm(a, kWidth, kWidth, nullptr, 0, 0, 0, 1, m->L[9], b, kWidth, n, false, s)))
+                                                          rows_dev, r0, out + r0);
+        if ((e = gemm(a, kWidth, kWidth, nullptr, 0, 0, 0, 1, m->L[9], b, kWidth, n, false,
+                      rows_dev, r0, s)))
             return e;
         // rgb hidden reads [feature, gamma(d)], gamma(d) row = ray = (r0 + r) / S
-        if ((e = gemm(b, kWidth, kWidth, gd, kGdPad, kGdPad, r0, S, m->L[10], a, kWidth, n, true, s)))
+        if ((e = gemm(b, kWidth, kWidth, gd, kGdPad, kGdPad, r0, S, m->L[10], a, kWidth, n, true,
+                      rows_dev, r0, s)))
             return e;
         note_launch();
         k_rgb_head<<<(n * 32 + 255) / 256, 256, 0, s>>>(a, kWidth, m->L[11].W, m->L[11].b, n,
-                                                        out + r0);
+                                                        rows_dev, r0, out + r0);
         if ((e = cudaGetLastError())) return e;
     }
     return cudaSuccess;

@@ -131,6 +131,9 @@ struct Params {
     float4* out;
     int* abort_flag;        // per-launch: set on a timed-out wait
     int* status_code;       // map status word
+    unsigned long long wait_ns;  // limit of the bounded waits of k_mlp_tc
+    int hold_weights;       // failure-injection hook (k_mlp_tc): the weight
+                            // stream issues no copies, so the waits expire
 };
 
 struct __align__(8) Bars {
@@ -348,7 +351,7 @@ __device__ __forceinline__ void epilogue_warps(const Params& p, int warp, int wa
         float sigma = 0.0f;
         for (int l = 0; l < kLayers && ok; ++l, ++tl) {
             if (!(PAIR ? mbar_wait_cluster<true>(bar_acc, acc_ph, abort_flag)
-                       : mbar_wait_sleep(bar_acc, acc_ph, abort_flag))) {
+                       : mbar_wait_sleep(bar_acc, acc_ph, abort_flag, p.wait_ns))) {
                 ok = false;
                 break;
             }
@@ -480,14 +483,16 @@ __global__ void __launch_bounds__(Variant<F8, EPIW, STAG>::kThreads, 1)
 
     if (warp == 0) {
         // ------------------------------------------------ TMA producer
-        if (lane == 0) {
+        // (hold_weights: issues nothing, so that the gate's first wait runs
+        // out; a failure-detection test hook)
+        if (lane == 0 && !p.hold_weights) {
             uint32_t g = 0;
             bool ok = true;
             for (long long pr = blockIdx.x; pr < n_pairs && ok; pr += gridDim.x) {
                 for (int b = 0; b < Fm::kBlocks; ++b, ++g) {
                     const uint32_t st = g % kStages, ph = (g / kStages) & 1u;
                     TC_TRACE(0, g);
-                    if (!mbar_wait(smem_u32(&bars.empty[st]), ph ^ 1u, abort_flag)) {
+                    if (!mbar_wait(smem_u32(&bars.empty[st]), ph ^ 1u, abort_flag, p.wait_ns)) {
                         ok = false;
                         break;
                     }
@@ -627,14 +632,15 @@ __global__ void __launch_bounds__(Variant<F8, EPIW, STAG>::kThreads, 1)
         bool ok = true;
         int tl = 0;
         auto wait_ready = [&](int s) -> bool {
-            const bool r = mbar_wait(smem_u32(&bars.a_ready[s]), rdy_ph[s], abort_flag);
+            const bool r = mbar_wait(smem_u32(&bars.a_ready[s]), rdy_ph[s], abort_flag, p.wait_ns);
             rdy_ph[s] ^= 1u;
             if (lane == 0) TC_TRACE(3 + s, tl);
             return r;
         };
         auto wait_block = [&](uint32_t gi) -> bool {
             if (lane == 0) TC_TRACE(15, gi);
-            const bool r = mbar_wait(smem_u32(&bars.full[gi % kStages]), (gi / kStages) & 1u, abort_flag);
+            const bool r = mbar_wait(smem_u32(&bars.full[gi % kStages]), (gi / kStages) & 1u, abort_flag,
+                                     p.wait_ns);
             if (lane == 0) TC_TRACE(13, gi);
             return r;
         };
@@ -1542,6 +1548,8 @@ struct TcState {
     int n_sm = 0;
     int max_pairs = 0;         // co-resident CTA pairs of the pair kernels
     int variant[3] = {-1, kDefaultVariant[1], kDefaultVariant[2]};   // by precision
+    int hold_launches = 0;                 // failure injection: launches left
+    unsigned long long hold_wait_ns = 0;   // their wait limit
     float tuned_ms[kNumVariants] = {};                                // last autotune
     bool tuned[3] = {false, false, false};
 };
@@ -1899,11 +1907,23 @@ static cudaError_t mlp_tc_variant(mcl_map* m, int precision, int variant, const 
     p.out = out;
     p.abort_flag = st->abort_flag;
     p.status_code = &m->status->code;
+    p.wait_ns = kWaitNs;
+    p.hold_weights = 0;
+    int vsel = vi;
+    if (st->hold_launches > 0) {
+        // failure injection: the untuned single-CTA kernel with its weight
+        // stream held and a short wait limit
+        --st->hold_launches;
+        p.hold_weights = 1;
+        p.wait_ns = st->hold_wait_ns;
+        vsel = kDefaultVariant[precision];
+        p.wblocks = precision == MCL_PREC_FP8 ? st->fp8.wblocks : st->bf16.wblocks;
+    }
     cudaError_t e = cudaMemsetAsync(st->abort_flag, 0, sizeof(int), s);
     if (e) return e;
     // persistent grid: one CTA per SM at most, one per work unit (a pair of
     // tiles, a single tile for the pipelined kernel, 512 rows for a CTA pair)
-    const TcVariant& v = kVariants[vi];
+    const TcVariant& v = kVariants[vsel];
     long long grid;
     if (v.cluster == 2) {
         const long long units = (p.M + 511) / 512;
@@ -2010,6 +2030,14 @@ int mlp_tc_autotune(mcl_map* m, int precision, long long rows, int* chosen, floa
     st->variant[precision] = best;
     st->tuned[precision] = true;
     if (chosen) *chosen = best;
+    return MCL_OK;
+}
+
+int mlp_tc_hold_weights(mcl_map* m, int n_launches, unsigned long long wait_ns) {
+    TcState* st = (TcState*)m->tc_aux;
+    if (!st) return fail(MCL_ERR_UNSUPPORTED, "no tensor-core MLP on this map");
+    st->hold_launches = n_launches;
+    st->hold_wait_ns = wait_ns;
     return MCL_OK;
 }
 

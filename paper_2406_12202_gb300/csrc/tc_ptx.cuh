@@ -8,9 +8,10 @@
 namespace mcl {
 namespace tc {
 
-// Bounded waits: a wait that has not completed after kWaitNs of GPU time
-// records MCL_ERR_TIMEOUT in *err and gives up; every waiter also gives up
-// as soon as another thread has recorded an error.
+// Bounded waits: a wait that has not completed after limit_ns of GPU time
+// (kWaitNs unless the caller passes a shorter limit) records MCL_ERR_TIMEOUT
+// in *err and gives up; every waiter also gives up as soon as another thread
+// has recorded an error.
 constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -59,7 +60,8 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
 // false if it does not within kWaitNs (recording MCL_ERR_TIMEOUT in *err),
 // or as soon as *err holds an error recorded by another thread.  err may be
 // NULL (drain waits at exit: time limit only).
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* err) {
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* err,
+                                          unsigned long long limit_ns = kWaitNs) {
 #pragma unroll 1
     for (int i = 0; i < 32; ++i)
         if (mbar_try_wait(bar, parity)) return true;
@@ -69,7 +71,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
         if (mbar_try_wait(bar, parity)) return true;
         if ((it & 63u) == 0u) {
             if (err && *err != 0) return false;
-            if (globaltimer() - t0 > kWaitNs) {
+            if (globaltimer() - t0 > limit_ns) {
                 if (err) atomicCAS((int*)err, 0, -4 /* MCL_ERR_TIMEOUT */);
                 return false;
             }
@@ -81,7 +83,8 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
 // epilogue warps during a layer's MMAs): after a short spin they back off
 // with __nanosleep so that their polling does not compete with the MMA
 // issue and TMA threads.
-__device__ __forceinline__ bool mbar_wait_sleep(uint32_t bar, uint32_t parity, volatile int* err) {
+__device__ __forceinline__ bool mbar_wait_sleep(uint32_t bar, uint32_t parity, volatile int* err,
+                                                unsigned long long limit_ns = kWaitNs) {
 #pragma unroll 1
     for (int i = 0; i < 8; ++i)
         if (mbar_try_wait(bar, parity)) return true;
@@ -92,7 +95,7 @@ __device__ __forceinline__ bool mbar_wait_sleep(uint32_t bar, uint32_t parity, v
         if (mbar_try_wait(bar, parity)) return true;
         if ((it & 15u) == 0u) {
             if (err && *err != 0) return false;
-            if (globaltimer() - t0 > kWaitNs) {
+            if (globaltimer() - t0 > limit_ns) {
                 if (err) atomicCAS((int*)err, 0, -4 /* MCL_ERR_TIMEOUT */);
                 return false;
             }
@@ -158,7 +161,8 @@ __device__ __forceinline__ bool mbar_try_wait_cluster(uint32_t bar, uint32_t par
 }
 
 template <bool kSleep>
-__device__ __forceinline__ bool mbar_wait_cluster(uint32_t bar, uint32_t parity, volatile int* err) {
+__device__ __forceinline__ bool mbar_wait_cluster(uint32_t bar, uint32_t parity, volatile int* err,
+                                                  unsigned long long limit_ns = kWaitNs) {
 #pragma unroll 1
     for (int i = 0; i < (kSleep ? 8 : 32); ++i)
         if (mbar_try_wait_cluster(bar, parity)) return true;
@@ -169,7 +173,7 @@ __device__ __forceinline__ bool mbar_wait_cluster(uint32_t bar, uint32_t parity,
         if (mbar_try_wait_cluster(bar, parity)) return true;
         if ((it & (kSleep ? 15u : 63u)) == 0u) {
             if (err && *err != 0) return false;
-            if (globaltimer() - t0 > kWaitNs) {
+            if (globaltimer() - t0 > limit_ns) {
                 if (err) atomicCAS((int*)err, 0, -4 /* MCL_ERR_TIMEOUT */);
                 return false;
             }

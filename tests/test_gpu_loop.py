@@ -154,3 +154,65 @@ def test_gt_particle_pulls_the_estimate(M, gm):
     log, fin = gm.localize(parts, [N], [img], K, sch, opts, use_graph=False)
     r = M.Map.decode_log(log, 1, 3)[0]
     assert np.linalg.norm(np.array(r[0]["est"][:3]) - gt[[3, 7, 11]]) < 1e-3
+
+
+def test_loop_log_replays_through_the_oracle(M, gm):
+    """Every record of a 2-query, 8-iteration run against the FP64 oracle's
+    statement of the refinement statistic and the schedule (Sec. III-C):
+    the particles at the start of iteration t (a run of t iterations) are
+    weighted through mcl_update with the iteration's pixel set, and
+    orc_loop_statistics of those weights must give the record's spread
+    (1e-9 relative), pose estimate and survivor count (exactly), and
+    orc_loop_schedule the next record's stage and particle count (exactly)."""
+    import torch
+    Q, stride, iters = 2, 700, 8
+    n0 = [700, 450]
+    parts = torch.full((Q, stride, 12), float("nan"), device="cuda")
+    imgs = []
+    for q in range(Q):
+        P, gt = _query(M, 70 + q, n0[q], with_gt=False)
+        parts[q, :n0[q]] = P
+        img, K = _observation(M, gm, gt)
+        imgs.append(img)
+    levels, pixels, caps = [0, 1, 2], [16, 32, 64], [700, 350, 175]
+    refine, iter_caps, n_min = [0.3, 0.05, 0.0], [3, 3, 10], 64
+    sch = M.schedule(levels, pixels, caps, n_min=n_min, iter_caps=iter_caps, refine=refine,
+                     iterations=iters)
+    seed = 321
+    opts = M.UpdateOptions(n_coarse=64, n_fine=128, precision="bf16", seed=seed)
+    full = parts.clone()
+    log, fin = gm.localize(full, n0, imgs, K, sch, opts, use_graph=False)
+    recs = M.Map.decode_log(log, Q, iters)
+    # particles at the start of each iteration
+    starts = [[parts[q, :n0[q]].clone() for q in range(Q)]]
+    for t in range(1, iters):
+        p = parts.clone()
+        _, f = gm.localize(p, n0, imgs, K, M.schedule(levels, pixels, caps, n_min=n_min,
+                                                      iter_caps=iter_caps, refine=refine,
+                                                      iterations=t), opts, use_graph=False)
+        starts.append([p[q, :int(f[q].item())].clone() for q in range(Q)])
+    for q in range(Q):
+        stage, it = 0, 0
+        for t in range(iters):
+            r = recs[q][t]
+            Pq = starts[t][q]
+            assert r["stage"] == stage and r["n_particles"] == Pq.shape[0]
+            B, lev = pixels[stage], levels[stage]
+            f = 4 >> lev
+            px = M.draw_pixels(W // f, H // f, B, seed, ctr(q, t, 0))
+            out = gm.update(Pq.contiguous(), imgs[q], K, lev, px, opts)
+            w = out["w"].cpu().numpy()
+            mask = out["mask"].cpu().numpy()
+            st = oracle.loop_statistics(Pq.cpu().numpy().astype(np.float64), w, mask)
+            assert r["spread"] == pytest.approx(st["spread"], rel=1e-9)
+            assert np.allclose(r["est"][:3], st["mean"], rtol=0, atol=1e-12)
+            assert r["est"][3] == pytest.approx(st["yaw"], abs=1e-12)
+            assert r["n_survivors"] == st["n_survivors"]
+            nxt = oracle.loop_schedule(stage, it, st["n_survivors"], st["spread"], refine,
+                                       iter_caps, caps, n_min, stride)
+            stage, it, n_next = nxt
+            if t + 1 < iters:
+                assert recs[q][t + 1]["stage"] == stage
+                assert recs[q][t + 1]["n_particles"] == n_next
+            else:
+                assert int(fin[q].item()) == n_next
