@@ -409,6 +409,19 @@ int mcl_autotune(mcl_map* map, int precision, long long rows, int* chosen, float
  * 0 <= n_launches; 0.01 <= wait_ms <= 2000. */
 int mcl_inject_weight_stall(mcl_map* map, int n_launches, double wait_ms);
 
+/* Fused ray epilogues of the tensor-core forms (on by default): when the
+ * pass shapes allow it (n_coarse -- or n_guided with the proposal -- and
+ * n_fine divide 128, and a ray's merged samples fit the kernel's staging
+ * buffer), the NeRF MLP kernel's epilogue draws the importance samples of
+ * the first pass and, in the last pass, merges the samples, composites them
+ * (Eq. 1), applies Eq. 5 / F and the photometric E (Eq. 6), so the fine
+ * pass's per-sample outputs never leave the chip.  The arithmetic is that of
+ * the separate kernels in another order (warp-shuffle scans instead of one
+ * thread walking a ray), so results agree to FP32 rounding.  enable = 0
+ * runs the separate kernels (mcl_update, mcl_render and mcl_localize on
+ * this map). */
+int mcl_set_fused_epilogue(mcl_map* map, int enable);
+
 /* Pin the MLP kernel variant of a precision (see MCL_MLP_VARIANTS). */
 int mcl_set_mlp_variant(mcl_map* map, int precision, int variant);
 

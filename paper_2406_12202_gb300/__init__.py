@@ -151,6 +151,7 @@ def lib():
                                        C.POINTER(C.c_float), vp]
             L.mcl_set_mlp_variant.argtypes = [vp, i32, i32]
             L.mcl_inject_weight_stall.argtypes = [vp, i32, f64]
+            L.mcl_set_fused_epilogue.argtypes = [vp, i32]
             L.mcl_last_error.restype = C.c_char_p
             L.mcl_last_error.argtypes = []
             _lib = L
@@ -438,6 +439,11 @@ class Map:
                                   _stream()))
         return ch.value, {i: float(ms[i]) for i in range(MLP_VARIANTS) if ms[i] >= 0}
 
+    def set_fused_epilogue(self, enable: bool):
+        """Fused ray epilogues of the tensor-core forms on / off
+        (mcl_set_fused_epilogue; on by default)."""
+        _check(lib().mcl_set_fused_epilogue(self.handle, int(bool(enable))))
+
     def set_mlp_variant(self, precision: str, variant: int):
         _check(lib().mcl_set_mlp_variant(self.handle, _PREC[precision], int(variant)))
 
@@ -533,7 +539,7 @@ EXPORTED = ("mcl_init_map", "mcl_destroy_map", "mcl_update", "mcl_render", "mcl_
             "mcl_proposal_set", "mcl_proposal_get", "mcl_render_histogram",
             "mcl_proposal_loss_grad", "mcl_proposal_train", "mcl_proposal_query", "mcl_autotune",
             "mcl_predict_odom",
-            "mcl_set_mlp_variant", "mcl_inject_weight_stall")
+            "mcl_set_mlp_variant", "mcl_inject_weight_stall", "mcl_set_fused_epilogue")
 
 # Kernel variants of the tensor-core MLP (include/mcl.h, MCL_MLP_VARIANTS):
 # (precision, epilogue warps per tile, staggered tiles)

@@ -100,7 +100,7 @@ static void free_map(mcl_map* m) {
     if (m->loop.stream) cudaStreamDestroy(m->loop.stream);
     if (m->loop.ev_in) cudaEventDestroy(m->loop.ev_in);
     if (m->loop.ev_out) cudaEventDestroy(m->loop.ev_out);
-    void* ptrs[] = {m->w32, m->rays, m->gd, m->zc, m->zf, m->out_c, m->out_f, m->e_ray,
+    void* ptrs[] = {m->w32, m->rays, m->gd, m->zc, m->zf, m->out_c, m->out_f, m->obs, m->e_ray,
                     m->logw64, m->cdf, m->status, m->act0, m->act1, m->gxbuf,
                     m->loop.plan, m->loop.qs, m->loop.n0, (void*)m->loop.imgs, m->loop.pix,
                     m->loop.P_next, m->loop.w, m->loop.mask, m->loop.idx, m->prop_w,
@@ -194,6 +194,7 @@ extern "C" int mcl_init_map(const float* host_weights, size_t n_floats, const mc
         {(void**)&m->zf, R * S * sizeof(float), "z fine"},
         {(void**)&m->out_c, R * S * sizeof(float4), "coarse outputs"},
         {(void**)&m->out_f, R * S * sizeof(float4), "fine outputs"},
+        {(void**)&m->obs, R * sizeof(float4), "observed colours"},
         {(void**)&m->e_ray, R * sizeof(float), "per-ray loss"},
         {(void**)&m->logw64, (size_t)cfg->max_particles * sizeof(double), "log weights"},
         {(void**)&m->cdf, (size_t)cfg->max_particles * sizeof(unsigned long long), "cdf"},
@@ -276,7 +277,8 @@ static int check_samples(const mcl_map* m, const mcl_opts* o) {
     return MCL_OK;
 }
 
-// The two sample sets the final composite merges (after render_passes).
+// The two sample sets the final composite merges (after render_passes);
+// fused: the tensor-core MLP's last pass has already composited them.
 struct Passes {
     const float* za;
     const float4* oa;
@@ -285,6 +287,19 @@ struct Passes {
     const float4* ob;
     int nb;
     int factor;
+    bool fused;
+};
+
+// Per-ray outputs of the final stage (composite, Eq. 5 / F, E), produced by
+// the fused epilogue of the tensor-core forms when the pass shapes allow it.
+struct FinalOut {
+    const float* image;   // observation [H, W, 3] (NULL: render only)
+    float* e_ray;         // E * F per ray (with image)
+    float* rgb;
+    float* E;
+    float* F;
+    float* z_trans;
+    float* z_opaque;
 };
 
 // Common front half of mcl_update, mcl_render and the training targets:
@@ -292,7 +307,7 @@ struct Passes {
 // hierarchical sampler) or proposal + guided + importance samples.
 static int render_passes(mcl_map* m, const float* d_poses, int N, const mcl_intrinsics* K,
                          int level, const int32_t* d_pixels, int B, const mcl_opts* o,
-                         Passes* out, cudaStream_t s) {
+                         Passes* out, cudaStream_t s, const FinalOut* fin = nullptr) {
     int rc;
     if ((rc = check_opts(o))) return rc;
     if (!d_poses || !K || !d_pixels) return fail(MCL_ERR_ARG, "NULL pose / intrinsics / pixel set");
@@ -313,25 +328,71 @@ static int render_passes(mcl_map* m, const float* d_poses, int N, const mcl_intr
         ro.n_coarse = o->n_proposal;
         ro.jitter = 0;
     }
+    // fused ray epilogues: the first NeRF pass (coarse or guided samples, nA
+    // per ray) draws the importance samples, the last composites
+    const int nA = prop ? o->n_guided : o->n_coarse;
+    const bool fused = fin && o->precision != MCL_PREC_FP32 && m->fuse_epilogue &&
+                       (o->n_fine > 0 ? mlp_tc_can_fuse(1, nA, 0) && mlp_tc_can_fuse(2, o->n_fine, nA)
+                                      : mlp_tc_can_fuse(2, nA, 0));
+    out->fused = fused;
+    FuseArgs fa1{}, fa2{};
+    if (fused) {
+        fa1.mode = 1;
+        fa1.nf_out = o->n_fine;
+        fa2.mode = 2;
+        fa2.alpha = o->alpha;
+        fa2.tau = o->tau;
+        fa2.use_rej = o->use_rejection;
+        fa2.obs = fin->image ? m->obs : nullptr;
+        fa2.e_ray = fin->e_ray;
+        fa2.rgb_out = fin->rgb;
+        fa2.E_out = fin->E;
+        fa2.F_out = fin->F;
+        fa2.zt_out = fin->z_trans;
+        fa2.zo_out = fin->z_opaque;
+    }
     {
         PhaseScope ph(m, MCL_PHASE_RAYGEN, s);
+        const bool with_obs = fused && fin->image;
         if ((rc = cuda_check(launch_raygen(d_poses, N, d_pixels, B, K->fx / f, K->fy / f,
-                                           K->cx / f, K->cy / f, ro, m->rays, m->gd, m->zc, s),
+                                           K->cx / f, K->cy / f, ro, m->rays, m->gd, m->zc, s,
+                                           with_obs ? fin->image : nullptr, K->width, K->height, f,
+                                           with_obs ? m->obs : nullptr),
                              "raygen")))
             return rc;
         if (o->precision != MCL_PREC_FP32 &&
             (rc = cuda_check(mlp_tc_ray_bias(m, m->gd, nr, nullptr, s), "per-ray bias")))
             return rc;
     }
-    auto mlp = [&](const float* z, int S, float4* dst) -> cudaError_t {
+    auto mlp = [&](const float* z, int S, float4* dst, const FuseArgs* fa) -> cudaError_t {
         if (o->precision == MCL_PREC_FP32) return mlp_fp32(m, m->rays, m->gd, z, S, nr, dst, s);
-        return mlp_tc(m, o->precision, m->rays, m->gd, z, S, nr, nullptr, dst, s);
+        return mlp_tc(m, o->precision, m->rays, m->gd, z, S, nr, nullptr, dst, s, fa);
     };
     out->factor = f;
     if (!prop) {
+        if (fused) {
+            // coarse pass: its epilogue draws the importance samples into zf
+            // (or, without them, composites); fine pass: final composite
+            fa1.z_out = m->zf;
+            fa2.z_first = m->zc;
+            fa2.out_first = m->out_c;
+            fa2.S1 = o->n_fine > 0 ? o->n_coarse : 0;
+            {
+                PhaseScope ph(m, MCL_PHASE_MLP_COARSE, s);
+                if ((rc = cuda_check(mlp(m->zc, o->n_coarse, m->out_c, o->n_fine > 0 ? &fa1 : &fa2),
+                                     "mlp (coarse, fused)")))
+                    return rc;
+            }
+            if (o->n_fine > 0) {
+                PhaseScope ph(m, MCL_PHASE_MLP_FINE, s);
+                if ((rc = cuda_check(mlp(m->zf, o->n_fine, m->out_f, &fa2), "mlp (fine, fused)")))
+                    return rc;
+            }
+            return MCL_OK;
+        }
         {
             PhaseScope ph(m, MCL_PHASE_MLP_COARSE, s);
-            if ((rc = cuda_check(mlp(m->zc, o->n_coarse, m->out_c), "mlp (coarse)"))) return rc;
+            if ((rc = cuda_check(mlp(m->zc, o->n_coarse, m->out_c, nullptr), "mlp (coarse)"))) return rc;
         }
         if (o->n_fine > 0) {
             {
@@ -342,9 +403,9 @@ static int render_passes(mcl_map* m, const float* d_poses, int N, const mcl_intr
                     return rc;
             }
             PhaseScope ph(m, MCL_PHASE_MLP_FINE, s);
-            if ((rc = cuda_check(mlp(m->zf, o->n_fine, m->out_f), "mlp (fine)"))) return rc;
+            if ((rc = cuda_check(mlp(m->zf, o->n_fine, m->out_f, nullptr), "mlp (fine)"))) return rc;
         }
-        *out = Passes{m->zc, m->out_c, o->n_coarse, m->zf, m->out_f, o->n_fine, f};
+        *out = Passes{m->zc, m->out_c, o->n_coarse, m->zf, m->out_f, o->n_fine, f, false};
         return MCL_OK;
     }
     // proposal: densities at the stratified samples (into out_f), guided
@@ -361,9 +422,29 @@ static int render_passes(mcl_map* m, const float* d_poses, int N, const mcl_intr
                              "proposal sampling")))
             return rc;
     }
+    if (fused) {
+        // guided pass: its epilogue draws the importance samples into zc (or,
+        // without them, composites); importance pass: final composite
+        fa1.z_out = m->zc;
+        fa2.z_first = m->zf;
+        fa2.out_first = m->out_c;
+        fa2.S1 = o->n_fine > 0 ? o->n_guided : 0;
+        {
+            PhaseScope ph(m, MCL_PHASE_MLP_COARSE, s);
+            if ((rc = cuda_check(mlp(m->zf, o->n_guided, m->out_c, o->n_fine > 0 ? &fa1 : &fa2),
+                                 "mlp (guided, fused)")))
+                return rc;
+        }
+        if (o->n_fine > 0) {
+            PhaseScope ph(m, MCL_PHASE_MLP_FINE, s);
+            if ((rc = cuda_check(mlp(m->zc, o->n_fine, m->out_f, &fa2), "mlp (fine, fused)")))
+                return rc;
+        }
+        return MCL_OK;
+    }
     {
         PhaseScope ph(m, MCL_PHASE_MLP_COARSE, s);
-        if ((rc = cuda_check(mlp(m->zf, o->n_guided, m->out_c), "mlp (guided)"))) return rc;
+        if ((rc = cuda_check(mlp(m->zf, o->n_guided, m->out_c, nullptr), "mlp (guided)"))) return rc;
     }
     if (o->n_fine > 0) {
         {
@@ -374,9 +455,9 @@ static int render_passes(mcl_map* m, const float* d_poses, int N, const mcl_intr
                 return rc;
         }
         PhaseScope ph(m, MCL_PHASE_MLP_FINE, s);
-        if ((rc = cuda_check(mlp(m->zc, o->n_fine, m->out_f), "mlp (fine)"))) return rc;
+        if ((rc = cuda_check(mlp(m->zc, o->n_fine, m->out_f, nullptr), "mlp (fine)"))) return rc;
     }
-    *out = Passes{m->zf, m->out_c, o->n_guided, m->zc, m->out_f, o->n_fine, f};
+    *out = Passes{m->zf, m->out_c, o->n_guided, m->zc, m->out_f, o->n_fine, f, false};
     return MCL_OK;
 }
 
@@ -400,9 +481,12 @@ extern "C" int mcl_update(mcl_map* m, const float* d_particles, int N, const flo
     cudaStream_t s = (cudaStream_t)stream;
     int rc;
     Passes ps;
-    if ((rc = render_passes(m, d_particles, N, K, level, d_pixels, B, o, &ps, s))) return rc;
+    const FinalOut fin{d_image, m->e_ray, dbg ? dbg->rgb : nullptr, dbg ? dbg->E : nullptr,
+                       dbg ? dbg->F : nullptr, dbg ? dbg->z_trans : nullptr,
+                       dbg ? dbg->z_opaque : nullptr};
+    if ((rc = render_passes(m, d_particles, N, K, level, d_pixels, B, o, &ps, s, &fin))) return rc;
     const int nr = N * B;
-    {
+    if (!ps.fused) {
         PhaseScope ph(m, MCL_PHASE_COMPOSITE, s);
         if ((rc = cuda_check(launch_final_composite(m->rays, nr, ps.za, ps.oa, ps.na, ps.zb, ps.ob,
                                                     ps.nb, d_image, K->width, K->height, ps.factor,
@@ -465,7 +549,9 @@ extern "C" int mcl_render(mcl_map* m, const float* d_poses, int n_poses, const m
     cudaStream_t s = (cudaStream_t)stream;
     int rc;
     Passes ps;
-    if ((rc = render_passes(m, d_poses, n_poses, K, level, d_pixels, B, o, &ps, s))) return rc;
+    const FinalOut fin{nullptr, nullptr, d_rgb, nullptr, d_F, nullptr, nullptr};
+    if ((rc = render_passes(m, d_poses, n_poses, K, level, d_pixels, B, o, &ps, s, &fin))) return rc;
+    if (ps.fused) return MCL_OK;
     PhaseScope ph(m, MCL_PHASE_COMPOSITE, s);
     return cuda_check(launch_final_composite(m->rays, n_poses * B, ps.za, ps.oa, ps.na, ps.zb,
                                              ps.ob, ps.nb, nullptr, K->width, K->height, ps.factor,
@@ -716,6 +802,14 @@ extern "C" int mcl_inject_weight_stall(mcl_map* m, int n_launches, double wait_m
     if (n_launches < 0 || !(wait_ms >= 0.01 && wait_ms <= 2000.0))
         return fail(MCL_ERR_ARG, "mcl_inject_weight_stall: n_launches >= 0, 0.01 <= wait_ms <= 2000");
     return mlp_tc_hold_weights(m, n_launches, (unsigned long long)(wait_ms * 1e6));
+}
+
+extern "C" int mcl_set_fused_epilogue(mcl_map* m, int enable) {
+    g_err[0] = 0;
+    if (!m) return fail(MCL_ERR_ARG, "mcl_set_fused_epilogue: NULL map");
+    m->fuse_epilogue = enable != 0;
+    m->loop.key = 0;   // a captured loop holds the old launch sequence
+    return MCL_OK;
 }
 
 extern "C" int mcl_set_mlp_variant(mcl_map* m, int precision, int variant) {

@@ -98,6 +98,7 @@ struct mcl_map {
     float* zf = nullptr;          // [max_rays * max_samples] fine z
     float4* out_c = nullptr;      // [max_rays * max_samples] (sigma_raw, rgb)
     float4* out_f = nullptr;
+    float4* obs = nullptr;        // [max_rays] observed colour per ray (fused epilogue)
     float* e_ray = nullptr;       // [max_rays] E*F
     double* logw64 = nullptr;     // [max_particles]
     unsigned long long* cdf = nullptr;  // [max_particles] resampling CDF
@@ -127,6 +128,7 @@ struct mcl_map {
     uint16_t* prop_packed = nullptr;   // BF16 weights of the tensor-core proposal kernel
     int* prop_abort = nullptr;         // per-launch abort flag of that kernel
     int n_sm = 0;
+    bool fuse_epilogue = true;         // tensor-core forms: fused ray epilogues
 };
 
 namespace mcl {
@@ -139,9 +141,14 @@ int cuda_check(cudaError_t e, const char* what);
 void note_launch(int n = 1);
 
 // render.cu
+// obs (optional): per-ray box-filtered colour of the level image at the
+// ray's pixel (factor x factor block of the full-resolution W x H image;
+// NaN for a pixel outside the level image).
 cudaError_t launch_raygen(const float* particles, int N, const int32_t* pixels, int B,
                           float fx, float fy, float cx, float cy, const mcl_opts& o,
-                          Ray* rays, float* gd, float* zc, cudaStream_t s);
+                          Ray* rays, float* gd, float* zc, cudaStream_t s,
+                          const float* image = nullptr, int W = 0, int H = 0, int factor = 1,
+                          float4* obs = nullptr);
 cudaError_t launch_query_setup(const float* X, const float* D, int n, Ray* rays, float* gd,
                                float* z, cudaStream_t s);
 cudaError_t launch_coarse_to_fine(const Ray* rays, int n_rays, const int* n_rays_dev,
@@ -173,9 +180,39 @@ bool mlp_tc_tuned(const mcl_map* m, int precision);
 int mlp_tc_hold_weights(mcl_map* m, int n_launches, unsigned long long wait_ns);
 cudaError_t mlp_tc_ray_bias(mcl_map* m, const float* gd, int n_rays, const int* n_rays_dev,
                             cudaStream_t s);
+// Fused ray epilogue of a tensor-core MLP pass (tiles hold whole rays).
+//   mode 1 (first pass of the hierarchical sampler): Eq. 1 weights of each
+//          ray's S samples -> nf_out inverse-CDF samples into z_out [rays,
+//          nf_out]; out is written as usual;
+//   mode 2 (last pass): merge with the first pass (z_first, out_first
+//          [rays, S1]; S1 = 0: none), Eq. 1 composite, Eq. 5 / F, and with
+//          obs (per-ray observed colour) E and e_ray = E F; optional per-ray
+//          rgb / E / F / z_trans / z_opaque; out is not written.
+struct FuseArgs {
+    int mode;
+    int nf_out;
+    float* z_out;
+    const float* z_first;
+    const float4* out_first;
+    int S1;
+    float alpha, tau;
+    int use_rej;
+    const float4* obs;
+    float* e_ray;
+    float* rgb_out;
+    float* E_out;
+    float* F_out;
+    float* zt_out;
+    float* zo_out;
+};
+// Whether a pass of S samples per ray (and S1 first-pass samples, mode 2)
+// can run with the fused epilogue.
+bool mlp_tc_can_fuse(int mode, int S, int S1);
 // rows_dev (optional): device-side row count (rows = n_rays * S is the bound).
+// fuse (optional): fused ray epilogue of the pass.
 cudaError_t mlp_tc(mcl_map* m, int precision, const Ray* rays, const float* gd, const float* z,
-                   int S, int n_rays, const int* rows_dev, float4* out, cudaStream_t s);
+                   int S, int n_rays, const int* rows_dev, float4* out, cudaStream_t s,
+                   const FuseArgs* fuse = nullptr);
 
 // resample.cu
 // status may be NULL (degenerate weights then show only as idx = -1)

@@ -66,7 +66,9 @@ __global__ void k_raygen_b(const LoopPlan* __restrict__ pl, int nq, const float*
                            int stride, const int32_t* __restrict__ pix, float fx, float fy,
                            float cx, float cy, int nc, float near_z, float far_z, int jitter,
                            uint64_t seed, int t, int max_rays, Ray* __restrict__ rays,
-                           float* __restrict__ gd, float* __restrict__ zc) {
+                           float* __restrict__ gd, float* __restrict__ zc,
+                           const float* const* __restrict__ imgs, int W, int H,
+                           float4* __restrict__ obs) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= max_rays || r >= pl->total_rays) return;
     const int q = query_of_ray(pl, nq, r);
@@ -79,6 +81,7 @@ __global__ void k_raygen_b(const LoopPlan* __restrict__ pl, int nq, const float*
              cy / f, ray, gd + (size_t)r * kGdPad);
     rays[r] = ray;
     coarse_samples(rl, nc, near_z, far_z, jitter, seed, loop_ctr(q, t, 3), zc + (size_t)r * nc);
+    if (obs) obs[r] = observed_colour(imgs[q], W, H, f, px[2 * j], px[2 * j + 1]);
 }
 
 __global__ void k_final_b(const LoopPlan* __restrict__ pl, int nq, const float* const* __restrict__ imgs,
@@ -258,11 +261,30 @@ int enqueue_localize(mcl_map* m, int nq, float* P_user, int stride, const mcl_in
     float* const za = prop ? m->zf : m->zc;
     float* const zb = prop ? m->zc : m->zf;
     const int tb = 128;
-    // the NeRF MLP of the precision, rows from the plan in device memory
+    // the NeRF MLP of the precision, rows from the plan in device memory;
+    // tensor-core forms with the fused ray epilogues where the shapes allow
     const bool fp32 = o.precision == MCL_PREC_FP32;
-    auto mlp = [&](const float* z, int S, const int* rows_dev, float4* dst) -> cudaError_t {
+    const bool fused = !fp32 && m->fuse_epilogue &&
+                       (nf > 0 ? mlp_tc_can_fuse(1, nc, 0) && mlp_tc_can_fuse(2, nf, nc)
+                               : mlp_tc_can_fuse(2, nc, 0));
+    FuseArgs fa1{}, fa2{};
+    fa1.mode = 1;
+    fa1.nf_out = nf;
+    fa1.z_out = zb;
+    fa2.mode = 2;
+    fa2.z_first = za;
+    fa2.out_first = m->out_c;
+    fa2.S1 = nf > 0 ? nc : 0;
+    fa2.alpha = o.alpha;
+    fa2.tau = o.tau;
+    fa2.use_rej = o.use_rejection;
+    fa2.obs = m->obs;
+    fa2.e_ray = m->e_ray;
+    auto mlp = [&](const float* z, int S, const int* rows_dev, float4* dst,
+                   const FuseArgs* fa) -> cudaError_t {
         if (fp32) return mlp_fp32(m, m->rays, m->gd, z, S, max_rays_run, dst, s, rows_dev);
-        return mlp_tc(m, o.precision, m->rays, m->gd, z, S, max_rays_run, rows_dev, dst, s);
+        return mlp_tc(m, o.precision, m->rays, m->gd, z, S, max_rays_run, rows_dev, dst, s,
+                      fused ? fa : nullptr);
     };
     float* Pc = P_user;
     float* Pn = L.P_next;
@@ -274,7 +296,8 @@ int enqueue_localize(mcl_map* m, int nq, float* P_user, int stride, const mcl_in
         k_pixels<<<1, 64, 0, s>>>(L.plan, nq, K.width, K.height, o.seed, t, L.pix);
         k_raygen_b<<<(max_rays_run + tb - 1) / tb, tb, 0, s>>>(
             L.plan, nq, Pc, stride, L.pix, K.fx, K.fy, K.cx, K.cy, np, o.near_z, o.far_z,
-            prop ? 0 : o.jitter, o.seed, t, max_rays_run, m->rays, m->gd, m->zc);
+            prop ? 0 : o.jitter, o.seed, t, max_rays_run, m->rays, m->gd, m->zc, L.imgs, K.width,
+            K.height, fused ? m->obs : nullptr);
         if (!fp32 && (rc = cuda_check(mlp_tc_ray_bias(m, m->gd, max_rays_run, &L.plan->total_rays, s),
                                       "loop ray bias")))
             return rc;
@@ -287,20 +310,25 @@ int enqueue_localize(mcl_map* m, int nq, float* P_user, int stride, const mcl_in
                                  "loop proposal sampling")))
                 return rc;
         }
-        if ((rc = cuda_check(mlp(za, nc, &L.plan->rows_c, m->out_c), "loop mlp (coarse)")))
+        if ((rc = cuda_check(mlp(za, nc, &L.plan->rows_c, m->out_c, nf > 0 ? &fa1 : &fa2),
+                             "loop mlp (coarse)")))
             return rc;
         if (nf > 0) {
-            if ((rc = cuda_check(launch_coarse_to_fine(m->rays, max_rays_run, &L.plan->total_rays,
+            if (!fused &&
+                (rc = cuda_check(launch_coarse_to_fine(m->rays, max_rays_run, &L.plan->total_rays,
                                                        za, nc, m->out_c, nf, zb, s),
                                  "loop importance sampling")))
                 return rc;
-            if ((rc = cuda_check(mlp(zb, nf, &L.plan->rows_f, m->out_f), "loop mlp (fine)")))
+            if ((rc = cuda_check(mlp(zb, nf, &L.plan->rows_f, m->out_f, &fa2), "loop mlp (fine)")))
                 return rc;
         }
-        note_launch(5);
-        k_final_b<<<(max_rays_run + tb - 1) / tb, tb, 0, s>>>(
-            L.plan, nq, L.imgs, K.width, L.pix, m->rays, za, m->out_c, nc, zb, m->out_f, nf,
-            o.alpha, o.tau, o.use_rejection, max_rays_run, m->e_ray);
+        if (!fused) {
+            note_launch();
+            k_final_b<<<(max_rays_run + tb - 1) / tb, tb, 0, s>>>(
+                L.plan, nq, L.imgs, K.width, L.pix, m->rays, za, m->out_c, nc, zb, m->out_f, nf,
+                o.alpha, o.tau, o.use_rejection, max_rays_run, m->e_ray);
+        }
+        note_launch(4);
         k_weights_b<<<nq, kLoopThreads, 0, s>>>(L.plan, L.qs, Pc, stride, m->e_ray, o.s_min,
                                                  o.rho_reject, m->logw64, L.w, L.mask, d_log,
                                                  sch.iterations, t, sch);

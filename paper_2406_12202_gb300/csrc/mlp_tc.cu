@@ -134,6 +134,30 @@ struct Params {
     unsigned long long wait_ns;  // limit of the bounded waits of k_mlp_tc
     int hold_weights;       // failure-injection hook (k_mlp_tc): the weight
                             // stream issues no copies, so the waits expire
+    // Fused ray epilogues (tiles hold whole rays: 128 % S == 0).
+    //   fuse 0: write (sigma_raw, rgb) of every row to out;
+    //   fuse 1: also the first pass of the hierarchical sampler: Eq. 1
+    //           weights of each ray's S samples -> nf_out inverse-CDF samples
+    //           into z_out [rays, nf_out];
+    //   fuse 2: the last pass: merge each ray's S samples with the S1 samples
+    //           of the first pass (z_first, out_first [rays, S1]; S1 = 0: this
+    //           pass only), Eq. 1 composite, Eq. 5 / F and E against obs; out
+    //           is not written.
+    int fuse;
+    int nf_out;
+    float* z_out;
+    const float* z_first;
+    const float4* out_first;
+    int S1;
+    float eq5_alpha, tau;   // Eq. 5 threshold, lower bound of F
+    int use_rej;
+    const float4* obs;      // [rays] observed level-image colour (NaN: none), or NULL
+    float* e_ray;           // [rays] E * F (with obs)
+    float* rgb_out;         // [rays, 3] (optional)
+    float* E_out;           // [rays] (optional)
+    float* F_out;
+    float* zt_out;
+    float* zo_out;
 };
 
 struct __align__(8) Bars {
@@ -141,6 +165,7 @@ struct __align__(8) Bars {
     uint64_t empty[kMaxStages];
     uint64_t acc_full[2];
     uint64_t a_ready[2];
+    uint64_t epi[2];        // the 128 row threads of a tile meet in the fused ray epilogues
     uint64_t drain;
     uint32_t tmem_base;
 };
@@ -247,6 +272,264 @@ __device__ __forceinline__ void rgb_group(const uint32_t (&v)[32], const float4*
     }
 }
 
+
+// ---------------------------------------------------------------------------
+// Fused ray epilogues.  After the last layer, the 128 threads that own the
+// rows of a tile (one row each) work on the tile's R = 128 / S whole rays:
+// they stage samples in shared memory (the first 16 KB of the tile's
+// activation buffer, free between the last layer's MMA and the next work
+// unit's first epilogue), meet at the tile's `epi` mbarrier (bounded waits,
+// so an aborted launch cannot hang them), and one warp per ray runs the
+// sequential parts of Eq. 1 as warp-shuffle scans: each lane takes a
+// contiguous chunk of the ray's samples, the transmittance entering a chunk
+// is the exclusive product scan of the chunks' transmittances, and running
+// weight sums are exclusive sum scans.
+// ---------------------------------------------------------------------------
+constexpr uint32_t kFuseScratch = 16384;
+
+struct EpiSync {
+    uint32_t bar;
+    uint32_t ph;
+    volatile int* err;
+    unsigned long long limit;
+    // every one of the tile's 128 row threads arrives; returns false if the
+    // wait gave up (abort or time limit)
+    __device__ __forceinline__ bool sync() {
+        mbar_arrive(bar);
+        const bool r = mbar_wait(bar, ph, err, limit);
+        ph ^= 1u;
+        return r;
+    }
+};
+
+__device__ __forceinline__ float warp_excl_prod(float v, int lane) {
+    float x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const float t = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x *= t;
+    }
+    const float e = __shfl_up_sync(0xffffffffu, x, 1);
+    return lane == 0 ? 1.0f : e;
+}
+
+__device__ __forceinline__ float warp_incl_sum(float v, int lane) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const float t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+    }
+    return v;
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// First pass of the hierarchical sampler, fused: Eq. 1 weights w_k of each
+// ray's S samples, pdf over the interior bins (between midpoints of
+// consecutive samples) proportional to w_1 .. w_{S-2} + 1e-5, inverse CDF at
+// u_j = j / (nf - 1) (bin: first CDF entry strictly greater than u_j, linear
+// interpolation inside it).  Row thread r holds (z, sigma_raw) of row r.
+__device__ __forceinline__ bool tail_importance(const Params& p, EpiSync& es, float* scr, int r,
+                                                int lane, int quad, long long ray0,
+                                                long long n_rays, float z, float sg) {
+    const int S = p.S, R = 128 / S, nf = p.nf_out, ne = S - 1;
+    float* zs = scr;            // [128]
+    float* ss = scr + 128;      // [128]
+    float* cdfs = scr + 256;    // [R][S]
+    zs[r] = z;
+    ss[r] = sg;
+    if (!es.sync()) return false;
+    const int c = (S + 31) >> 5;
+    for (int g = quad; g < R; g += 4) {
+        const long long ray = ray0 + g;
+        if (ray >= n_rays) continue;
+        const float dn = p.rays[ray].dnorm;
+        const float* z_ = zs + g * S;
+        const float* s_ = ss + g * S;
+        float* cdf = cdfs + g * S;
+        const int k0 = lane * c, k1 = min(k0 + c, S);
+        float wl[4];
+        float Tl = 1.0f;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int k = k0 + i;
+            wl[i] = 0.0f;
+            if (i < c && k < k1) {
+                const float delta = (k < S - 1) ? (z_[k + 1] - z_[k]) * dn : 1e10f;
+                const float a = 1.0f - expf(-fmaxf(s_[k], 0.0f) * delta);
+                wl[i] = Tl * a;
+                Tl *= 1.0f - a;
+            }
+        }
+        const float T0 = warp_excl_prod(Tl, lane);
+        float pl[4];
+        float psum = 0.0f;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int k = k0 + i;
+            pl[i] = (i < c && k < k1 && k >= 1 && k <= S - 2) ? T0 * wl[i] + 1e-5f : 0.0f;
+            psum += pl[i];
+        }
+        const float incl = warp_incl_sum(psum, lane);
+        const float tot = __shfl_sync(0xffffffffu, incl, 31);
+        float run = incl - psum;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int k = k0 + i;
+            if (i < c && k < k1 && k >= 1 && k <= S - 2) {
+                run += pl[i];
+                cdf[k] = run / tot;
+            }
+        }
+        if (lane == 0) cdf[0] = 0.0f;
+        __syncwarp();
+        for (int j = lane; j < nf; j += 32) {
+            const float u = nf > 1 ? (float)j / (float)(nf - 1) : 0.0f;
+            int lo = 0, hi = ne;   // first index in [0, ne) with cdf > u, ne if none
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (cdf[mid] > u) hi = mid;
+                else lo = mid + 1;
+            }
+            const int below = lo - 1 < 0 ? 0 : lo - 1;
+            const int above = lo > ne - 1 ? ne - 1 : lo;
+            float denom = cdf[above] - cdf[below];
+            if (denom < 1e-5f) denom = 1.0f;
+            const float t = (u - cdf[below]) / denom;
+            const float eb = 0.5f * (z_[below] + z_[below + 1]);
+            const float ea = 0.5f * (z_[above] + z_[above + 1]);
+            p.z_out[ray * nf + j] = eb + t * (ea - eb);
+        }
+        __syncwarp();
+    }
+    return es.sync();
+}
+
+// Last pass, fused: merge each ray's S samples of this pass with the S1
+// samples of the first pass (both sorted; equal z take the first pass's
+// sample first), Eq. 1 composite over the merged samples (delta_last =
+// 1e10), Eq. 5 on the running weight sum, F of Eq. 6 and the photometric E
+// against the ray's observed colour.  Row thread r holds (z, sigma_raw, rgb)
+// of row r and has prefetched first-pass samples q = r and r + 128 of the
+// tile (fz / fo).
+__device__ __forceinline__ bool tail_final(const Params& p, EpiSync& es, float* scr, int r,
+                                           int lane, int quad, long long ray0, long long n_rays,
+                                           float z, float4 v, const float (&fz)[2],
+                                           const float4 (&fo)[2]) {
+    const int S = p.S, S1 = p.S1, R = 128 / S, n = S + S1;
+    float* zB = scr;                    // [128] this pass
+    float* zA = scr + 128;              // [R * S1] first pass
+    float* mz = zA + R * S1;            // merged [R][n]: z, sigma (then alpha), r, g, b
+    float* ms = mz + R * n;
+    float* mr = ms + R * n;
+    float* mg = mr + R * n;
+    float* mb = mg + R * n;
+    zB[r] = z;
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const int q = r + 128 * i;
+        if (q < R * S1) zA[q] = fz[i];
+    }
+    if (!es.sync()) return false;
+    {
+        // this pass's sample j of ray g: j + (first-pass samples with z <= it)
+        const int g = r / S, j = r - g * S;
+        const float* a = zA + g * S1;
+        int lo = 0, hi = S1;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (a[mid] <= z) lo = mid + 1;
+            else hi = mid;
+        }
+        const int k = g * n + j + lo;
+        mz[k] = z; ms[k] = v.x; mr[k] = v.y; mg[k] = v.z; mb[k] = v.w;
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        // first-pass sample q of ray g: i + (this pass's samples with z < it)
+        const int q = r + 128 * i;
+        if (q < R * S1) {
+            const int g = q / S1, ii = q - g * S1;
+            const float* b = zB + g * S;
+            const float zq = fz[i];
+            int lo = 0, hi = S;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (b[mid] < zq) lo = mid + 1;
+                else hi = mid;
+            }
+            const int k = g * n + ii + lo;
+            mz[k] = zq; ms[k] = fo[i].x; mr[k] = fo[i].y; mg[k] = fo[i].z; mb[k] = fo[i].w;
+        }
+    }
+    if (!es.sync()) return false;
+    const int c = (n + 31) >> 5;
+    for (int g = quad; g < R; g += 4) {
+        const long long ray = ray0 + g;
+        if (ray >= n_rays) continue;
+        const float dn = p.rays[ray].dnorm;
+        float* z_ = mz + g * n;
+        float* s_ = ms + g * n;
+        const float* r_ = mr + g * n;
+        const float* g_ = mg + g * n;
+        const float* b_ = mb + g * n;
+        const int k0 = min(lane * c, n), k1 = min(k0 + c, n);
+        // chunk pass 1: alpha (stored over sigma), local transmittance,
+        // colour and weight sums of the chunk
+        float Tl = 1.0f, cr = 0.0f, cg = 0.0f, cb = 0.0f, wsum = 0.0f;
+        for (int k = k0; k < k1; ++k) {
+            const float delta = (k < n - 1) ? (z_[k + 1] - z_[k]) * dn : 1e10f;
+            const float a = 1.0f - expf(-fmaxf(s_[k], 0.0f) * delta);
+            const float w = Tl * a;
+            cr += w * r_[k]; cg += w * g_[k]; cb += w * b_[k];
+            wsum += w;
+            Tl *= 1.0f - a;
+            s_[k] = a;
+        }
+        const float T0 = warp_excl_prod(Tl, lane);
+        const float Cr = warp_sum(T0 * cr), Cg = warp_sum(T0 * cg), Cb = warp_sum(T0 * cb);
+        const float incl = warp_incl_sum(T0 * wsum, lane);
+        const float W0 = incl - T0 * wsum;
+        // chunk pass 2: running weight sum W_k, Eq. 5 decisions
+        int kt = n, ko = -1;
+        float Tl2 = 1.0f, wc = 0.0f;
+        for (int k = k0; k < k1; ++k) {
+            const float w = Tl2 * s_[k];
+            wc += w;
+            Tl2 *= 1.0f - s_[k];
+            const float Wk = W0 + T0 * wc;
+            if (kt == n && Wk >= p.eq5_alpha) kt = k;
+            if (Wk <= 1.0f - p.eq5_alpha) ko = k;
+        }
+        kt = __reduce_min_sync(0xffffffffu, kt);
+        ko = __reduce_max_sync(0xffffffffu, ko);
+        if (lane == 0) {
+            const float zt = kt < n ? z_[kt] : z_[0];
+            const float zo = ko >= 0 ? z_[ko] : z_[0];
+            const float F = p.use_rej ? fmaxf(zo - zt, p.tau) : 1.0f;
+            if (p.rgb_out) {
+                p.rgb_out[3 * ray] = Cr; p.rgb_out[3 * ray + 1] = Cg; p.rgb_out[3 * ray + 2] = Cb;
+            }
+            if (p.F_out) p.F_out[ray] = F;
+            if (p.zt_out) p.zt_out[ray] = zt;
+            if (p.zo_out) p.zo_out[ray] = zo;
+            if (p.obs) {
+                const float4 ob = p.obs[ray];
+                const float e0 = ob.x - Cr, e1 = ob.y - Cg, e2 = ob.z - Cb;
+                const float E = isfinite(dn) ? e0 * e0 + e1 * e1 + e2 * e2 : __int_as_float(0x7fc00000);
+                if (p.E_out) p.E_out[ray] = E;
+                p.e_ray[ray] = E * F;
+            }
+        }
+        __syncwarp();
+    }
+    return es.sync();
+}
+
 // Operand writes of one thread (activations or gamma(x)) and its TMEM reads
 // are done: make the writes visible to the tensor core and signal the MMA
 // issuer.  Single CTA: every epilogue thread arrives on the local barrier.
@@ -277,7 +560,8 @@ __device__ __forceinline__ void epilogue_warps(const Params& p, int warp, int wa
                                                uint32_t bar_ready1, uint32_t bar_acc0,
                                                uint32_t bar_acc1, long long M, long long u0,
                                                long long du, long long n_units, long long unit_rows,
-                                               long long row_base) {
+                                               long long row_base, uint8_t* act_ptr,
+                                               uint32_t bar_epi0, uint32_t bar_epi1) {
     volatile int* abort_flag = p.abort_flag;
     // EPIW warps per tile: warp w covers TMEM lane quadrant (w % 4), i.e.
     // rows 32 (w % 4) .. +31; with 8 warps the first four take accumulator
@@ -299,10 +583,26 @@ __device__ __forceinline__ void epilogue_warps(const Params& p, int warp, int wa
     bool ok = true;
     const bool tracer = (r == 0 && h0 == 0);
     int tl = 0;
+    // fused ray epilogue of a finished unit, run by the row-owning warps
+    // (h0 == 0) after the next unit's prologue, while its first MMAs run
+    EpiSync es{slot ? bar_epi1 : bar_epi0, 0u, abort_flag, p.wait_ns};
+    float* scr = reinterpret_cast<float*>(act_ptr + slot * kActBytes);
+    const long long n_rays = M / p.S;
+    bool pend = false;
+    long long pend_ray0 = 0;
+    float pz = 0.f;
+    float4 pv = make_float4(0.f, 0.f, 0.f, 0.f);
+    float fz[2] = {0.f, 0.f};
+    float4 fo[2] = {make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f)};
+    auto run_tail = [&]() -> bool {
+        if (p.fuse == 1) return tail_importance(p, es, scr, (int)r, lane, quad, pend_ray0, n_rays, pz, pv.x);
+        return tail_final(p, es, scr, (int)r, lane, quad, pend_ray0, n_rays, pz, pv, fz, fo);
+    };
     for (long long pr = u0; pr < n_units && ok; pr += du) {
         const long long grow = pr * unit_rows + row_base + slot * 128 + r;
         const bool valid = grow < M;
         const long long ray = valid ? grow / p.S : 0;
+        float zrow = 0.f;
         // ---- prologue: this thread's halves of gamma(x) into the tile's
         //      gamma(x) buffer
         {
@@ -310,6 +610,7 @@ __device__ __forceinline__ void epilogue_warps(const Params& p, int warp, int wa
             if (valid) {
                 const Ray R = p.rays[ray];
                 const float zz = p.z[grow];
+                zrow = zz;
                 x[0] = fmaf(zz, R.dx, R.ox);
                 x[1] = fmaf(zz, R.dy, R.oy);
                 x[2] = fmaf(zz, R.dz, R.oz);
@@ -347,6 +648,11 @@ __device__ __forceinline__ void epilogue_warps(const Params& p, int warp, int wa
                 }
             }
             signal_ready<PAIR>(bar_ready, lane);
+        }
+        if (pend) {
+            ok = run_tail();
+            pend = false;
+            if (!ok) break;
         }
         float sigma = 0.0f;
         for (int l = 0; l < kLayers && ok; ++l, ++tl) {
@@ -427,17 +733,36 @@ __device__ __forceinline__ void epilogue_warps(const Params& p, int warp, int wa
                     if constexpr (F8) sigma *= p.alpha_sigma;
                 }
                 tc_fence_before();
-                if (valid) {
-                    float4 res;
-                    res.x = sigma + p.b_sigma;
-                    res.y = 1.0f / (1.0f + __expf(-(o0 + p.b_out0)));
-                    res.z = 1.0f / (1.0f + __expf(-(o1 + p.b_out1)));
-                    res.w = 1.0f / (1.0f + __expf(-(o2 + p.b_out2)));
-                    p.out[grow] = res;
+                float4 res;
+                res.x = sigma + p.b_sigma;
+                res.y = 1.0f / (1.0f + __expf(-(o0 + p.b_out0)));
+                res.z = 1.0f / (1.0f + __expf(-(o1 + p.b_out1)));
+                res.w = 1.0f / (1.0f + __expf(-(o2 + p.b_out2)));
+                if (valid && p.fuse != 2) p.out[grow] = res;
+                if (p.fuse) {
+                    pend = true;
+                    pend_ray0 = (pr * unit_rows + row_base + slot * 128) / p.S;
+                    pz = zrow;
+                    pv = valid ? res : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+                if (p.fuse == 2) {
+                    // first-pass samples q = r, r + 128 of this tile's rays,
+                    // in flight while the next unit's prologue runs
+                    const int R1 = (128 / p.S) * p.S1;
+#pragma unroll
+                    for (int i = 0; i < 2; ++i) {
+                        const int q = (int)r + 128 * i;
+                        if (q < R1 && pend_ray0 + q / p.S1 < n_rays) {
+                            const long long idx = (pend_ray0 + q / p.S1) * p.S1 + q % p.S1;
+                            fz[i] = p.z_first[idx];
+                            fo[i] = p.out_first[idx];
+                        }
+                    }
                 }
             }
         }
     }
+    if (pend && ok) ok = run_tail();
     if (!ok) record_abort(p);
 }
 
@@ -468,6 +793,7 @@ __global__ void __launch_bounds__(Variant<F8, EPIW, STAG>::kThreads, 1)
         for (int s = 0; s < 2; ++s) {
             mbar_init(smem_u32(&bars.acc_full[s]), 1);
             mbar_init(smem_u32(&bars.a_ready[s]), Vt::kEpiThreads);
+            mbar_init(smem_u32(&bars.epi[s]), 128);
         }
         mbar_init(smem_u32(&bars.drain), 1);
         fence_mbar_init();
@@ -676,7 +1002,8 @@ __global__ void __launch_bounds__(Variant<F8, EPIW, STAG>::kThreads, 1)
         epilogue_warps<F8, EPIW, false>(p, warp, 3, lane, tmem, s_act, s_gx,
                                         smem_u32(&bars.a_ready[0]), smem_u32(&bars.a_ready[1]),
                                         smem_u32(&bars.acc_full[0]), smem_u32(&bars.acc_full[1]),
-                                        M, blockIdx.x, gridDim.x, n_pairs, 256, 0);
+                                        M, blockIdx.x, gridDim.x, n_pairs, 256, 0, smem,
+                                        smem_u32(&bars.epi[0]), smem_u32(&bars.epi[1]));
     }
     tc_fence_before();
     __syncthreads();
@@ -718,6 +1045,7 @@ struct __align__(8) PairBars {
     uint64_t empty[kPairMaxStages];
     uint64_t acc_full[2];
     uint64_t a_ready[2];
+    uint64_t epi[2];                  // this CTA's row threads, fused ray epilogues
     uint64_t drain;
     uint32_t tmem_base;
 };
@@ -753,6 +1081,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kPairThreads, 1)
         for (int s = 0; s < 2; ++s) {
             mbar_init(smem_u32(&bars.acc_full[s]), 1);
             mbar_init(smem_u32(&bars.a_ready[s]), 8);   // 4 epilogue warps x 2 CTAs
+            mbar_init(smem_u32(&bars.epi[s]), 128);
         }
         mbar_init(smem_u32(&bars.drain), 1);
         fence_mbar_init();
@@ -969,7 +1298,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kPairThreads, 1)
         const uint32_t rdy1 = mapa_shared(smem_u32(&bars.a_ready[1]), 0);
         epilogue_warps<F8, 4, true>(p, warp, 3, lane, tmem, s_act, s_gx, rdy0, rdy1,
                                     smem_u32(&bars.acc_full[0]), smem_u32(&bars.acc_full[1]), M, u0, du,
-                                    n_units, 512, (long long)rank * 256);
+                                    n_units, 512, (long long)rank * 256, smem,
+                                    smem_u32(&bars.epi[0]), smem_u32(&bars.epi[1]));
     }
     __syncwarp();
     tc_fence_before();
@@ -1868,21 +2198,41 @@ cudaError_t mlp_tc_ray_bias(mcl_map* m, const float* gd, int n_rays, const int* 
 
 static cudaError_t mlp_tc_variant(mcl_map* m, int precision, int variant, const Ray* rays,
                                   const float* z, int S, int n_rays, const int* rows_dev,
-                                  float4* out, cudaStream_t s);
+                                  float4* out, cudaStream_t s, const FuseArgs* fuse = nullptr);
+
+// The fused ray epilogues work on whole rays inside a 128-row tile (S divides
+// 128) and stage a tile's samples in the first kFuseScratch bytes of its
+// activation buffer; the first-pass samples of a tile's rays are prefetched
+// two per row thread.
+bool mlp_tc_can_fuse(int mode, int S, int S1) {
+    if (S < 1 || S > 128 || 128 % S != 0) return false;
+    const int R = 128 / S;
+    if (mode == 1) return S >= 4 && 4 * (256 + R * S) <= (int)kFuseScratch;
+    if (mode == 2)
+        return S1 >= 0 && S1 <= kMaxCoarse && R * S1 <= 256 &&
+               4 * (128 + R * S1 + 5 * R * (S + S1)) <= (int)kFuseScratch;
+    return false;
+}
 
 cudaError_t mlp_tc(mcl_map* m, int precision, const Ray* rays, const float* gd, const float* z,
-                   int S, int n_rays, const int* rows_dev, float4* out, cudaStream_t s) {
+                   int S, int n_rays, const int* rows_dev, float4* out, cudaStream_t s,
+                   const FuseArgs* fuse) {
     (void)gd;
-    return mlp_tc_variant(m, precision, -1, rays, z, S, n_rays, rows_dev, out, s);
+    return mlp_tc_variant(m, precision, -1, rays, z, S, n_rays, rows_dev, out, s, fuse);
 }
 
 static cudaError_t mlp_tc_variant(mcl_map* m, int precision, int variant, const Ray* rays,
                                   const float* z, int S, int n_rays, const int* rows_dev,
-                                  float4* out, cudaStream_t s) {
+                                  float4* out, cudaStream_t s, const FuseArgs* fuse) {
     TcState* st = (TcState*)m->tc_aux;
     if (!mlp_tc_available(m, precision)) return cudaErrorNotSupported;
     Params p;
-    const int vi = variant >= 0 ? variant : st->variant[precision];
+    memset(&p, 0, sizeof(p));
+    int vi = variant >= 0 ? variant : st->variant[precision];
+    // the split and pipelined schedules have their own epilogues: fused
+    // passes run on the untuned single-CTA kernel instead
+    if (fuse && (kVariants[vi].fn == &k_mlp_tc_split || kVariants[vi].fn == &k_mlp_tc_pipe))
+        vi = kDefaultVariant[precision];
     p.wblocks = precision == MCL_PREC_FP8 ? st->fp8.wblocks
                 : kVariants[vi].fn == &k_mlp_tc_split ? st->bf16_split.wblocks
                                                       : st->bf16.wblocks;
@@ -1905,6 +2255,24 @@ static cudaError_t mlp_tc_variant(mcl_map* m, int precision, int variant, const 
     p.b_out1 = st->b_out[1];
     p.b_out2 = st->b_out[2];
     p.out = out;
+    if (fuse) {
+        p.fuse = fuse->mode;
+        p.nf_out = fuse->nf_out;
+        p.z_out = fuse->z_out;
+        p.z_first = fuse->z_first;
+        p.out_first = fuse->out_first;
+        p.S1 = fuse->S1;
+        p.eq5_alpha = fuse->alpha;
+        p.tau = fuse->tau;
+        p.use_rej = fuse->use_rej;
+        p.obs = fuse->obs;
+        p.e_ray = fuse->e_ray;
+        p.rgb_out = fuse->rgb_out;
+        p.E_out = fuse->E_out;
+        p.F_out = fuse->F_out;
+        p.zt_out = fuse->zt_out;
+        p.zo_out = fuse->zo_out;
+    }
     p.abort_flag = st->abort_flag;
     p.status_code = &m->status->code;
     p.wait_ns = kWaitNs;

@@ -14,7 +14,9 @@ namespace mcl {
 __global__ void k_raygen(const float* __restrict__ P, int N, const int32_t* __restrict__ px,
                          int B, float fx, float fy, float cx, float cy, int nc, float near_z,
                          float far_z, int jitter, uint64_t seed, uint64_t ctr,
-                         Ray* __restrict__ rays, float* __restrict__ gd, float* __restrict__ zc) {
+                         Ray* __restrict__ rays, float* __restrict__ gd, float* __restrict__ zc,
+                         const float* __restrict__ img, int W, int H, int factor,
+                         float4* __restrict__ obs) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= N * B) return;
     const int i = r / B, j = r - (r / B) * B;
@@ -23,6 +25,7 @@ __global__ void k_raygen(const float* __restrict__ P, int N, const int32_t* __re
              gd + (size_t)r * kGdPad);
     rays[r] = ray;
     coarse_samples(r, nc, near_z, far_z, jitter, seed, ctr, zc + (size_t)r * nc);
+    if (obs) obs[r] = observed_colour(img, W, H, factor, px[2 * j], px[2 * j + 1]);
 }
 
 // Point queries: one "ray" per point with o = x, d = 0 and one sample at
@@ -66,12 +69,14 @@ cudaError_t launch_query_setup(const float* X, const float* D, int n, Ray* rays,
 
 cudaError_t launch_raygen(const float* particles, int N, const int32_t* pixels, int B, float fx,
                           float fy, float cx, float cy, const mcl_opts& o, Ray* rays, float* gd,
-                          float* zc, cudaStream_t s) {
+                          float* zc, cudaStream_t s, const float* image, int W, int H, int factor,
+                          float4* obs) {
     const int n = N * B, tb = 128;
     note_launch();
     k_raygen<<<(n + tb - 1) / tb, tb, 0, s>>>(particles, N, pixels, B, fx, fy, cx, cy, o.n_coarse,
                                                o.near_z, o.far_z, o.jitter, o.seed, o.counter,
-                                               rays, gd, zc);
+                                               rays, gd, zc, image, W, H, factor,
+                                               image ? obs : nullptr);
     return cudaGetLastError();
 }
 

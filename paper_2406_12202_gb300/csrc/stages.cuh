@@ -185,6 +185,25 @@ __device__ __forceinline__ RayResult composite_ray(float dn, const float* __rest
     return res;
 }
 
+// Box-filtered colour of level-image pixel (u, v) (factor x factor block of
+// the full-resolution image, W pixels per row); NaN outside the level image.
+__device__ __forceinline__ float4 observed_colour(const float* __restrict__ img, int W, int H,
+                                                  int factor, int u, int v) {
+    if (u < 0 || v < 0 || u >= W / factor || v >= H / factor) {
+        const float nan = __int_as_float(0x7fc00000);
+        return make_float4(nan, nan, nan, nan);
+    }
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+    for (int dy = 0; dy < factor; ++dy) {
+        const float* row = img + ((size_t)(v * factor + dy) * W + (size_t)u * factor) * 3;
+        for (int dx = 0; dx < factor; ++dx) {
+            s0 += row[3 * dx]; s1 += row[3 * dx + 1]; s2 += row[3 * dx + 2];
+        }
+    }
+    const float inv = 1.0f / (float)(factor * factor);
+    return make_float4(s0 * inv, s1 * inv, s2 * inv, 0.f);
+}
+
 // E = squared RGB distance between the rendered colour and the box-filtered
 // observed pixel (u, v) of the level image (factor x factor block of the
 // full-resolution image, W pixels per row).  NaN when the ray is invalid.
