@@ -278,22 +278,23 @@ __device__ __forceinline__ void rgb_group(const uint32_t (&v)[32], const float4*
 // rows of a tile (one row each) work on the tile's R = 128 / S whole rays:
 // they stage samples in shared memory (the first 16 KB of the tile's
 // activation buffer, free between the last layer's MMA and the next work
-// unit's first epilogue), meet at the tile's `epi` mbarrier (bounded waits,
-// so an aborted launch cannot hang them), and one warp per ray runs the
+// unit's first epilogue), meet at the tile's `epi` mbarrier (EpiSync), and
+// one warp per ray runs the
 // sequential parts of Eq. 1 as warp-shuffle scans: each lane takes a
 // contiguous chunk of the ray's samples, the transmittance entering a chunk
 // is the exclusive product scan of the chunks' transmittances, and running
 // weight sums are exclusive sum scans.
 // ---------------------------------------------------------------------------
-constexpr uint32_t kFuseScratch = 16384;
 
+// The tile's 128 row threads meet at the tile's `epi` mbarrier: every thread
+// arrives, then waits for the phase with the kernel's bounded wait, so a
+// launch that aborts cannot leave the others waiting.
 struct EpiSync {
     uint32_t bar;
     uint32_t ph;
     volatile int* err;
     unsigned long long limit;
-    // every one of the tile's 128 row threads arrives; returns false if the
-    // wait gave up (abort or time limit)
+    // returns false if the wait gave up (abort or time limit)
     __device__ __forceinline__ bool sync() {
         mbar_arrive(bar);
         const bool r = mbar_wait(bar, ph, err, limit);
@@ -328,85 +329,111 @@ __device__ __forceinline__ float warp_sum(float v) {
     return v;
 }
 
+// Staging in the tile's activation buffer.  Warp q (the warp of TMEM lane
+// quadrant q) rewrites only its own rows in the next unit's first epilogue:
+// bytes [q 4096, +4096) of each 16 KB K-block.  Ray g of a tile (at most 4)
+// is composited by warp g, and its samples are staged in that warp's part of
+// K-block 0, so the other warps never wait for the compositing warp: once
+// the staging is complete they go on to the next layer.  Data that every
+// thread reads (this pass's z of the whole tile, the first pass's z) sits in
+// K-block 1 and is dead after the second barrier.
+__device__ __forceinline__ float* warp_part(float* scr, int q) {
+    return scr + q * 1024;   // 4096 bytes
+}
+
 // First pass of the hierarchical sampler, fused: Eq. 1 weights w_k of each
 // ray's S samples, pdf over the interior bins (between midpoints of
 // consecutive samples) proportional to w_1 .. w_{S-2} + 1e-5, inverse CDF at
 // u_j = j / (nf - 1) (bin: first CDF entry strictly greater than u_j, linear
 // interpolation inside it).  Row thread r holds (z, sigma_raw) of row r.
+// R = 128 / S <= 4 rays per tile; one barrier.
 __device__ __forceinline__ bool tail_importance(const Params& p, EpiSync& es, float* scr, int r,
                                                 int lane, int quad, long long ray0,
-                                                long long n_rays, float z, float sg) {
+                                                long long n_rays, float z, float sg, float dn_row) {
     const int S = p.S, R = 128 / S, nf = p.nf_out, ne = S - 1;
-    float* zs = scr;            // [128]
-    float* ss = scr + 128;      // [128]
-    float* cdfs = scr + 256;    // [R][S]
-    zs[r] = z;
-    ss[r] = sg;
+    {
+        // ray g's part: z [S], sigma [S], cdf [S], |d|
+        const int g = r / S, k = r - g * S;
+        float* part = warp_part(scr, g);
+        part[k] = z;
+        part[S + k] = sg;
+        if (k == 0) part[3 * S] = dn_row;
+    }
     if (!es.sync()) return false;
+    if (quad >= R) return true;
+    const long long ray = ray0 + quad;
+    if (ray >= n_rays) return true;
+    float* part = warp_part(scr, quad);
+    const float* z_ = part;
+    const float* s_ = part + S;
+    float* cdf = part + 2 * S;
+    const float dn = part[3 * S];
     const int c = (S + 31) >> 5;
-    for (int g = quad; g < R; g += 4) {
-        const long long ray = ray0 + g;
-        if (ray >= n_rays) continue;
-        const float dn = p.rays[ray].dnorm;
-        const float* z_ = zs + g * S;
-        const float* s_ = ss + g * S;
-        float* cdf = cdfs + g * S;
-        const int k0 = lane * c, k1 = min(k0 + c, S);
-        float wl[4];
-        float Tl = 1.0f;
+    const int k0 = lane * c, k1 = min(k0 + c, S);
+    float wl[4];
+    float Tl = 1.0f;
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const int k = k0 + i;
-            wl[i] = 0.0f;
-            if (i < c && k < k1) {
-                const float delta = (k < S - 1) ? (z_[k + 1] - z_[k]) * dn : 1e10f;
-                const float a = 1.0f - expf(-fmaxf(s_[k], 0.0f) * delta);
-                wl[i] = Tl * a;
-                Tl *= 1.0f - a;
-            }
+    for (int i = 0; i < 4; ++i) {
+        const int k = k0 + i;
+        wl[i] = 0.0f;
+        if (i < c && k < k1) {
+            const float delta = (k < S - 1) ? (z_[k + 1] - z_[k]) * dn : 1e10f;
+            const float a = 1.0f - expf(-fmaxf(s_[k], 0.0f) * delta);
+            wl[i] = Tl * a;
+            Tl *= 1.0f - a;
         }
-        const float T0 = warp_excl_prod(Tl, lane);
-        float pl[4];
-        float psum = 0.0f;
+    }
+    const float T0 = warp_excl_prod(Tl, lane);
+    float pl[4];
+    float psum = 0.0f;
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const int k = k0 + i;
-            pl[i] = (i < c && k < k1 && k >= 1 && k <= S - 2) ? T0 * wl[i] + 1e-5f : 0.0f;
-            psum += pl[i];
-        }
-        const float incl = warp_incl_sum(psum, lane);
-        const float tot = __shfl_sync(0xffffffffu, incl, 31);
-        float run = incl - psum;
+    for (int i = 0; i < 4; ++i) {
+        const int k = k0 + i;
+        pl[i] = (i < c && k < k1 && k >= 1 && k <= S - 2) ? T0 * wl[i] + 1e-5f : 0.0f;
+        psum += pl[i];
+    }
+    const float incl = warp_incl_sum(psum, lane);
+    const float tot = __shfl_sync(0xffffffffu, incl, 31);
+    float run = incl - psum;
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const int k = k0 + i;
-            if (i < c && k < k1 && k >= 1 && k <= S - 2) {
-                run += pl[i];
-                cdf[k] = run / tot;
-            }
+    for (int i = 0; i < 4; ++i) {
+        const int k = k0 + i;
+        if (i < c && k < k1 && k >= 1 && k <= S - 2) {
+            run += pl[i];
+            cdf[k] = run / tot;
         }
-        if (lane == 0) cdf[0] = 0.0f;
-        __syncwarp();
-        for (int j = lane; j < nf; j += 32) {
-            const float u = nf > 1 ? (float)j / (float)(nf - 1) : 0.0f;
+    }
+    if (lane == 0) cdf[0] = 0.0f;
+    __syncwarp();
+    // lane l: outputs j = d l .. d l + d - 1 (u increasing): one binary search,
+    // then forward steps
+    const int d = (nf + 31) >> 5;
+    int idx = 0;
+    for (int t = 0; t < d; ++t) {
+        const int j = lane * d + t;
+        if (j >= nf) break;
+        const float u = nf > 1 ? (float)j / (float)(nf - 1) : 0.0f;
+        if (t == 0) {
             int lo = 0, hi = ne;   // first index in [0, ne) with cdf > u, ne if none
             while (lo < hi) {
                 const int mid = (lo + hi) >> 1;
                 if (cdf[mid] > u) hi = mid;
                 else lo = mid + 1;
             }
-            const int below = lo - 1 < 0 ? 0 : lo - 1;
-            const int above = lo > ne - 1 ? ne - 1 : lo;
-            float denom = cdf[above] - cdf[below];
-            if (denom < 1e-5f) denom = 1.0f;
-            const float t = (u - cdf[below]) / denom;
-            const float eb = 0.5f * (z_[below] + z_[below + 1]);
-            const float ea = 0.5f * (z_[above] + z_[above + 1]);
-            p.z_out[ray * nf + j] = eb + t * (ea - eb);
+            idx = lo;
+        } else {
+            while (idx < ne && cdf[idx] <= u) ++idx;
         }
-        __syncwarp();
+        const int below = idx - 1 < 0 ? 0 : idx - 1;
+        const int above = idx > ne - 1 ? ne - 1 : idx;
+        float denom = cdf[above] - cdf[below];
+        if (denom < 1e-5f) denom = 1.0f;
+        const float tt = (u - cdf[below]) / denom;
+        const float eb = 0.5f * (z_[below] + z_[below + 1]);
+        const float ea = 0.5f * (z_[above] + z_[above + 1]);
+        p.z_out[ray * nf + j] = eb + tt * (ea - eb);
     }
-    return es.sync();
+    return true;
 }
 
 // Last pass, fused: merge each ray's S samples of this pass with the S1
@@ -415,20 +442,20 @@ __device__ __forceinline__ bool tail_importance(const Params& p, EpiSync& es, fl
 // 1e10), Eq. 5 on the running weight sum, F of Eq. 6 and the photometric E
 // against the ray's observed colour.  Row thread r holds (z, sigma_raw, rgb)
 // of row r and has prefetched first-pass samples q = r and r + 128 of the
-// tile (fz / fo).
+// tile (fz / fo) and, in warp g, the observed colour of ray g (ob).  R =
+// 128 / S <= 4 rays per tile, at most 204 merged samples per ray; two
+// barriers.
 __device__ __forceinline__ bool tail_final(const Params& p, EpiSync& es, float* scr, int r,
                                            int lane, int quad, long long ray0, long long n_rays,
-                                           float z, float4 v, const float (&fz)[2],
-                                           const float4 (&fo)[2]) {
+                                           float z, float4 v, float dn_row, const float (&fz)[2],
+                                           const float4 (&fo)[2], const float4& ob) {
     const int S = p.S, S1 = p.S1, R = 128 / S, n = S + S1;
-    float* zB = scr;                    // [128] this pass
-    float* zA = scr + 128;              // [R * S1] first pass
-    float* mz = zA + R * S1;            // merged [R][n]: z, sigma (then alpha), r, g, b
-    float* ms = mz + R * n;
-    float* mr = ms + R * n;
-    float* mg = mr + R * n;
-    float* mb = mg + R * n;
+    float* shared_z = scr + 4096;       // K-block 1: read by every thread
+    float* zB = shared_z;               // [128] this pass
+    float* dns = shared_z + 128;        // [4] |d| of each ray
+    float* zA = shared_z + 132;         // [R * S1] first pass
     zB[r] = z;
+    if (r % S == 0) dns[r / S] = dn_row;
 #pragma unroll
     for (int i = 0; i < 2; ++i) {
         const int q = r + 128 * i;
@@ -445,8 +472,9 @@ __device__ __forceinline__ bool tail_final(const Params& p, EpiSync& es, float* 
             if (a[mid] <= z) lo = mid + 1;
             else hi = mid;
         }
-        const int k = g * n + j + lo;
-        mz[k] = z; ms[k] = v.x; mr[k] = v.y; mg[k] = v.z; mb[k] = v.w;
+        float* m = warp_part(scr, g);   // merged [n] z, sigma (then alpha), r, g, b
+        const int k = j + lo;
+        m[k] = z; m[n + k] = v.x; m[2 * n + k] = v.y; m[3 * n + k] = v.z; m[4 * n + k] = v.w;
     }
 #pragma unroll
     for (int i = 0; i < 2; ++i) {
@@ -462,72 +490,73 @@ __device__ __forceinline__ bool tail_final(const Params& p, EpiSync& es, float* 
                 if (b[mid] < zq) lo = mid + 1;
                 else hi = mid;
             }
-            const int k = g * n + ii + lo;
-            mz[k] = zq; ms[k] = fo[i].x; mr[k] = fo[i].y; mg[k] = fo[i].z; mb[k] = fo[i].w;
+            float* m = warp_part(scr, g);
+            const int k = ii + lo;
+            m[k] = zq; m[n + k] = fo[i].x; m[2 * n + k] = fo[i].y; m[3 * n + k] = fo[i].z;
+            m[4 * n + k] = fo[i].w;
         }
     }
+    const float dn = dns[quad < R ? quad : 0];
     if (!es.sync()) return false;
+    if (quad >= R) return true;
+    const long long ray = ray0 + quad;
+    if (ray >= n_rays) return true;
+    float* m = warp_part(scr, quad);
+    const float* z_ = m;
+    float* s_ = m + n;
+    const float* r_ = m + 2 * n;
+    const float* g_ = m + 3 * n;
+    const float* b_ = m + 4 * n;
     const int c = (n + 31) >> 5;
-    for (int g = quad; g < R; g += 4) {
-        const long long ray = ray0 + g;
-        if (ray >= n_rays) continue;
-        const float dn = p.rays[ray].dnorm;
-        float* z_ = mz + g * n;
-        float* s_ = ms + g * n;
-        const float* r_ = mr + g * n;
-        const float* g_ = mg + g * n;
-        const float* b_ = mb + g * n;
-        const int k0 = min(lane * c, n), k1 = min(k0 + c, n);
-        // chunk pass 1: alpha (stored over sigma), local transmittance,
-        // colour and weight sums of the chunk
-        float Tl = 1.0f, cr = 0.0f, cg = 0.0f, cb = 0.0f, wsum = 0.0f;
-        for (int k = k0; k < k1; ++k) {
-            const float delta = (k < n - 1) ? (z_[k + 1] - z_[k]) * dn : 1e10f;
-            const float a = 1.0f - expf(-fmaxf(s_[k], 0.0f) * delta);
-            const float w = Tl * a;
-            cr += w * r_[k]; cg += w * g_[k]; cb += w * b_[k];
-            wsum += w;
-            Tl *= 1.0f - a;
-            s_[k] = a;
-        }
-        const float T0 = warp_excl_prod(Tl, lane);
-        const float Cr = warp_sum(T0 * cr), Cg = warp_sum(T0 * cg), Cb = warp_sum(T0 * cb);
-        const float incl = warp_incl_sum(T0 * wsum, lane);
-        const float W0 = incl - T0 * wsum;
-        // chunk pass 2: running weight sum W_k, Eq. 5 decisions
-        int kt = n, ko = -1;
-        float Tl2 = 1.0f, wc = 0.0f;
-        for (int k = k0; k < k1; ++k) {
-            const float w = Tl2 * s_[k];
-            wc += w;
-            Tl2 *= 1.0f - s_[k];
-            const float Wk = W0 + T0 * wc;
-            if (kt == n && Wk >= p.eq5_alpha) kt = k;
-            if (Wk <= 1.0f - p.eq5_alpha) ko = k;
-        }
-        kt = __reduce_min_sync(0xffffffffu, kt);
-        ko = __reduce_max_sync(0xffffffffu, ko);
-        if (lane == 0) {
-            const float zt = kt < n ? z_[kt] : z_[0];
-            const float zo = ko >= 0 ? z_[ko] : z_[0];
-            const float F = p.use_rej ? fmaxf(zo - zt, p.tau) : 1.0f;
-            if (p.rgb_out) {
-                p.rgb_out[3 * ray] = Cr; p.rgb_out[3 * ray + 1] = Cg; p.rgb_out[3 * ray + 2] = Cb;
-            }
-            if (p.F_out) p.F_out[ray] = F;
-            if (p.zt_out) p.zt_out[ray] = zt;
-            if (p.zo_out) p.zo_out[ray] = zo;
-            if (p.obs) {
-                const float4 ob = p.obs[ray];
-                const float e0 = ob.x - Cr, e1 = ob.y - Cg, e2 = ob.z - Cb;
-                const float E = isfinite(dn) ? e0 * e0 + e1 * e1 + e2 * e2 : __int_as_float(0x7fc00000);
-                if (p.E_out) p.E_out[ray] = E;
-                p.e_ray[ray] = E * F;
-            }
-        }
-        __syncwarp();
+    const int k0 = min(lane * c, n), k1 = min(k0 + c, n);
+    // chunk pass 1: alpha (stored over sigma), local transmittance, colour
+    // and weight sums of the chunk
+    float Tl = 1.0f, cr = 0.0f, cg = 0.0f, cb = 0.0f, wsum = 0.0f;
+    for (int k = k0; k < k1; ++k) {
+        const float delta = (k < n - 1) ? (z_[k + 1] - z_[k]) * dn : 1e10f;
+        const float a = 1.0f - expf(-fmaxf(s_[k], 0.0f) * delta);
+        const float w = Tl * a;
+        cr += w * r_[k]; cg += w * g_[k]; cb += w * b_[k];
+        wsum += w;
+        Tl *= 1.0f - a;
+        s_[k] = a;
     }
-    return es.sync();
+    const float T0 = warp_excl_prod(Tl, lane);
+    const float Cr = warp_sum(T0 * cr), Cg = warp_sum(T0 * cg), Cb = warp_sum(T0 * cb);
+    const float incl = warp_incl_sum(T0 * wsum, lane);
+    const float W0 = incl - T0 * wsum;
+    // chunk pass 2: running weight sum W_k, Eq. 5 decisions
+    int kt = n, ko = -1;
+    float Tl2 = 1.0f, wc = 0.0f;
+    for (int k = k0; k < k1; ++k) {
+        const float w = Tl2 * s_[k];
+        wc += w;
+        Tl2 *= 1.0f - s_[k];
+        const float Wk = W0 + T0 * wc;
+        if (kt == n && Wk >= p.eq5_alpha) kt = k;
+        if (Wk <= 1.0f - p.eq5_alpha) ko = k;
+    }
+    kt = __reduce_min_sync(0xffffffffu, kt);
+    ko = __reduce_max_sync(0xffffffffu, ko);
+    if (lane == 0) {
+        const float zt = kt < n ? z_[kt] : z_[0];
+        const float zo = ko >= 0 ? z_[ko] : z_[0];
+        const float F = p.use_rej ? fmaxf(zo - zt, p.tau) : 1.0f;
+        if (p.rgb_out) {
+            p.rgb_out[3 * ray] = Cr; p.rgb_out[3 * ray + 1] = Cg; p.rgb_out[3 * ray + 2] = Cb;
+        }
+        if (p.F_out) p.F_out[ray] = F;
+        if (p.zt_out) p.zt_out[ray] = zt;
+        if (p.zo_out) p.zo_out[ray] = zo;
+        if (p.obs) {
+            const float e0 = ob.x - Cr, e1 = ob.y - Cg, e2 = ob.z - Cb;
+            const float E = isfinite(dn) ? e0 * e0 + e1 * e1 + e2 * e2 : __int_as_float(0x7fc00000);
+            if (p.E_out) p.E_out[ray] = E;
+            p.e_ray[ray] = E * F;
+        }
+    }
+    __syncwarp();
+    return true;
 }
 
 // Operand writes of one thread (activations or gamma(x)) and its TMEM reads
@@ -553,15 +582,17 @@ __device__ __forceinline__ void signal_ready(uint32_t bar, int lane) {
 // into the slot's buffer, then per layer TMEM -> bias + ReLU (and the FP8
 // scales) -> the next layer's A operand, and after the last layer the RGB
 // output layer and the density.  PAIR: bar_ready* are shared::cluster
-// addresses of the even CTA's barriers.
-template <bool F8, int EPIW, bool PAIR>
+// addresses of the even CTA's barriers.  FUSE (0, 1, 2): the fused ray
+// epilogue of the pass (Params::fuse); instantiations without it carry no
+// code or registers for it.
+template <bool F8, int EPIW, bool PAIR, int FUSE = 0>
 __device__ __forceinline__ void epilogue_warps(const Params& p, int warp, int warp0, int lane, uint32_t tmem,
                                                uint32_t s_act, uint32_t s_gx, uint32_t bar_ready0,
                                                uint32_t bar_ready1, uint32_t bar_acc0,
                                                uint32_t bar_acc1, long long M, long long u0,
                                                long long du, long long n_units, long long unit_rows,
                                                long long row_base, uint8_t* act_ptr,
-                                               uint32_t bar_epi0, uint32_t bar_epi1) {
+                                               uint32_t bar_epi0 = 0, uint32_t bar_epi1 = 0) {
     volatile int* abort_flag = p.abort_flag;
     // EPIW warps per tile: warp w covers TMEM lane quadrant (w % 4), i.e.
     // rows 32 (w % 4) .. +31; with 8 warps the first four take accumulator
@@ -590,19 +621,22 @@ __device__ __forceinline__ void epilogue_warps(const Params& p, int warp, int wa
     const long long n_rays = M / p.S;
     bool pend = false;
     long long pend_ray0 = 0;
-    float pz = 0.f;
+    float pz = 0.f, pdn = 0.f;
     float4 pv = make_float4(0.f, 0.f, 0.f, 0.f);
     float fz[2] = {0.f, 0.f};
     float4 fo[2] = {make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f)};
+    float4 ob = make_float4(0.f, 0.f, 0.f, 0.f);
     auto run_tail = [&]() -> bool {
-        if (p.fuse == 1) return tail_importance(p, es, scr, (int)r, lane, quad, pend_ray0, n_rays, pz, pv.x);
-        return tail_final(p, es, scr, (int)r, lane, quad, pend_ray0, n_rays, pz, pv, fz, fo);
+        if constexpr (FUSE == 1)
+            return tail_importance(p, es, scr, (int)r, lane, quad, pend_ray0, n_rays, pz, pv.x, pdn);
+        else
+            return tail_final(p, es, scr, (int)r, lane, quad, pend_ray0, n_rays, pz, pv, pdn, fz, fo, ob);
     };
     for (long long pr = u0; pr < n_units && ok; pr += du) {
         const long long grow = pr * unit_rows + row_base + slot * 128 + r;
         const bool valid = grow < M;
         const long long ray = valid ? grow / p.S : 0;
-        float zrow = 0.f;
+        float zrow = 0.f, dnrow = 0.f;
         // ---- prologue: this thread's halves of gamma(x) into the tile's
         //      gamma(x) buffer
         {
@@ -611,6 +645,7 @@ __device__ __forceinline__ void epilogue_warps(const Params& p, int warp, int wa
                 const Ray R = p.rays[ray];
                 const float zz = p.z[grow];
                 zrow = zz;
+                dnrow = R.dnorm;
                 x[0] = fmaf(zz, R.dx, R.ox);
                 x[1] = fmaf(zz, R.dy, R.oy);
                 x[2] = fmaf(zz, R.dz, R.oz);
@@ -649,15 +684,28 @@ __device__ __forceinline__ void epilogue_warps(const Params& p, int warp, int wa
             }
             signal_ready<PAIR>(bar_ready, lane);
         }
-        if (pend) {
-            ok = run_tail();
-            pend = false;
-            if (!ok) break;
+        if constexpr (FUSE != 0) {
+            // (a failure leaves the function at once: no path from inside
+            // the layer loop reaches a use of the pending-ray state, so that
+            // state is live only between the last layer and the tail)
+            if (pend) {
+                pend = false;
+                if (!run_tail()) {
+                    record_abort(p);
+                    return;
+                }
+            }
         }
         float sigma = 0.0f;
+        float4 res = make_float4(0.f, 0.f, 0.f, 0.f);
         for (int l = 0; l < kLayers && ok; ++l, ++tl) {
-            if (!(PAIR ? mbar_wait_cluster<true>(bar_acc, acc_ph, abort_flag)
-                       : mbar_wait_sleep(bar_acc, acc_ph, abort_flag, p.wait_ns))) {
+            const bool got = PAIR ? mbar_wait_cluster<true>(bar_acc, acc_ph, abort_flag)
+                                  : mbar_wait_sleep(bar_acc, acc_ph, abort_flag, p.wait_ns);
+            if (!got) {
+                if constexpr (FUSE != 0) {
+                    record_abort(p);
+                    return;
+                }
                 ok = false;
                 break;
             }
@@ -733,40 +781,49 @@ __device__ __forceinline__ void epilogue_warps(const Params& p, int warp, int wa
                     if constexpr (F8) sigma *= p.alpha_sigma;
                 }
                 tc_fence_before();
-                float4 res;
                 res.x = sigma + p.b_sigma;
                 res.y = 1.0f / (1.0f + __expf(-(o0 + p.b_out0)));
                 res.z = 1.0f / (1.0f + __expf(-(o1 + p.b_out1)));
                 res.w = 1.0f / (1.0f + __expf(-(o2 + p.b_out2)));
-                if (valid && p.fuse != 2) p.out[grow] = res;
-                if (p.fuse) {
-                    pend = true;
-                    pend_ray0 = (pr * unit_rows + row_base + slot * 128) / p.S;
-                    pz = zrow;
-                    pv = valid ? res : make_float4(0.f, 0.f, 0.f, 0.f);
-                }
-                if (p.fuse == 2) {
-                    // first-pass samples q = r, r + 128 of this tile's rays,
-                    // in flight while the next unit's prologue runs
-                    const int R1 = (128 / p.S) * p.S1;
+                if (valid && FUSE != 2) p.out[grow] = res;
+            }
+        }
+        if constexpr (FUSE != 0) {
+            // the unit's ray epilogue runs after the next unit's prologue
+            pend = true;
+            pend_ray0 = (pr * unit_rows + row_base + slot * 128) / p.S;
+            pz = zrow;
+            pdn = dnrow;
+            pv = valid ? res : make_float4(0.f, 0.f, 0.f, 0.f);
+            if constexpr (FUSE == 2) {
+                // first-pass samples q = r, r + 128 of this tile's rays, in
+                // flight while the next unit's prologue runs
+                const int R1 = (128 / p.S) * p.S1;
 #pragma unroll
-                    for (int i = 0; i < 2; ++i) {
-                        const int q = (int)r + 128 * i;
-                        if (q < R1 && pend_ray0 + q / p.S1 < n_rays) {
-                            const long long idx = (pend_ray0 + q / p.S1) * p.S1 + q % p.S1;
-                            fz[i] = p.z_first[idx];
-                            fo[i] = p.out_first[idx];
-                        }
+                for (int i = 0; i < 2; ++i) {
+                    const int q = (int)r + 128 * i;
+                    if (q < R1 && pend_ray0 + q / p.S1 < n_rays) {
+                        const long long idx = (pend_ray0 + q / p.S1) * p.S1 + q % p.S1;
+                        fz[i] = p.z_first[idx];
+                        fo[i] = p.out_first[idx];
                     }
                 }
+                // observed colour of the ray this warp will composite
+                if (p.obs && quad < 128 / p.S && pend_ray0 + quad < n_rays)
+                    ob = p.obs[pend_ray0 + quad];
             }
         }
     }
-    if (pend && ok) ok = run_tail();
+    if constexpr (FUSE != 0) {
+        if (pend && !run_tail()) {
+            record_abort(p);
+            return;
+        }
+    }
     if (!ok) record_abort(p);
 }
 
-template <bool F8, int EPIW, bool STAG>
+template <bool F8, int EPIW, bool STAG, int FUSE = 0>
 __global__ void __launch_bounds__(Variant<F8, EPIW, STAG>::kThreads, 1)
     k_mlp_tc(const __grid_constant__ Params p) {
     using Fm = Form<F8>;
@@ -999,7 +1056,7 @@ __global__ void __launch_bounds__(Variant<F8, EPIW, STAG>::kThreads, 1)
         }
         if (!ok && lane == 0) record_abort(p);
     } else {
-        epilogue_warps<F8, EPIW, false>(p, warp, 3, lane, tmem, s_act, s_gx,
+        epilogue_warps<F8, EPIW, false, FUSE>(p, warp, 3, lane, tmem, s_act, s_gx,
                                         smem_u32(&bars.a_ready[0]), smem_u32(&bars.a_ready[1]),
                                         smem_u32(&bars.acc_full[0]), smem_u32(&bars.acc_full[1]),
                                         M, blockIdx.x, gridDim.x, n_pairs, 256, 0, smem,
@@ -1045,7 +1102,6 @@ struct __align__(8) PairBars {
     uint64_t empty[kPairMaxStages];
     uint64_t acc_full[2];
     uint64_t a_ready[2];
-    uint64_t epi[2];                  // this CTA's row threads, fused ray epilogues
     uint64_t drain;
     uint32_t tmem_base;
 };
@@ -1081,7 +1137,6 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kPairThreads, 1)
         for (int s = 0; s < 2; ++s) {
             mbar_init(smem_u32(&bars.acc_full[s]), 1);
             mbar_init(smem_u32(&bars.a_ready[s]), 8);   // 4 epilogue warps x 2 CTAs
-            mbar_init(smem_u32(&bars.epi[s]), 128);
         }
         mbar_init(smem_u32(&bars.drain), 1);
         fence_mbar_init();
@@ -1298,8 +1353,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kPairThreads, 1)
         const uint32_t rdy1 = mapa_shared(smem_u32(&bars.a_ready[1]), 0);
         epilogue_warps<F8, 4, true>(p, warp, 3, lane, tmem, s_act, s_gx, rdy0, rdy1,
                                     smem_u32(&bars.acc_full[0]), smem_u32(&bars.acc_full[1]), M, u0, du,
-                                    n_units, 512, (long long)rank * 256, smem,
-                                    smem_u32(&bars.epi[0]), smem_u32(&bars.epi[1]));
+                                    n_units, 512, (long long)rank * 256, smem);
     }
     __syncwarp();
     tc_fence_before();
@@ -1850,6 +1904,12 @@ const TcVariant kVariants[] = {
     make_pair_variant<false, false>(), make_pair_variant<true, false>(),
     make_pair_variant<true, true>(),
 };
+// Fused passes (Params::fuse 1, 2) run on the single-CTA kernel with 4
+// epilogue warps per tile, in lockstep (BF16) or staggered (FP8): the
+// autotuner's choice at every size measured.
+void (*const kFusedKernels[2][2])(Params) = {
+    {&k_mlp_tc<false, 4, false, 1>, &k_mlp_tc<false, 4, false, 2>},
+    {&k_mlp_tc<true, 4, true, 1>, &k_mlp_tc<true, 4, true, 2>}};
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 static_assert(kNumVariants == MCL_MLP_VARIANTS, "variant table");
 // untuned choice per precision (fastest measured at all sizes on GB300):
@@ -2149,6 +2209,13 @@ int mlp_tc_prepare(mcl_map* m, const float* blob) {
                                                   (int)v.smem),
                              "smem attribute")))
             return rc;
+    for (int f8 = 0; f8 < 2; ++f8)
+        for (int mode = 0; mode < 2; ++mode)
+            if ((rc = cuda_check(cudaFuncSetAttribute(kFusedKernels[f8][mode],
+                                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                      (int)kVariants[kDefaultVariant[f8 + 1]].smem),
+                                 "smem attribute (fused)")))
+                return rc;
     {
         // persistent grid of the pair kernels: every pair resident at once
         cudaLaunchConfig_t cfg = {};
@@ -2201,16 +2268,15 @@ static cudaError_t mlp_tc_variant(mcl_map* m, int precision, int variant, const 
                                   float4* out, cudaStream_t s, const FuseArgs* fuse = nullptr);
 
 // The fused ray epilogues work on whole rays inside a 128-row tile (S divides
-// 128) and stage a tile's samples in the first kFuseScratch bytes of its
-// activation buffer; the first-pass samples of a tile's rays are prefetched
-// two per row thread.
+// 128) and stage a tile's samples in its activation buffer (see warp_part);
+// the first-pass samples of a tile's rays are prefetched two per row thread.
 bool mlp_tc_can_fuse(int mode, int S, int S1) {
-    if (S < 1 || S > 128 || 128 % S != 0) return false;
+    // whole rays per tile, at most four (one compositing warp each), each
+    // ray's staged samples within its warp's 4 KB part of the buffer
+    if (S < 32 || S > 128 || 128 % S != 0) return false;
     const int R = 128 / S;
-    if (mode == 1) return S >= 4 && 4 * (256 + R * S) <= (int)kFuseScratch;
-    if (mode == 2)
-        return S1 >= 0 && S1 <= kMaxCoarse && R * S1 <= 256 &&
-               4 * (128 + R * S1 + 5 * R * (S + S1)) <= (int)kFuseScratch;
+    if (mode == 1) return 3 * S + 1 <= 1024;
+    if (mode == 2) return S1 >= 0 && S1 <= kMaxCoarse && R * S1 <= 256 && 5 * (S + S1) <= 1024;
     return false;
 }
 
@@ -2229,10 +2295,9 @@ static cudaError_t mlp_tc_variant(mcl_map* m, int precision, int variant, const 
     Params p;
     memset(&p, 0, sizeof(p));
     int vi = variant >= 0 ? variant : st->variant[precision];
-    // the split and pipelined schedules have their own epilogues: fused
-    // passes run on the untuned single-CTA kernel instead
-    if (fuse && (kVariants[vi].fn == &k_mlp_tc_split || kVariants[vi].fn == &k_mlp_tc_pipe))
-        vi = kDefaultVariant[precision];
+    // fused passes run on their own instantiation of the untuned single-CTA
+    // kernel (kFusedKernels)
+    if (fuse) vi = kDefaultVariant[precision];
     p.wblocks = precision == MCL_PREC_FP8 ? st->fp8.wblocks
                 : kVariants[vi].fn == &k_mlp_tc_split ? st->bf16_split.wblocks
                                                       : st->bf16.wblocks;
@@ -2292,6 +2357,7 @@ static cudaError_t mlp_tc_variant(mcl_map* m, int precision, int variant, const 
     // persistent grid: one CTA per SM at most, one per work unit (a pair of
     // tiles, a single tile for the pipelined kernel, 512 rows for a CTA pair)
     const TcVariant& v = kVariants[vsel];
+    void (*fn)(Params) = fuse ? kFusedKernels[precision == MCL_PREC_FP8][fuse->mode - 1] : v.fn;
     long long grid;
     if (v.cluster == 2) {
         const long long units = (p.M + 511) / 512;
@@ -2301,7 +2367,7 @@ static cudaError_t mlp_tc_variant(mcl_map* m, int precision, int variant, const 
         grid = units < st->n_sm ? units : st->n_sm;
     }
     note_launch();
-    v.fn<<<(unsigned)grid, v.threads, v.smem, s>>>(p);
+    fn<<<(unsigned)grid, v.threads, v.smem, s>>>(p);
     return cudaGetLastError();
 }
 

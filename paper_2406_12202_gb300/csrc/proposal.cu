@@ -54,7 +54,9 @@ __device__ __forceinline__ float prop_point(const float* __restrict__ Wsh, const
                                             float* __restrict__ g, float* __restrict__ hsave) {
     float in[kPW], out[kPW];
     prop_pe(x, g);
-#pragma unroll
+    // outer loops over output units are not unrolled (the inner dot products
+    // are): the same arithmetic per unit, a fraction of the code size
+#pragma unroll 1
     for (int o = 0; o < kPW; ++o) {
         const float* w = Wsh + kPOff1 + o * kPIn;
         float s = Wsh[kPOff1 + kPW * kPIn + o];
@@ -69,7 +71,7 @@ __device__ __forceinline__ float prop_point(const float* __restrict__ Wsh, const
     for (int l = 1; l < kPDepth; ++l) {
         const float* W = Wsh + prop_off(l);
         const float* b = W + kPW * kPW;
-#pragma unroll
+#pragma unroll 1
         for (int o = 0; o < kPW; ++o) {
             float s = b[o];
 #pragma unroll
@@ -210,7 +212,7 @@ __global__ void k_prop_bwd_data(const float* __restrict__ W, const float* __rest
         for (int l = kPDepth - 1; l >= 1; --l) {
             const float* Wl = wsh + prop_off(l);
             float nxt[kPW];
-#pragma unroll
+#pragma unroll 1
             for (int i = 0; i < kPW; ++i) {
                 float s = 0.0f;
 #pragma unroll
