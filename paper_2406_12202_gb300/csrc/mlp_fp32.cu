@@ -51,7 +51,11 @@ __global__ void k_pe_xyz(const Ray* __restrict__ rays, const float* __restrict__
 // C[M, N] = act([A1 | A2] W^T + b).  A1: [M, K1] (lda1); A2 row for output
 // row r is (r + a2_off) / a2_div (lda2, K2 columns); W: [N, K1 + K2]
 // row-major.  K1, K2 multiples of 16, N a multiple of 128.  128x128 tile,
-// 256 threads, 8x8 outputs per thread, register double-buffered loads.
+// 256 threads, 8x8 outputs per thread.  Shared memory holds two k-tiles of
+// 16: while the threads multiply one, the next is loaded from global memory
+// into registers and stored into the other buffer, so each k-tile costs one
+// barrier.  Every output accumulates its products in ascending k with one
+// FMA each.
 template <bool RELU>
 __global__ __launch_bounds__(256, 2) void k_sgemm(const float* __restrict__ A1, int lda1, int K1,
                                                const float* __restrict__ A2, int lda2, int K2,
@@ -61,8 +65,8 @@ __global__ __launch_bounds__(256, 2) void k_sgemm(const float* __restrict__ A1, 
                                                float* __restrict__ C, int ldc, int M,
                                                const int* __restrict__ rows_dev, long r0) {
     constexpr int BM = 128, BN = 128, BK = 16, PAD = 4;
-    __shared__ __align__(16) float As[BK][BM + PAD];
-    __shared__ __align__(16) float Bs[BK][BN + PAD];
+    __shared__ __align__(16) float As[2][BK][BM + PAD];
+    __shared__ __align__(16) float Bs[2][BK][BN + PAD];
     const int tid = threadIdx.x;
     const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
     M = rows_in_chunk(M, r0, rows_dev);
@@ -94,28 +98,29 @@ __global__ __launch_bounds__(256, 2) void k_sgemm(const float* __restrict__ A1, 
             rb[h] = *reinterpret_cast<const float4*>(W + (size_t)nr * K + k0 + lk);
         }
     };
-    auto store = [&]() {
+    auto store = [&](int buf) {
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int c = lr + h * 64;
-            As[lk + 0][c] = ra[h].x; As[lk + 1][c] = ra[h].y;
-            As[lk + 2][c] = ra[h].z; As[lk + 3][c] = ra[h].w;
-            Bs[lk + 0][c] = rb[h].x; Bs[lk + 1][c] = rb[h].y;
-            Bs[lk + 2][c] = rb[h].z; Bs[lk + 3][c] = rb[h].w;
+            As[buf][lk + 0][c] = ra[h].x; As[buf][lk + 1][c] = ra[h].y;
+            As[buf][lk + 2][c] = ra[h].z; As[buf][lk + 3][c] = ra[h].w;
+            Bs[buf][lk + 0][c] = rb[h].x; Bs[buf][lk + 1][c] = rb[h].y;
+            Bs[buf][lk + 2][c] = rb[h].z; Bs[buf][lk + 3][c] = rb[h].w;
         }
     };
     load(0);
-    store();
+    store(0);
     __syncthreads();
+    int cur = 0;
     for (int k0 = 0; k0 < K; k0 += BK) {
         const bool more = k0 + BK < K;
         if (more) load(k0 + BK);
 #pragma unroll
         for (int kk = 0; kk < BK; ++kk) {
-            const float4 a0 = *reinterpret_cast<const float4*>(&As[kk][ty * 4]);
-            const float4 a1 = *reinterpret_cast<const float4*>(&As[kk][64 + ty * 4]);
-            const float4 b0 = *reinterpret_cast<const float4*>(&Bs[kk][tx * 4]);
-            const float4 b1 = *reinterpret_cast<const float4*>(&Bs[kk][64 + tx * 4]);
+            const float4 a0 = *reinterpret_cast<const float4*>(&As[cur][kk][ty * 4]);
+            const float4 a1 = *reinterpret_cast<const float4*>(&As[cur][kk][64 + ty * 4]);
+            const float4 b0 = *reinterpret_cast<const float4*>(&Bs[cur][kk][tx * 4]);
+            const float4 b1 = *reinterpret_cast<const float4*>(&Bs[cur][kk][64 + tx * 4]);
             const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
             const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
@@ -123,10 +128,11 @@ __global__ __launch_bounds__(256, 2) void k_sgemm(const float* __restrict__ A1, 
 #pragma unroll
                 for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
         }
-        __syncthreads();
         if (more) {
-            store();
+            // the other buffer was last read before the previous barrier
+            store(cur ^ 1);
             __syncthreads();
+            cur ^= 1;
         }
     }
 #pragma unroll
