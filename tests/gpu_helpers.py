@@ -101,7 +101,10 @@ def oracle_sensitivity(sc, uj=None):
 
 # The FP32 GPU form is held to K_ULP one-ulp perturbations of the exact
 # answer on top of the 1e-4 relative bar when importance sampling is on.
-K_ULP = 16
+# Measured on the GB300 over the six importance-sampled parity tests: the
+# largest error was 3.13 times the one-ulp sensitivity (the others 0.02 to
+# 0.70), so K_ULP is the next integer bar above it with a margin.
+K_ULP = 4
 
 
 def check_fp32_parity(g, r, N, B, rgb_rel=1e-4, rgb_abs=1e-6, logw_rel=1e-4, z_abs=2e-5,
@@ -118,10 +121,15 @@ def check_fp32_parity(g, r, N, B, rgb_rel=1e-4, rgb_abs=1e-6, logw_rel=1e-4, z_a
     particles with S_i >= S_FLOOR.  Normalised weights must follow the GPU's
     own log-weights.  Returns a dict of the observed maxima."""
     rep = {}
+    err = np.abs(g["rgb"] - r["rgb"])
     if sens is not None:
         rgb_abs = max(rgb_abs, K_ULP * sens["rgb"])
         rep["tol_rgb_abs"] = rgb_abs
-    err = np.abs(g["rgb"] - r["rgb"])
+        # the observed error in units of the exact answer's one-ulp
+        # sensitivity: K_ULP is set just above the largest ratio seen
+        rep["ulp_ratio"] = float(err.max() / max(sens["rgb"], 1e-30))
+        print(f"FP32 importance-sampled parity: max |dRGB| {err.max():.3g} = "
+              f"{rep['ulp_ratio']:.2f} x the one-ulp sensitivity {sens['rgb']:.3g}")
     tol = rgb_rel * np.abs(r["rgb"]) + rgb_abs
     rep["rgb_max_abs"] = float(err.max())
     assert np.all(err <= tol), f"RGB off: max err {err.max():.3g}, worst excess {(err - tol).max():.3g}"

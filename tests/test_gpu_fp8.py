@@ -1,6 +1,11 @@
 """FP8 (E4M3 operands, FP32 accumulation) form of the tensor-core NeRF MLP
 against the FP64 oracle.
 
+The bars derived from the E4M3 format's own error floor (twice the error of
+the plain layer structure with per-tensor-scaled E4M3 operands, every ray
+counted) are in test_gpu_format_floor.py; the checks below are coarser
+sanity bounds, kept from before that floor was measured.
+
 FP8 bars (stated, derived from the format, not inherited from BF16): E4M3
 keeps 4 significant bits, so every operand (positional encoding, weights,
 activations) carries a relative rounding of up to 2^-4 (about 1.8 % rms for

@@ -2,6 +2,12 @@
 MLP against the FP64 oracle: the MLP itself at sampled points, then whole
 weight updates.
 
+The bars derived from the BF16 format's own error floor (twice the error of
+the plain layer structure with BF16-rounded operands, every ray counted) are
+in test_gpu_format_floor.py; the checks below are the survey's absolute
+bars where that floor allows them (the c1 workload: RGB max 2e-2, mean 5e-3,
+Spearman 0.99, top-10 9) and coarser sanity bounds elsewhere.
+
 BF16 bars (stated, not inherited from FP32): BF16 keeps 8 significant bits,
 so each of the 63 positional-encoding inputs and 256 activations per layer
 carries a relative rounding of up to 2^-9; through nine layers this gives
@@ -129,7 +135,7 @@ def scene(map_seed, *a, **k):
 
 def test_bf16_update_c1_workload(M, gmaps):
     sc = scene(0, 0, 32, 8, 100, 100, 138.9, 32, 0, add_gt=False)
-    _bf16_update(M, gmaps, sc, 3e-2, 6e-3, 0.99, 9)
+    _bf16_update(M, gmaps, sc, 2e-2, 5e-3, 0.99, 9)
 
 
 def test_bf16_update_hierarchical(M, gmaps):
