@@ -39,28 +39,6 @@
 #include "internal.cuh"
 #include "tc_ptx.cuh"
 
-#ifdef MCL_TC_TRACE
-// Timeline instrumentation of CTA 0 (compiled only with -DMCL_TC_TRACE):
-// globaltimer stamps of the MMA issuer, the first row of each tile's
-// epilogue and the TMA producer for the first two tile pairs.
-constexpr int kTraceSlots = 16, kTraceLen = 128;
-__device__ unsigned long long g_tc_trace[kTraceSlots * kTraceLen];
-#define TC_TRACE_CTA(cta, slot, idx)                                                  \
-    do {                                                                              \
-        if (blockIdx.x == (cta) && (slot) < kTraceSlots && (idx) < kTraceLen)         \
-            g_tc_trace[(slot) * kTraceLen + (idx)] = mcl::tc::globaltimer();          \
-    } while (0)
-#define TC_TRACE(slot, idx) TC_TRACE_CTA(0, slot, idx)
-extern "C" int mcl_tc_trace_read(unsigned long long* out, int n) {
-    const int m = n < kTraceSlots * kTraceLen ? n : kTraceSlots * kTraceLen;
-    return (int)cudaMemcpyFromSymbol(out, g_tc_trace, sizeof(unsigned long long) * m);
-}
-#else
-#define TC_TRACE_CTA(cta, slot, idx) \
-    do {                             \
-    } while (0)
-#define TC_TRACE(slot, idx) TC_TRACE_CTA(0, slot, idx)
-#endif
 
 namespace mcl {
 
@@ -612,8 +590,6 @@ __device__ __forceinline__ void epilogue_warps(const Params& p, int warp, int wa
     const uint32_t bar_acc = slot ? bar_acc1 : bar_acc0;
     uint32_t acc_ph = 0;
     bool ok = true;
-    const bool tracer = (r == 0 && h0 == 0);
-    int tl = 0;
     // fused ray epilogue of a finished unit, run by the row-owning warps
     // (h0 == 0) after the next unit's prologue, while its first MMAs run
     EpiSync es{slot ? bar_epi1 : bar_epi0, 0u, abort_flag, p.wait_ns};
@@ -698,7 +674,7 @@ __device__ __forceinline__ void epilogue_warps(const Params& p, int warp, int wa
         }
         float sigma = 0.0f;
         float4 res = make_float4(0.f, 0.f, 0.f, 0.f);
-        for (int l = 0; l < kLayers && ok; ++l, ++tl) {
+        for (int l = 0; l < kLayers && ok; ++l) {
             const bool got = PAIR ? mbar_wait_cluster<true>(bar_acc, acc_ph, abort_flag)
                                   : mbar_wait_sleep(bar_acc, acc_ph, abort_flag, p.wait_ns);
             if (!got) {
@@ -709,7 +685,6 @@ __device__ __forceinline__ void epilogue_warps(const Params& p, int warp, int wa
                 ok = false;
                 break;
             }
-            if (tracer) TC_TRACE(6 + 2 * slot, tl);
             acc_ph ^= 1u;
             tc_fence_after();
             if (l < 8) {
@@ -754,7 +729,6 @@ __device__ __forceinline__ void epilogue_warps(const Params& p, int warp, int wa
                         }
                     }
                 }
-                if (tracer) TC_TRACE(7 + 2 * slot, tl);
                 signal_ready<PAIR>(bar_ready, lane);
             } else if (h0 == 0) {
                 const float4* rb4 = reinterpret_cast<const float4*>(p.ray_bias + ray * 128);
@@ -874,12 +848,10 @@ __global__ void __launch_bounds__(Variant<F8, EPIW, STAG>::kThreads, 1)
             for (long long pr = blockIdx.x; pr < n_pairs && ok; pr += gridDim.x) {
                 for (int b = 0; b < Fm::kBlocks; ++b, ++g) {
                     const uint32_t st = g % kStages, ph = (g / kStages) & 1u;
-                    TC_TRACE(0, g);
                     if (!mbar_wait(smem_u32(&bars.empty[st]), ph ^ 1u, abort_flag, p.wait_ns)) {
                         ok = false;
                         break;
                     }
-                    TC_TRACE(1, g);
                     mbar_arrive_expect_tx(smem_u32(&bars.full[st]), kStageBytes);
                     bulk_load(s_ring + st * kStageBytes, p.wblocks + (size_t)b * kStageBytes,
                               kStageBytes, smem_u32(&bars.full[st]));
@@ -902,7 +874,6 @@ __global__ void __launch_bounds__(Variant<F8, EPIW, STAG>::kThreads, 1)
         bool ok = true;
         const uint32_t id256 = F8 ? idesc_e4m3(128, 256) : idesc_bf16(128, 256);
         const uint32_t id144 = F8 ? idesc_e4m3(128, 144) : idesc_bf16(128, 144);
-        int tl = 0;
         // Operand descriptors: the bases are built once; an operand at byte
         // offset o from a base is base + o / 16 (the 14-bit start-address
         // field does not overflow: all of shared memory is below 256 KB), so
@@ -934,10 +905,9 @@ __global__ void __launch_bounds__(Variant<F8, EPIW, STAG>::kThreads, 1)
         };
         auto gate = [&]() -> bool { return !named_bar_or(1, 64, false); };
         for (long long pr = blockIdx.x; pr < n_pairs && ok; pr += gridDim.x) {
-            for (int l = 0; l < kLayers && ok; ++l, ++tl) {
+            for (int l = 0; l < kLayers && ok; ++l) {
                 const int nch = c_chunks[F8 ? 1 : 0][l];
                 const uint32_t idesc = (l == 8) ? id144 : id256;
-                if (lane == 0) TC_TRACE(2, tl);
                 if constexpr (STAG) {
                     // Staggered tiles: all of layer l for tile 0, then all of
                     // it for tile 1 from the same resident weight blocks (a
@@ -996,7 +966,6 @@ __global__ void __launch_bounds__(Variant<F8, EPIW, STAG>::kThreads, 1)
                         }
                     }
                 }
-                if (lane == 0) TC_TRACE(5, tl);
             }
         }
         if (lane == 0) {
@@ -1013,18 +982,14 @@ __global__ void __launch_bounds__(Variant<F8, EPIW, STAG>::kThreads, 1)
         uint32_t g = 0;
         uint32_t rdy_ph[2] = {0, 0};
         bool ok = true;
-        int tl = 0;
         auto wait_ready = [&](int s) -> bool {
             const bool r = mbar_wait(smem_u32(&bars.a_ready[s]), rdy_ph[s], abort_flag, p.wait_ns);
             rdy_ph[s] ^= 1u;
-            if (lane == 0) TC_TRACE(3 + s, tl);
             return r;
         };
         auto wait_block = [&](uint32_t gi) -> bool {
-            if (lane == 0) TC_TRACE(15, gi);
             const bool r = mbar_wait(smem_u32(&bars.full[gi % kStages]), (gi / kStages) & 1u, abort_flag,
                                      p.wait_ns);
-            if (lane == 0) TC_TRACE(13, gi);
             return r;
         };
         auto release = [&](bool good) -> bool {
@@ -1032,7 +997,7 @@ __global__ void __launch_bounds__(Variant<F8, EPIW, STAG>::kThreads, 1)
             return !named_bar_or(1, 64, !good);
         };
         for (long long pr = blockIdx.x; pr < n_pairs && ok; pr += gridDim.x) {
-            for (int l = 0; l < kLayers && ok; ++l, ++tl) {
+            for (int l = 0; l < kLayers && ok; ++l) {
                 const int nch = c_chunks[F8 ? 1 : 0][l];
                 if constexpr (STAG) {
                     for (int c = 0; c < nch; ++c) {
@@ -1158,13 +1123,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kPairThreads, 1)
             for (long long u = u0; u < n_units && ok; u += du) {
                 for (int b = 0; b < Fm::kBlocks; ++b, ++g) {
                     const uint32_t st = g % kStages, ph = (g / kStages) & 1u;
-                    TC_TRACE(0, g);
                     if (!mbar_wait_cluster<false>(smem_u32(&bars.empty[st]), ph ^ 1u, abort_flag)) {
                         ok = false;
                         break;
                     }
-                    TC_TRACE(1, g);
-                    TC_TRACE_CTA(1, 11, g);
                     const uint32_t bytes = b >= kLastBlock0 ? Pf::kHalfLast : Pf::kHalf;
                     mbar_arrive_expect_tx(smem_u32(&bars.full[st]), bytes);
                     bulk_load(s_ring + st * Pf::kHalf, p.wblocks + (size_t)b * kStageBytes + rank * bytes,
@@ -1191,7 +1153,6 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kPairThreads, 1)
                         ok = false;
                         break;
                     }
-                    TC_TRACE_CTA(1, 10, g);
                     mbar_arrive_cluster(mapa_shared(smem_u32(&bars.pfull[st]), 0));
                 }
             if (!ok) record_abort(p);
@@ -1206,7 +1167,6 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kPairThreads, 1)
         const uint32_t id256 = F8 ? idesc_e4m3(256, 256) : idesc_bf16(256, 256);
         const uint32_t id144 = F8 ? idesc_e4m3(256, 144) : idesc_bf16(256, 144);
         constexpr uint16_t kBoth = 3;
-        int tl = 0;
         const uint64_t d_act[2] = {smem_desc(s_act, 1024, kLayoutSw128),
                                    smem_desc(s_act + kActBytes, 1024, kLayoutSw128)};
         const uint64_t d_gx[2] = {smem_desc(s_gx, 1024, kLayoutSw128),
@@ -1231,10 +1191,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kPairThreads, 1)
         };
         auto gate = [&]() -> bool { return !named_bar_or(1, 64, false); };
         for (long long u = u0; u < n_units && ok; u += du) {
-            for (int l = 0; l < kLayers && ok; ++l, ++tl) {
+            for (int l = 0; l < kLayers && ok; ++l) {
                 const int nch = c_chunks[F8 ? 1 : 0][l];
                 const uint32_t idesc = (l == 8) ? id144 : id256;
-                if (lane == 0) TC_TRACE(2, tl);
                 if constexpr (STAG) {
                     for (int c = 0; c < nch; ++c) {
                         if (!gate()) { ok = false; break; }
@@ -1285,7 +1244,6 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kPairThreads, 1)
                         }
                     }
                 }
-                if (lane == 0) TC_TRACE(5, tl);
             }
         }
         if (lane == 0) {
@@ -1302,21 +1260,16 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kPairThreads, 1)
             uint32_t g = 0;
             uint32_t rdy_ph[2] = {0, 0};
             bool ok = true;
-            int tl = 0;
             auto wait_ready = [&](int s) -> bool {
                 const bool r = mbar_wait_cluster<false>(smem_u32(&bars.a_ready[s]), rdy_ph[s], abort_flag);
                 rdy_ph[s] ^= 1u;
-                if (lane == 0) TC_TRACE(3 + s, tl);
                 return r;
             };
             // block gi present in both CTAs
             auto wait_block = [&](uint32_t gi) -> bool {
                 const uint32_t st = gi % kStages, ph = (gi / kStages) & 1u;
-                if (lane == 0) TC_TRACE(15, gi);
                 const bool r = mbar_wait(smem_u32(&bars.full[st]), ph, abort_flag);
-                if (lane == 0) TC_TRACE(12, gi);
                 const bool r2 = r && mbar_wait_cluster<false>(smem_u32(&bars.pfull[st]), ph, abort_flag);
-                if (lane == 0) TC_TRACE(13, gi);
                 return r2;
             };
             auto release = [&](bool good) -> bool {
@@ -1324,7 +1277,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kPairThreads, 1)
                 return !named_bar_or(1, 64, !good);
             };
             for (long long u = u0; u < n_units && ok; u += du) {
-                for (int l = 0; l < kLayers && ok; ++l, ++tl) {
+                for (int l = 0; l < kLayers && ok; ++l) {
                     const int nch = c_chunks[F8 ? 1 : 0][l];
                     if constexpr (STAG) {
                         for (int c = 0; c < nch; ++c) {
