@@ -543,14 +543,14 @@ EXPORTED = ("mcl_init_map", "mcl_destroy_map", "mcl_update", "mcl_render", "mcl_
 
 # Kernel variants of the tensor-core MLP (include/mcl.h, MCL_MLP_VARIANTS):
 # (precision, epilogue warps per tile, staggered tiles)
-MLP_VARIANTS = 11
+MLP_VARIANTS = 12
 # index: (precision, epilogue warps per tile, schedule)
 MLP_VARIANT_TABLE = {0: ("bf16", 4, "lockstep"), 1: ("bf16", 8, "lockstep"),
                      2: ("fp8", 4, "lockstep"), 3: ("fp8", 8, "lockstep"),
                      4: ("fp8", 4, "staggered"), 5: ("fp8", 8, "staggered"),
                      6: ("bf16", 4, "split"), 7: ("bf16", 4, "pipelined"),
                      8: ("bf16", 4, "lockstep pair"), 9: ("fp8", 4, "lockstep pair"),
-                     10: ("fp8", 4, "staggered pair")}
+                     10: ("fp8", 4, "staggered pair"), 11: ("bf16", 4, "staggered")}
 
 # Weights of the learned proposal (gamma(x) with 6 frequencies -> 4 x 64 ReLU
 # -> density): 64*39+64 + 3*(64*64+64) + 64+1.

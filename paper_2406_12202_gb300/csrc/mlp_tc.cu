@@ -69,13 +69,14 @@ static_assert(Form<false>::kSmemBytes <= 232448 && Form<true>::kSmemBytes <= 232
 // Kernel variant: operand form, epilogue warps per tile (4: one per TMEM lane
 // quadrant, each thread a whole row; 8: two per quadrant, each thread half a
 // row), and the tile schedule (lockstep: each weight block serves both
-// tiles at once; staggered: tile 1 runs a layer after tile 0 on the
-// resident blocks, so each tile's epilogue overlaps the other's MMAs; needs
-// a whole layer in the ring, i.e. FP8).  The autotuner picks among them.
+// tiles at once; staggered: tile 1 runs a layer after tile 0, so each tile's
+// epilogue overlaps the other's MMAs -- FP8 keeps the layer's blocks resident
+// in its 8-stage ring for tile 1, BF16 (whose layer does not fit in its
+// 4-stage ring) streams every block twice, once per tile).  The autotuner
+// picks among them.
 template <bool F8, int EPIW, bool STAG>
 struct Variant {
     static_assert(EPIW == 4 || EPIW == 8, "epilogue warps");
-    static_assert(!STAG || F8, "a BF16 layer does not fit in the weight ring");
     static constexpr int kEpiThreads = 32 * EPIW;
     static constexpr int kThreads = 96 + 2 * kEpiThreads;   // + TMA, MMA and gate warps
 };
@@ -87,6 +88,8 @@ struct Variant {
 // column 128 of the last MMA.
 __constant__ int c_chunks[2][kLayers] = {{2, 8, 8, 8, 8, 10, 8, 8, 8},
                                          {1, 4, 4, 4, 4, 5, 4, 4, 4}};
+// first weight block of each layer (BF16 form), for the re-streamed schedule
+__constant__ int c_block0_bf16[kLayers] = {0, 2, 10, 18, 26, 34, 44, 52, 60};
 
 struct Params {
     const uint8_t* wblocks; // weight blocks of the form, pre-swizzled, in consumption order
@@ -845,16 +848,24 @@ __global__ void __launch_bounds__(Variant<F8, EPIW, STAG>::kThreads, 1)
         if (lane == 0 && !p.hold_weights) {
             uint32_t g = 0;
             bool ok = true;
+            auto stream = [&](int b) -> bool {
+                const uint32_t st = g % kStages, ph = (g / kStages) & 1u;
+                if (!mbar_wait(smem_u32(&bars.empty[st]), ph ^ 1u, abort_flag, p.wait_ns)) return false;
+                mbar_arrive_expect_tx(smem_u32(&bars.full[st]), kStageBytes);
+                bulk_load(s_ring + st * kStageBytes, p.wblocks + (size_t)b * kStageBytes, kStageBytes,
+                          smem_u32(&bars.full[st]));
+                ++g;
+                return true;
+            };
             for (long long pr = blockIdx.x; pr < n_pairs && ok; pr += gridDim.x) {
-                for (int b = 0; b < Fm::kBlocks; ++b, ++g) {
-                    const uint32_t st = g % kStages, ph = (g / kStages) & 1u;
-                    if (!mbar_wait(smem_u32(&bars.empty[st]), ph ^ 1u, abort_flag, p.wait_ns)) {
-                        ok = false;
-                        break;
-                    }
-                    mbar_arrive_expect_tx(smem_u32(&bars.full[st]), kStageBytes);
-                    bulk_load(s_ring + st * kStageBytes, p.wblocks + (size_t)b * kStageBytes,
-                              kStageBytes, smem_u32(&bars.full[st]));
+                if constexpr (STAG && !F8) {
+                    // each layer's blocks twice: for tile 0, then for tile 1
+                    for (int l = 0; l < kLayers && ok; ++l)
+                        for (int t = 0; t < 2 && ok; ++t)
+                            for (int c = 0; c < c_chunks[0][l] && ok; ++c)
+                                ok = stream(c_block0_bf16[l] + c);
+                } else {
+                    for (int b = 0; b < Fm::kBlocks && ok; ++b) ok = stream(b);
                 }
             }
             if (!ok) record_abort(p);
@@ -908,7 +919,23 @@ __global__ void __launch_bounds__(Variant<F8, EPIW, STAG>::kThreads, 1)
             for (int l = 0; l < kLayers && ok; ++l) {
                 const int nch = c_chunks[F8 ? 1 : 0][l];
                 const uint32_t idesc = (l == 8) ? id144 : id256;
-                if constexpr (STAG) {
+                if constexpr (STAG && !F8) {
+                    // Staggered tiles, BF16: all of layer l for tile 0, then
+                    // all of it for tile 1, each from its own stream of the
+                    // layer's blocks; a stage is released after its MMAs.
+                    for (int t = 0; t < 2 && ok; ++t)
+                        for (int c = 0; c < nch; ++c, ++g) {
+                            if (!gate()) { ok = false; break; }
+                            if (lane == 0) {
+                                tc_fence_after();
+                                const uint32_t st = g % kStages;
+                                issue(l, t, c, st, idesc);
+                                mma_commit(smem_u32(&bars.empty[st]));
+                                if (c == nch - 1) mma_commit(smem_u32(&bars.acc_full[t]));
+                            }
+                            __syncwarp();
+                        }
+                } else if constexpr (STAG) {
                     // Staggered tiles: all of layer l for tile 0, then all of
                     // it for tile 1 from the same resident weight blocks (a
                     // layer is at most 5 of the 8 stages), so tile 0's
@@ -999,7 +1026,15 @@ __global__ void __launch_bounds__(Variant<F8, EPIW, STAG>::kThreads, 1)
         for (long long pr = blockIdx.x; pr < n_pairs && ok; pr += gridDim.x) {
             for (int l = 0; l < kLayers && ok; ++l) {
                 const int nch = c_chunks[F8 ? 1 : 0][l];
-                if constexpr (STAG) {
+                if constexpr (STAG && !F8) {
+                    for (int t = 0; t < 2 && ok; ++t)
+                        for (int c = 0; c < nch; ++c, ++g) {
+                            bool good = true;
+                            if (c == 0) good = wait_ready(t);
+                            good = good && wait_block(g);
+                            if (!release(good)) { ok = false; break; }
+                        }
+                } else if constexpr (STAG) {
                     for (int c = 0; c < nch; ++c) {
                         bool good = true;
                         if (c == 0) good = wait_ready(0);
@@ -1855,7 +1890,7 @@ const TcVariant kVariants[] = {
     TcVariant{MCL_PREC_BF16, 4, true, &k_mlp_tc_split, kSplitThreads, kSplitSmem, 1},
     TcVariant{MCL_PREC_BF16, 4, false, &k_mlp_tc_pipe, kPipeThreads, kPipeSmem, 1},
     make_pair_variant<false, false>(), make_pair_variant<true, false>(),
-    make_pair_variant<true, true>(),
+    make_pair_variant<true, true>(),     make_variant<false, 4, true>(),
 };
 // Fused passes (Params::fuse 1, 2) run on the single-CTA kernel with 4
 // epilogue warps per tile, in lockstep (BF16) or staggered (FP8): the

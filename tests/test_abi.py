@@ -46,9 +46,16 @@ def test_binding_lists_every_declared_symbol():
 
 
 def test_last_error_without_gpu(built_lib):
-    lib = ctypes.CDLL(built_lib)
-    lib.mcl_last_error.restype = ctypes.c_char_p
-    assert lib.mcl_last_error() == b""
+    """A fresh process starts with an empty error message (checked in a
+    child process: the message is per thread and earlier tests in this one
+    may have set it)."""
+    import subprocess
+    import sys
+    code = ("import ctypes, sys; lib = ctypes.CDLL(sys.argv[1]); "
+            "lib.mcl_last_error.restype = ctypes.c_char_p; print(repr(lib.mcl_last_error()))")
+    out = subprocess.run([sys.executable, "-c", code, built_lib], capture_output=True, text=True,
+                         check=True).stdout.strip()
+    assert out == "b''"
 
 
 def header_defines():
