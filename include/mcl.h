@@ -366,6 +366,47 @@ int mcl_proposal_train(mcl_map* map, const float* d_poses, int n_poses,
                        const mcl_train_cfg* cfg, float* d_loss_log,
                        void* stream);
 
+/* ---- fitting the map to samples of a field (a project extension) ---------
+ * The paper takes the NeRF map as given (trained on images, Eq. 2, out of
+ * scope here).  These entry points fit the map's FP32 weights to point
+ * samples of a field instead -- points d_x [n,3], view directions d_dir
+ * [n,3] (normalised here) and targets d_target [n,4] = (density, r, g, b) --
+ * by minimising the mean of
+ *   sigma_weight (sigma_raw(x) - density)^2 + |rgb(x, d) - (r, g, b)|^2
+ * with the library's own FP32 forward (the plain form's kernels, every
+ * layer's output kept), backward (SGEMMs on transposed weights with the
+ * ReLU masks) and Adam.  Weight gradients are summed over each batch in a
+ * fixed order, so the same inputs give the same weights. */
+typedef struct {
+    int steps;            /* Adam steps                                      */
+    int batch;            /* points per step (the last epoch's tail is cut) */
+    float lr, beta1, beta2, eps;
+    float lr_end;         /* geometric decay from lr to lr_end (<= 0: none) */
+    float sigma_weight;   /* weight of the density term                     */
+    uint64_t seed;        /* shuffling of the points                        */
+} mcl_fit_cfg;
+
+/* Fit the map (starting from its current weights) with cfg->steps Adam
+ * steps on shuffled batches; d_loss_log (optional, device [steps]) receives
+ * each step's batch loss.  The tensor-core forms are rebuilt from the fitted
+ * weights (their calibration and kernel-variant choices start afresh, and a
+ * captured mcl_localize graph is dropped).  Synchronous; allocates and frees
+ * its training scratch (about 8.5 KB per point of a batch).  1 <= batch,
+ * 1 <= n, 1 <= steps. */
+int mcl_fit_map(mcl_map* map, const float* d_x, const float* d_dir, const float* d_target, int n,
+                const mcl_fit_cfg* cfg, float* d_loss_log, void* stream);
+
+/* The fitting loss of n points (mean, into *d_loss, device double) and its
+ * gradient with respect to the weights in the blob layout of mcl_init_map
+ * (d_grad: device, as many floats as the blob).  Synchronous; allocates its
+ * scratch. */
+int mcl_map_loss_grad(mcl_map* map, const float* d_x, const float* d_dir, const float* d_target,
+                      int n, float sigma_weight, double* d_loss, float* d_grad, void* stream);
+
+/* Copy the map's FP32 weights, in the blob layout of mcl_init_map, into
+ * host_out (n floats, the blob size).  Synchronous. */
+int mcl_get_map_weights(mcl_map* map, float* host_out, size_t n);
+
 /* Kernel variants of the tensor-core MLP (index: precision, epilogue warps
  * per 128-row tile, tile schedule):
  *   0 BF16 4 lockstep   1 BF16 8 lockstep   2 FP8 4 lockstep

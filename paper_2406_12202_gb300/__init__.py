@@ -97,6 +97,12 @@ class TrainCfg(C.Structure):
                 ("eps", C.c_float), ("seed", C.c_uint64), ("lr_end", C.c_float)]
 
 
+class FitCfg(C.Structure):
+    _fields_ = [("steps", C.c_int), ("batch", C.c_int), ("lr", C.c_float), ("beta1", C.c_float),
+                ("beta2", C.c_float), ("eps", C.c_float), ("lr_end", C.c_float),
+                ("sigma_weight", C.c_float), ("seed", C.c_uint64)]
+
+
 class Debug(C.Structure):
     _fields_ = [(n, C.c_void_p) for n in ("rgb", "E", "F", "z_trans", "z_opaque", "S")]
 
@@ -152,6 +158,9 @@ def lib():
             L.mcl_set_mlp_variant.argtypes = [vp, i32, i32]
             L.mcl_inject_weight_stall.argtypes = [vp, i32, f64]
             L.mcl_set_fused_epilogue.argtypes = [vp, i32]
+            L.mcl_fit_map.argtypes = [vp, vp, vp, vp, i32, C.POINTER(FitCfg), vp, vp]
+            L.mcl_map_loss_grad.argtypes = [vp, vp, vp, vp, i32, f32, vp, vp, vp]
+            L.mcl_get_map_weights.argtypes = [vp, vp, C.c_size_t]
             L.mcl_last_error.restype = C.c_char_p
             L.mcl_last_error.argtypes = []
             _lib = L
@@ -161,6 +170,19 @@ def lib():
 def _check(rc):
     if rc != MCL_OK:
         raise MclError(rc, lib().mcl_last_error().decode())
+
+
+def synth_blob_size(arch) -> int:
+    """Floats of a weight blob of architecture arch (the layer table of
+    mcl_init_map)."""
+    gx, gd = 3 + 6 * arch.n_freq_xyz, 3 + 6 * arch.n_freq_dir
+    D, W, skip, Wr = arch.trunk_depth, arch.trunk_width, arch.skip_layer, arch.rgb_width
+    n = 0
+    for l in range(1, D + 1):
+        fi = gx if l == 1 else (W + gx if l == skip + 1 else W)
+        n += fi * W + W
+    n += W + 1 + W * W + W + (W + gd) * Wr + Wr + Wr * 3 + 3
+    return n
 
 
 def _torch():
@@ -439,6 +461,42 @@ class Map:
                                   _stream()))
         return ch.value, {i: float(ms[i]) for i in range(MLP_VARIANTS) if ms[i] >= 0}
 
+    # ------------------------------------------------------------ map fitting
+    def fit(self, x, dirs, target, steps=2000, batch=16384, lr=1e-3, lr_end=1e-4, beta1=0.9,
+            beta2=0.999, eps=1e-8, sigma_weight=1e-2, seed=0):
+        """Fit the map's weights to field samples (mcl_fit_map): points x
+        [n,3], view directions dirs [n,3], targets [n,4] (density, r, g, b),
+        CUDA f32 tensors.  Returns the per-step batch losses [steps]."""
+        torch = _torch()
+        n = x.shape[0]
+        log = torch.empty(steps, dtype=torch.float32, device=x.device)
+        cfg = FitCfg(int(steps), int(batch), lr, beta1, beta2, eps, lr_end, sigma_weight, int(seed))
+        _check(lib().mcl_fit_map(self.handle, _ptr(x, torch.float32, (n, 3), "x"),
+                                 _ptr(dirs, torch.float32, (n, 3), "dirs"),
+                                 _ptr(target, torch.float32, (n, 4), "target"), n, C.byref(cfg),
+                                 log.data_ptr(), _stream()))
+        return log
+
+    def loss_grad(self, x, dirs, target, sigma_weight=1e-2):
+        """Fitting loss (mean) and its gradient in the blob layout
+        (mcl_map_loss_grad)."""
+        torch = _torch()
+        n = x.shape[0]
+        loss = torch.empty(1, dtype=torch.float64, device=x.device)
+        grad = torch.empty(synth_blob_size(self._arch), dtype=torch.float32, device=x.device)
+        _check(lib().mcl_map_loss_grad(self.handle, _ptr(x, torch.float32, (n, 3), "x"),
+                                       _ptr(dirs, torch.float32, (n, 3), "dirs"),
+                                       _ptr(target, torch.float32, (n, 4), "target"), n,
+                                       float(sigma_weight), loss.data_ptr(), grad.data_ptr(),
+                                       _stream()))
+        return float(loss.item()), grad
+
+    def weights(self) -> np.ndarray:
+        """The map's FP32 weights in the blob layout (mcl_get_map_weights)."""
+        w = np.zeros(synth_blob_size(self._arch), dtype=np.float32)
+        _check(lib().mcl_get_map_weights(self.handle, w.ctypes.data, w.size))
+        return w
+
     def set_fused_epilogue(self, enable: bool):
         """Fused ray epilogues of the tensor-core forms on / off
         (mcl_set_fused_epilogue; on by default)."""
@@ -539,7 +597,8 @@ EXPORTED = ("mcl_init_map", "mcl_destroy_map", "mcl_update", "mcl_render", "mcl_
             "mcl_proposal_set", "mcl_proposal_get", "mcl_render_histogram",
             "mcl_proposal_loss_grad", "mcl_proposal_train", "mcl_proposal_query", "mcl_autotune",
             "mcl_predict_odom",
-            "mcl_set_mlp_variant", "mcl_inject_weight_stall", "mcl_set_fused_epilogue")
+            "mcl_set_mlp_variant", "mcl_inject_weight_stall", "mcl_set_fused_epilogue",
+            "mcl_fit_map", "mcl_map_loss_grad", "mcl_get_map_weights")
 
 # Kernel variants of the tensor-core MLP (include/mcl.h, MCL_MLP_VARIANTS):
 # (precision, epilogue warps per tile, staggered tiles)

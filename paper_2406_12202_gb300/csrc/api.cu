@@ -80,6 +80,8 @@ static void layer_shapes(int* fin, int* fout) {
     fin[11] = kRgbW; fout[11] = 3;
 }
 
+void blob_layer_shapes(int* fin, int* fout) { layer_shapes(fin, fout); }
+
 static size_t blob_size() {
     int fin[12], fout[12];
     layer_shapes(fin, fout);
@@ -173,6 +175,7 @@ extern "C" int mcl_init_map(const float* host_weights, size_t n_floats, const mc
         free_map(m);
         return rc;
     }
+    m->w32_n = tot;
     for (int l = 0; l < 12; ++l) {
         m->L[l].W = m->w32 + offW[l];
         m->L[l].b = m->w32 + offB[l];
@@ -810,6 +813,46 @@ extern "C" int mcl_set_fused_epilogue(mcl_map* m, int enable) {
     m->fuse_epilogue = enable != 0;
     m->loop.key = 0;   // a captured loop holds the old launch sequence
     return MCL_OK;
+}
+
+extern "C" int mcl_fit_map(mcl_map* m, const float* d_x, const float* d_dir, const float* d_target,
+                           int n, const mcl_fit_cfg* cfg, float* d_loss_log, void* stream) {
+    g_err[0] = 0;
+    if (!m || !d_x || !d_dir || !d_target || !cfg || n < 1)
+        return fail(MCL_ERR_ARG, "mcl_fit_map: bad argument");
+    if (cfg->steps < 1 || cfg->batch < 1 || !(cfg->lr > 0.f) || !(cfg->beta1 >= 0.f && cfg->beta1 < 1.f) ||
+        !(cfg->beta2 >= 0.f && cfg->beta2 < 1.f) || !(cfg->eps > 0.f) || !(cfg->sigma_weight >= 0.f))
+        return fail(MCL_ERR_ARG, "mcl_fit_map: bad fitting configuration");
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc;
+    if ((rc = fit_map(m, d_x, d_dir, d_target, n, *cfg, d_loss_log, s))) return rc;
+    // rebuild the tensor-core forms from the fitted weights
+    std::vector<float> blob(blob_size());
+    if ((rc = map_download(m, blob.data()))) return rc;
+    if (m->loop.exec) {
+        cudaGraphExecDestroy(m->loop.exec);
+        m->loop.exec = nullptr;
+    }
+    m->loop.key = 0;
+    mlp_tc_free(m);
+    if ((rc = mlp_tc_prepare(m, blob.data()))) return rc;
+    return cuda_check(cudaDeviceSynchronize(), "mcl_fit_map");
+}
+
+extern "C" int mcl_map_loss_grad(mcl_map* m, const float* d_x, const float* d_dir,
+                                 const float* d_target, int n, float sigma_weight, double* d_loss,
+                                 float* d_grad, void* stream) {
+    g_err[0] = 0;
+    if (!m || !d_x || !d_dir || !d_target || !d_loss || !d_grad || n < 1 || !(sigma_weight >= 0.f))
+        return fail(MCL_ERR_ARG, "mcl_map_loss_grad: bad argument");
+    return map_loss_grad(m, d_x, d_dir, d_target, n, sigma_weight, d_loss, d_grad, (cudaStream_t)stream);
+}
+
+extern "C" int mcl_get_map_weights(mcl_map* m, float* host_out, size_t n) {
+    g_err[0] = 0;
+    if (!m || !host_out || n != blob_size())
+        return fail(MCL_ERR_ARG, "mcl_get_map_weights: need %zu floats", blob_size());
+    return map_download(m, host_out);
 }
 
 extern "C" int mcl_set_mlp_variant(mcl_map* m, int precision, int variant) {

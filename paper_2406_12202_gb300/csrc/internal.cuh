@@ -86,6 +86,7 @@ struct mcl_map {
     // FP32 padded layers: 0..7 trunk, 8 sigma(row vector), 9 feature,
     // 10 rgb_hidden ([feat | gamma(d) | 0]), 11 rgb_out.
     float* w32 = nullptr;
+    size_t w32_n = 0;               // floats of w32 (padded layers)
     mcl::LayerF32 L[12];
     // tensor-core path weights (filled by mlp_tc_prepare)
     void* tc_blob = nullptr;
@@ -168,6 +169,31 @@ cudaError_t launch_weights(const float* e_ray, int N, int B, const mcl_opts& o, 
 // rows_dev (optional): device-side row count (n_rays * S is the bound).
 cudaError_t mlp_fp32(mcl_map* m, const Ray* rays, const float* gd, const float* z, int S,
                      int n_rays, float4* out, cudaStream_t s, const int* rows_dev = nullptr);
+
+// mlp_fp32.cu building blocks reused by the map fitter (fit.cu): the FP32
+// GEMM C = act([A1 | A2] W^T + b) (W [n_out][K1 + K2], n_out a multiple of
+// 128, K1 and K2 multiples of 16), gamma(x) of points (rays with z = 0), and
+// the density / colour heads (h [n,256] -> out.x; hid [n,256-stride] -> out.yzw).
+cudaError_t fp32_gemm(const float* A1, int lda1, int K1, const float* A2, int lda2, int K2,
+                      long a2_off, int a2_div, const float* W, const float* bias, int n_out,
+                      float* C, int ldc, int M, bool relu, cudaStream_t s);
+cudaError_t fp32_pe(const Ray* rays, const float* z, int n, float* gx, cudaStream_t s);
+cudaError_t fp32_heads(const float* h, const LayerF32& sigma, const float* hid, const LayerF32& rgb,
+                       int n, float4* out, cudaStream_t s);
+
+// proposal.cu: one Adam step (bias corrections c1 = 1 - b1^t, c2 = 1 - b2^t).
+cudaError_t launch_adam(float* W, const float* g, float* m, float* v, int n, float lr, float b1,
+                        float b2, float eps, float c1, float c2, cudaStream_t s);
+
+// api.cu: fan-in and fan-out of the 12 layers in blob order.
+void blob_layer_shapes(int* fin, int* fout);
+
+// fit.cu
+int fit_map(mcl_map* m, const float* d_x, const float* d_dir, const float* d_target, int n,
+            const mcl_fit_cfg& cfg, float* d_loss_log, cudaStream_t s);
+int map_loss_grad(mcl_map* m, const float* d_x, const float* d_dir, const float* d_target, int n,
+                  float sigma_weight, double* d_loss, float* d_grad, cudaStream_t s);
+int map_download(mcl_map* m, float* host_blob);
 
 // mlp_tc.cu
 int mlp_tc_prepare(mcl_map* m, const float* host_blob);

@@ -196,6 +196,31 @@ __global__ void k_rgb_head(const float* __restrict__ h, int ldh, const float* __
 
 static cudaError_t gemm(const float* A1, int lda1, int K1, const float* A2, int lda2, int K2,
                         long a2_off, int a2_div, const LayerF32& L, float* C, int ldc, int M,
+                        bool relu, const int* rows_dev, long r0, cudaStream_t s);
+
+cudaError_t fp32_gemm(const float* A1, int lda1, int K1, const float* A2, int lda2, int K2,
+                      long a2_off, int a2_div, const float* W, const float* bias, int n_out,
+                      float* C, int ldc, int M, bool relu, cudaStream_t s) {
+    LayerF32 L{W, bias, n_out, K1 + K2};
+    return gemm(A1, lda1, K1, A2, lda2, K2, a2_off, a2_div, L, C, ldc, M, relu, nullptr, 0, s);
+}
+
+cudaError_t fp32_pe(const Ray* rays, const float* z, int n, float* gx, cudaStream_t s) {
+    note_launch();
+    k_pe_xyz<<<(n + 127) / 128, 128, 0, s>>>(rays, z, 1, 0, n, nullptr, gx);
+    return cudaGetLastError();
+}
+
+cudaError_t fp32_heads(const float* h, const LayerF32& sigma, const float* hid, const LayerF32& rgb,
+                       int n, float4* out, cudaStream_t s) {
+    note_launch(2);
+    k_sigma_head<<<(n * 32 + 255) / 256, 256, 0, s>>>(h, kWidth, sigma.W, sigma.b, n, nullptr, 0, out);
+    k_rgb_head<<<(n * 32 + 255) / 256, 256, 0, s>>>(hid, kWidth, rgb.W, rgb.b, n, nullptr, 0, out);
+    return cudaGetLastError();
+}
+
+static cudaError_t gemm(const float* A1, int lda1, int K1, const float* A2, int lda2, int K2,
+                        long a2_off, int a2_div, const LayerF32& L, float* C, int ldc, int M,
                         bool relu, const int* rows_dev, long r0, cudaStream_t s) {
     dim3 grid((M + 127) / 128, L.n / 128);
     note_launch();

@@ -313,6 +313,13 @@ __global__ void k_adam(float* __restrict__ W, const float* __restrict__ g, float
     W[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
 }
 
+cudaError_t launch_adam(float* W, const float* g, float* m, float* v, int n, float lr, float b1,
+                        float b2, float eps, float c1, float c2, cudaStream_t s) {
+    note_launch();
+    k_adam<<<(n + 255) / 256, 256, 0, s>>>(W, g, m, v, n, lr, b1, b2, eps, c1, c2);
+    return cudaGetLastError();
+}
+
 // Targets: final weights of the full sampler re-binned onto nb equal
 // intervals of [near, far] (interval floor((z - near)/(far - near) nb),
 // clamped), normalised (uniform for a ray without weight).

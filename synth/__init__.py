@@ -232,6 +232,47 @@ def proposal_init_weights(seed: int = 0, head_bias: float = 1.0) -> np.ndarray:
     return np.concatenate(parts).astype(np.float32)
 
 
+def room_field(x, seed: int = 0, half: float = 3.0, eps: float = 0.015625,
+               density: float = 64.0, n_tex_freq: int = 4):
+    """The field that room_map_weights(seed, half, eps, density, n_tex_freq)
+    represents, evaluated at points x [n, 3]: density * clamp((max_c |x_c| -
+    half) / eps, 0, 1) and sigmoid(a . f(x)) with f = sin / cos(2^k x_c) in
+    the map's feature order (FP64).  Samples of it are the targets for
+    fitting a map to the room.  Returns (density [n], rgb [n, 3])."""
+    x = np.asarray(x, dtype=np.float64)
+    _, a = room_map_weights(seed, half, eps, density, n_tex_freq)
+    a = a.astype(np.float32).astype(np.float64)
+    m = np.abs(x).max(-1)
+    sig = density * np.clip((m - half) / eps, 0.0, 1.0)
+    feats = []
+    for k in range(n_tex_freq):
+        for c in range(3):
+            v = (2.0 ** k) * x[..., c]
+            feats.append(np.sin(v))
+            feats.append(np.cos(v))
+    f = np.stack(feats, -1)
+    return sig, 1.0 / (1.0 + np.exp(-(f @ a.T)))
+
+
+def room_fit_points(seed: int, n: int, half: float = 3.0):
+    """Seeded sample points for fitting a map to the room: half uniform in
+    the box [-(half + 0.5), half + 0.5]^3 (free space and walls), half in the
+    shell of the walls (one coordinate at +-(half + U(-0.1, 0.3)), the others
+    uniform in [-half, half]); unit view directions.  Returns (x [n,3],
+    dirs [n,3]) float32."""
+    rng = np.random.Generator(np.random.PCG64(seed + 2750159))
+    n1 = n // 2
+    x1 = rng.uniform(-(half + 0.5), half + 0.5, size=(n1, 3))
+    x2 = rng.uniform(-half, half, size=(n - n1, 3))
+    axis = rng.integers(0, 3, size=n - n1)
+    sign = rng.choice([-1.0, 1.0], size=n - n1)
+    x2[np.arange(n - n1), axis] = sign * (half + rng.uniform(-0.1, 0.3, size=n - n1))
+    x = np.concatenate([x1, x2])
+    d = rng.normal(size=(n, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    return x.astype(np.float32), d.astype(np.float32)
+
+
 def room_proposal_weights(half: float = 3.0, eps: float = 0.015625,
                           density: float = 64.0) -> np.ndarray:
     """Hand-set proposal blob whose raw density is exactly the room map's

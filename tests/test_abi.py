@@ -91,7 +91,7 @@ def test_binding_constants_match_header():
 
 STRUCTS = {"Arch": "mcl_arch", "MapConfig": "mcl_map_config", "Intrinsics": "mcl_intrinsics",
            "Opts": "mcl_opts", "Debug": "mcl_debug", "Schedule": "mcl_schedule",
-           "IterRecord": "mcl_iter_record", "TrainCfg": "mcl_train_cfg"}
+           "IterRecord": "mcl_iter_record", "TrainCfg": "mcl_train_cfg", "FitCfg": "mcl_fit_cfg"}
 
 
 def test_struct_layouts_match_binding(tmp_path):
