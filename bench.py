@@ -503,6 +503,97 @@ def job_rate(dist, seconds, units, device="cpu"):
     return float(t.item()), float(u.item()), float(u.item()) / float(t.item())
 
 
+def _room_queries(M, Q, iters, N0, W=100, H=100, focal=138.9):
+    """The room-map localisation workload: the hand-set room map, Q seeded
+    ground truths (seeds 100..) with 100 x 100 observations rendered by its
+    FP32 form (64 + 128 samples), a three-level schedule (64 px per level,
+    N0 / N0/2 / N0/4 particles, iters/3 iterations per level) and seeded
+    initial particles over the global spread.  Returns (map, K, ground
+    truths, images, schedule, initial particles [Q, N0, 12])."""
+    import numpy as np
+    import torch
+    import synth
+    blob, _ = synth.room_map_weights(0)
+    gm = M.Map(blob, max_rays=Q * N0 * 64, max_samples=192, max_particles=Q * N0,
+               max_queries=Q)
+    K = M.intrinsics(focal, focal, W / 2, H / 2, W, H)
+    o32 = M.UpdateOptions(n_coarse=64, n_fine=128, precision="fp32")
+    allpx = np.stack(np.meshgrid(np.arange(W), np.arange(H), indexing="xy"), -1).reshape(-1, 2)
+    px_all = torch.tensor(allpx, dtype=torch.int32, device="cuda")
+    gts, imgs = [], []
+    for q in range(Q):
+        g = synth.gt_pose(100 + q)
+        gts.append(g)
+        imgs.append(gm.render(torch.tensor(g[0][None], dtype=torch.float32, device="cuda"), K, 2,
+                              px_all, o32).reshape(H, W, 3).contiguous())
+    sch = M.schedule([0, 1, 2], [64, 64, 64], [N0, N0 // 2, N0 // 4], n_min=100,
+                     iter_caps=[iters // 3] * 3, refine=[0.02, 0.005, 0.0], iterations=iters,
+                     sigma_t=0.02, sigma_yaw=0.02)
+    parts0 = torch.tensor(np.stack([synth.random_particles(200 + q, N0)[0] for q in range(Q)]),
+                          dtype=torch.float32, device="cuda")
+    return gm, K, gts, imgs, sch, parts0
+
+
+def _localise(M, gm, parts0, imgs, K, sch, opts, gts, Q, iters):
+    """One device-loop run; per-query (position, yaw-degree) errors and the
+    accuracy / median summary of the final estimates."""
+    import numpy as np
+    N0 = parts0.shape[1]
+    log, _ = gm.localize(parts0.clone(), [N0] * Q, imgs, K, sch, opts, use_graph=True)
+    recs = M.Map.decode_log(log, Q, iters)
+    errs = [_pose_error(recs[q][-1]["est"], gts[q][1], gts[q][2]) for q in range(Q)]
+    return {"position_error_median": float(np.median([e[0] for e in errs])),
+            "yaw_error_deg_median": float(np.median([e[1] for e in errs])),
+            "accuracy_5cm_5deg": sum(e[0] < 0.05 and e[1] < 5.0 for e in errs) / Q,
+            "position_errors": [float(e[0]) for e in errs]}
+
+
+def run_fitted_map(M, Q=10, iters=45, n_points=1 << 20, steps=3000, batch=16384):
+    """A map fitted by the library's own backward kernels (mcl_fit_map) to
+    the room field, from He-init weights: n_points seeded samples (half
+    uniform in the box, half in the wall shell) with their closed-form
+    density and colour, `steps` Adam steps of `batch` points, the rate
+    decaying 1e-3 -> 1e-4.  Reported: fit time per step and points/s
+    (forward + backward + Adam), the loss, the fitted map's FP32 render
+    error against the hand-set map on 64 poses x 64 px, and localisation of
+    the equal-pose-error queries by the BF16 form with the fitted map and
+    with the hand-set map (observations from the hand-set map)."""
+    import numpy as np
+    import torch
+    import synth
+    N0 = 1500
+    hs, K, gts, imgs, sch, parts0 = _room_queries(M, Q, iters, N0)
+    x, d = synth.room_fit_points(1, n_points)
+    sig, rgb = synth.room_field(x)
+    tgt = np.concatenate([sig[:, None], rgb], 1).astype(np.float32)
+    xt, dt, tt = (torch.tensor(a, device="cuda") for a in (x, d, tgt))
+    fm = M.Map(synth.he_init_weights(0), max_rays=Q * N0 * 64, max_samples=192,
+               max_particles=Q * N0, max_queries=Q)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    lg = fm.fit(xt, dt, tt, steps=steps, batch=batch, lr=1e-3, lr_end=1e-4, sigma_weight=1e-2,
+                seed=3).cpu().numpy()
+    fit_s = time.perf_counter() - t0
+    o32 = M.UpdateOptions(n_coarse=64, n_fine=128, precision="fp32")
+    P = torch.tensor(synth.random_particles(5, 64)[0], dtype=torch.float32, device="cuda")
+    px = torch.tensor(synth.pixel_set(5, 25, 25, 64), dtype=torch.int32, device="cuda")
+    e = (fm.render(P, K, 0, px, o32) - hs.render(P, K, 0, px, o32)).abs().cpu().numpy()
+    ob = M.UpdateOptions(n_coarse=64, n_fine=32, precision="bf16", seed=1)
+    out = {"workload": f"room field, {n_points} samples, {steps} Adam steps x {batch} points from "
+                       f"He init; localisation as equal_pose_error ({Q} queries, BF16 64+32)",
+           "fit_ms_per_step": 1e3 * fit_s / steps,
+           "fit_points_per_s": steps * batch / fit_s,
+           "loss_first_20": float(lg[:20].mean()), "loss_last_100": float(lg[-100:].mean()),
+           "render_err_vs_handset_fp32": {"mean": float(e.mean()),
+                                          "p99": float(np.quantile(e, 0.99)),
+                                          "max": float(e.max())},
+           "fitted_bf16": _localise(M, fm, parts0, imgs, K, sch, ob, gts, Q, iters),
+           "handset_bf16": _localise(M, hs, parts0, imgs, K, sch, ob, gts, Q, iters)}
+    fm.close()
+    hs.close()
+    return out
+
+
 def run_pose_error(M, Q=10, iters=45):
     """Equal-pose-error comparison (Sec. IV-A accuracy definition: position
     error < 5 cm and rotation error < 5 deg) on the analytic room map, whose
@@ -520,33 +611,14 @@ def run_pose_error(M, Q=10, iters=45):
     import numpy as np
     import torch
     import synth
-    W = H = 100
-    focal = 138.9
     N0 = 1500
-    blob, _ = synth.room_map_weights(0)
-    gm = M.Map(blob, max_rays=Q * N0 * 64, max_samples=192, max_particles=Q * N0,
-               max_queries=Q)
-    K = M.intrinsics(focal, focal, W / 2, H / 2, W, H)
-    o32 = M.UpdateOptions(n_coarse=64, n_fine=128, precision="fp32")
-    allpx = np.stack(np.meshgrid(np.arange(W), np.arange(H), indexing="xy"), -1).reshape(-1, 2)
-    px_all = torch.tensor(allpx, dtype=torch.int32, device="cuda")
-    gts, imgs = [], []
-    for q in range(Q):
-        g = synth.gt_pose(100 + q)
-        gts.append(g)
-        imgs.append(gm.render(torch.tensor(g[0][None], dtype=torch.float32, device="cuda"), K, 2,
-                              px_all, o32).reshape(H, W, 3).contiguous())
+    gm, K, gts, imgs, sch, parts0 = _room_queries(M, Q, iters, N0)
     # learned proposal distilled from the FP32 full sampler on this map
     Ptr = torch.tensor(synth.random_particles(21, 256)[0], dtype=torch.float32, device="cuda")
     pxtr = torch.tensor(synth.pixel_set(21, 25, 25, 64), dtype=torch.int32, device="cuda")
     gm.proposal_set(synth.proposal_init_weights(0))
     gm.proposal_train(Ptr, pxtr, K, 0, M.UpdateOptions(n_coarse=64, n_fine=128, precision="fp32"),
                       epochs=40, batch_rays=2048, n_bins=64, lr=3e-3, lr_end=1e-4, seed=1)
-    sch = M.schedule([0, 1, 2], [64, 64, 64], [N0, N0 // 2, N0 // 4], n_min=100,
-                     iter_caps=[iters // 3] * 3, refine=[0.02, 0.005, 0.0], iterations=iters,
-                     sigma_t=0.02, sigma_yaw=0.02)
-    parts0 = torch.tensor(np.stack([synth.random_particles(200 + q, N0)[0] for q in range(Q)]),
-                          dtype=torch.float32, device="cuda")
     forms = {
         "fp32_full_64+32": M.UpdateOptions(n_coarse=64, n_fine=32, precision="fp32", seed=1),
         "bf16_full_64+32": M.UpdateOptions(n_coarse=64, n_fine=32, precision="bf16", seed=1),
@@ -857,6 +929,7 @@ def run_ours(args):
     if world == 1 and not args.no_extra and "bf16" in tc:
         for name, fn in (
                 ("equal_pose_error", lambda: run_pose_error(M)),
+                ("fitted_map", lambda: run_fitted_map(M)),
                 ("coarse_to_fine", lambda: run_coarse_to_fine(M, img, K, seed, "bf16")),
                 ("ablation", lambda: run_ablation(M, img, K, seed, "bf16")),
                 ("batched_queries", lambda: run_batched(M, seed, W, H, wl["focal"], prop_blob))):
