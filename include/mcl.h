@@ -415,17 +415,17 @@ int mcl_get_map_weights(mcl_map* map, float* host_out, size_t n);
  *   8 BF16 4 lockstep, CTA pair   9 FP8 4 lockstep, CTA pair
  *  10 FP8 4 staggered, CTA pair   11 BF16 4 staggered
  * Lockstep: each streamed weight block serves both tiles of a pair at once;
- * staggered: the second tile runs each layer after the first, so one tile's
- * epilogue overlaps the other's MMAs (FP8 keeps the layer's blocks resident
- * for the second tile; BF16, whose layer does not fit in its weight ring,
- * streams every block twice); split: lockstep, each layer as two
+ * staggered: the second tile runs each part of a layer (the blocks the
+ * weight ring holds: a whole FP8 layer, four BF16 blocks) after the first on
+ * the same resident blocks, so one tile's epilogue overlaps the other's
+ * MMAs; split: lockstep, each layer as two
  * 128-column halves whose epilogues overlap the MMAs of the other half and
  * of the next layer; pipelined: one tile per CTA with double-buffered
  * accumulators, the next layer's MMAs consuming the activations 64 columns
  * at a time as the epilogue writes them; CTA pair: clusters of two CTAs on
  * the two SMs of a TPC issue 256-row MMAs (tcgen05 cta_group::2), each CTA
  * streaming half of every weight block.  All variants of a precision give
- * bit-identical results.  Untuned defaults: 0 (BF16) and 4 (FP8). */
+ * bit-identical results.  Untuned defaults: 11 (BF16) and 4 (FP8). */
 #define MCL_MLP_VARIANTS 12
 
 /* Autotuner: time every variant of `precision` (MCL_PREC_BF16 or _FP8) on

@@ -22,11 +22,14 @@
 // through a named barrier, so that the issuing thread makes no shared-memory
 // access between MMAs; the other warps run prologue and epilogues, 4 or 8
 // per tile, one warp per TMEM lane quadrant and column half, one thread per
-// row.  BF16 runs the two
-// tiles in lockstep, each weight block serving both at once; FP8 staggers
-// them (tile 1 runs a layer on the resident blocks after tile 0), so each
-// tile's epilogue overlaps the other's MMAs.  Every wait is bounded (see
-// tc_ptx.cuh).
+// row.  The two tiles run staggered: each part of a layer's weight blocks
+// that the ring holds (the whole layer in FP8, half of it in BF16) is run
+// by tile 0 and then by tile 1 on the resident blocks, so each tile's
+// epilogue overlaps the other's MMAs (a lockstep schedule, each block
+// serving both tiles at once, is the alternative the autotuner measures).
+// The next work unit's gamma(x) is written while the last layers run, and
+// the last accumulator is read out of TMEM first, so that the next unit's
+// first MMAs overlap the RGB head.  Every wait is bounded (see tc_ptx.cuh).
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_fp8.h>
@@ -69,11 +72,10 @@ static_assert(Form<false>::kSmemBytes <= 232448 && Form<true>::kSmemBytes <= 232
 // Kernel variant: operand form, epilogue warps per tile (4: one per TMEM lane
 // quadrant, each thread a whole row; 8: two per quadrant, each thread half a
 // row), and the tile schedule (lockstep: each weight block serves both
-// tiles at once; staggered: tile 1 runs a layer after tile 0, so each tile's
-// epilogue overlaps the other's MMAs -- FP8 keeps the layer's blocks resident
-// in its 8-stage ring for tile 1, BF16 (whose layer does not fit in its
-// 4-stage ring) streams every block twice, once per tile).  The autotuner
-// picks among them.
+// tiles at once; staggered: tile 1 runs each part of a layer -- as many
+// blocks as the ring holds: the whole layer in FP8's 8-stage ring, four of
+// BF16's 8 or 10 -- after tile 0 on the same resident blocks, so each tile's
+// epilogue overlaps the other's MMAs).  The autotuner picks among them.
 template <bool F8, int EPIW, bool STAG>
 struct Variant {
     static_assert(EPIW == 4 || EPIW == 8, "epilogue warps");
@@ -88,8 +90,13 @@ struct Variant {
 // column 128 of the last MMA.
 __constant__ int c_chunks[2][kLayers] = {{2, 8, 8, 8, 8, 10, 8, 8, 8},
                                          {1, 4, 4, 4, 4, 5, 4, 4, 4}};
-// first weight block of each layer (BF16 form), for the re-streamed schedule
-__constant__ int c_block0_bf16[kLayers] = {0, 2, 10, 18, 26, 34, 44, 52, 60};
+
+struct EpiConsts {
+    uint32_t bias2[8][128];   // BF16: trunk biases as BF16 pairs
+    float beta[8][256];       // FP8: epilogue offset per column
+    float alpha_last[128];    // FP8: dequantisation of the RGB hidden layer
+    float w_out[3][128];      // RGB output layer
+};
 
 struct Params {
     const uint8_t* wblocks; // weight blocks of the form, pre-swizzled, in consumption order
@@ -99,15 +106,12 @@ struct Params {
     long long M;            // rows of the pass (upper bound when M_dev is set)
     long long n_pairs;
     const int* M_dev;       // optional: rows of the pass from device memory
-    const uint32_t* bias2;  // BF16: [8][128] trunk biases as BF16 pairs
-    const float* beta;      // FP8: [8][256] epilogue offset per column
     float alpha[8];         // FP8: epilogue scale per trunk layer
-    const float* alpha_last;// FP8: [128] dequantisation of the RGB hidden layer
+    const float* beta_g;    // FP8: [8][256] epilogue offset per column (global copy)
     float alpha_sigma;      // FP8: dequantisation of the density head
     float s_gx;             // FP8: scale of gamma(x)
     float b_sigma;
     const float* ray_bias;  // [n_rays][128]
-    const float* w_out;     // [3][128]
     float b_out0, b_out1, b_out2;
     float4* out;
     int* abort_flag;        // per-launch: set on a timed-out wait
@@ -139,6 +143,11 @@ struct Params {
     float* F_out;
     float* zt_out;
     float* zo_out;
+    // Per-column constants of the epilogues, carried in the parameter block
+    // (the constant bank): every thread of a warp reads the same column's
+    // value, and a constant-bank read does not go through the L1 that the
+    // 225 KB shared-memory carve-out leaves nearly empty.
+    EpiConsts ec;
 };
 
 struct __align__(8) Bars {
@@ -183,22 +192,17 @@ __device__ __forceinline__ void pe_half(const float x[3], float (&v)[32]) {
 
 // 32 accumulator columns of one row -> relu(acc + bias) as BF16 -> four
 // 16-byte chunks (j0 .. j0+3) of the row in a 128-byte-swizzled K-block.
-__device__ __forceinline__ void epi_chunk_store(const uint32_t (&v)[32], const uint4* b4,
+// bias: 16 BF16 pairs in the parameter block.
+__device__ __forceinline__ void epi_chunk_store(const uint32_t (&v)[32], const uint32_t* bias,
                                                 uint32_t blk, uint32_t r, uint32_t j0) {
     const uint32_t one2 = 0x3F803F80u;  // (1.0, 1.0) in BF16
     uint32_t pk[16];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const uint4 b = __ldg(b4 + q);
-        const uint32_t bb[4] = {b.x, b.y, b.z, b.w};
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const int i = 4 * q + e;
-            const uint32_t a = pack_bf16x2(__uint_as_float(v[2 * i]), __uint_as_float(v[2 * i + 1]));
-            uint32_t h;
-            asm("fma.rn.relu.bf16x2 %0, %1, %2, %3;" : "=r"(h) : "r"(a), "r"(one2), "r"(bb[e]));
-            pk[i] = h;
-        }
+    for (int i = 0; i < 16; ++i) {
+        const uint32_t a = pack_bf16x2(__uint_as_float(v[2 * i]), __uint_as_float(v[2 * i + 1]));
+        uint32_t h;
+        asm("fma.rn.relu.bf16x2 %0, %1, %2, %3;" : "=r"(h) : "r"(a), "r"(one2), "r"(bias[i]));
+        pk[i] = h;
     }
 #pragma unroll
     for (int q = 0; q < 4; ++q)
@@ -207,15 +211,19 @@ __device__ __forceinline__ void epi_chunk_store(const uint32_t (&v)[32], const u
 }
 
 // FP8 form: 32 accumulator columns -> relu(acc alpha + beta) (the next
-// layer's activation scale folded into alpha, beta) as E4M3 -> two 16-byte
-// chunks (j0, j0+1) of the row in a 128-byte-swizzled K-block.
+// layer's activation scale folded into alpha, beta: 32 values, in global
+// memory (kGlobal: eight 16-byte loads) or in the parameter block) as E4M3
+// -> two 16-byte chunks (j0, j0+1) of the row in a 128-byte-swizzled K-block.
+template <bool kGlobal>
 __device__ __forceinline__ void epi_chunk_store_f8(const uint32_t (&v)[32], float alpha,
-                                                   const float4* b4, uint32_t blk, uint32_t r,
+                                                   const float* beta, uint32_t blk, uint32_t r,
                                                    uint32_t j0) {
     uint32_t pk[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
-        const float4 b = __ldg(b4 + q);
+        float4 b;
+        if constexpr (kGlobal) b = __ldg(reinterpret_cast<const float4*>(beta) + q);
+        else b = make_float4(beta[4 * q], beta[4 * q + 1], beta[4 * q + 2], beta[4 * q + 3]);
         pk[q] = pack_e4m3x4_relu(fmaf(__uint_as_float(v[4 * q + 0]), alpha, b.x),
                                  fmaf(__uint_as_float(v[4 * q + 1]), alpha, b.y),
                                  fmaf(__uint_as_float(v[4 * q + 2]), alpha, b.z),
@@ -226,30 +234,28 @@ __device__ __forceinline__ void epi_chunk_store_f8(const uint32_t (&v)[32], floa
 }
 
 // One 32-column group of the last layer: h = relu(acc (* alpha) + b_ray),
-// then the 128 -> 3 output layer as running dot products.
+// then the 128 -> 3 output layer as running dot products (wo [3][128] and
+// al [128]: the parameter block; rb4: the ray's bias in global memory).
 template <bool F8>
 __device__ __forceinline__ void rgb_group(const uint32_t (&v)[32], const float4* rb4,
-                                          const float4* wo4, const float4* al4, int c32,
+                                          const float* wo, const float* al, int c32,
                                           float& o0, float& o1, float& o2) {
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
         const float4 b = __ldg(rb4 + c32 * 8 + q);
-        const float4 w0 = __ldg(wo4 + c32 * 8 + q);
-        const float4 w1 = __ldg(wo4 + 32 + c32 * 8 + q);
-        const float4 w2 = __ldg(wo4 + 64 + c32 * 8 + q);
+        const int c = c32 * 32 + 4 * q;
         float a0 = __uint_as_float(v[4 * q + 0]), a1 = __uint_as_float(v[4 * q + 1]);
         float a2 = __uint_as_float(v[4 * q + 2]), a3 = __uint_as_float(v[4 * q + 3]);
         if constexpr (F8) {
-            const float4 al = __ldg(al4 + c32 * 8 + q);
-            a0 *= al.x; a1 *= al.y; a2 *= al.z; a3 *= al.w;
+            a0 *= al[c]; a1 *= al[c + 1]; a2 *= al[c + 2]; a3 *= al[c + 3];
         }
         const float h0 = fmaxf(a0 + b.x, 0.0f);
         const float h1 = fmaxf(a1 + b.y, 0.0f);
         const float h2 = fmaxf(a2 + b.z, 0.0f);
         const float h3 = fmaxf(a3 + b.w, 0.0f);
-        o0 = fmaf(h0, w0.x, fmaf(h1, w0.y, fmaf(h2, w0.z, fmaf(h3, w0.w, o0))));
-        o1 = fmaf(h0, w1.x, fmaf(h1, w1.y, fmaf(h2, w1.z, fmaf(h3, w1.w, o1))));
-        o2 = fmaf(h0, w2.x, fmaf(h1, w2.y, fmaf(h2, w2.z, fmaf(h3, w2.w, o2))));
+        o0 = fmaf(h0, wo[c], fmaf(h1, wo[c + 1], fmaf(h2, wo[c + 2], fmaf(h3, wo[c + 3], o0))));
+        o1 = fmaf(h0, wo[128 + c], fmaf(h1, wo[129 + c], fmaf(h2, wo[130 + c], fmaf(h3, wo[131 + c], o1))));
+        o2 = fmaf(h0, wo[256 + c], fmaf(h1, wo[257 + c], fmaf(h2, wo[258 + c], fmaf(h3, wo[259 + c], o2))));
     }
 }
 
@@ -598,84 +604,75 @@ __device__ __forceinline__ void epilogue_warps(const Params& p, int warp, int wa
     EpiSync es{slot ? bar_epi1 : bar_epi0, 0u, abort_flag, p.wait_ns};
     float* scr = reinterpret_cast<float*>(act_ptr + slot * kActBytes);
     const long long n_rays = M / p.S;
-    bool pend = false;
-    long long pend_ray0 = 0;
-    float pz = 0.f, pdn = 0.f;
-    float4 pv = make_float4(0.f, 0.f, 0.f, 0.f);
     float fz[2] = {0.f, 0.f};
     float4 fo[2] = {make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f)};
     float4 ob = make_float4(0.f, 0.f, 0.f, 0.f);
-    auto run_tail = [&]() -> bool {
-        if constexpr (FUSE == 1)
-            return tail_importance(p, es, scr, (int)r, lane, quad, pend_ray0, n_rays, pz, pv.x, pdn);
-        else
-            return tail_final(p, es, scr, (int)r, lane, quad, pend_ray0, n_rays, pz, pv, pdn, fz, fo, ob);
+    // Prologue of unit pu: this thread's halves of gamma(x) of its row into
+    // the tile's gamma(x) buffer; returns the row's z and its ray's |d|.
+    auto prologue = [&](long long pu, float& z_out, float& dn_out) {
+        const long long gr = pu * unit_rows + row_base + slot * 128 + r;
+        const bool vr = gr < M;
+        float x[3] = {0.f, 0.f, 0.f};
+        z_out = 0.f;
+        dn_out = 0.f;
+        if (vr) {
+            const Ray R = p.rays[gr / p.S];
+            const float zz = p.z[gr];
+            z_out = zz;
+            dn_out = R.dnorm;
+            x[0] = fmaf(zz, R.dx, R.ox);
+            x[1] = fmaf(zz, R.dy, R.oy);
+            x[2] = fmaf(zz, R.dz, R.oz);
+        }
+        for (int half = h0; half < h1; ++half) {
+            float v[32];
+            if (vr) {
+                if (half == 0) pe_half<0>(x, v);
+                else pe_half<1>(x, v);
+            } else {
+#pragma unroll
+                for (int i = 0; i < 32; ++i) v[i] = 0.0f;
+            }
+            if constexpr (F8) {
+                const float sg = p.s_gx;
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    uint32_t w[4];
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const int i = 16 * j + 4 * e;
+                        w[e] = pack_e4m3x4(v[i] * sg, v[i + 1] * sg, v[i + 2] * sg, v[i + 3] * sg);
+                    }
+                    st_shared_v4(g_base + sw128_offset(r, 2 * half + j), w[0], w[1], w[2], w[3]);
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    st_shared_v4(g_base + sw128_offset(r, 4 * half + j), pack_bf16x2(v[8 * j], v[8 * j + 1]),
+                                 pack_bf16x2(v[8 * j + 2], v[8 * j + 3]),
+                                 pack_bf16x2(v[8 * j + 4], v[8 * j + 5]),
+                                 pack_bf16x2(v[8 * j + 6], v[8 * j + 7]));
+            }
+        }
     };
+    // The first unit's gamma(x) is written and signalled up front.  Every
+    // later unit's is written during the previous unit, after the epilogue
+    // of the skip layer (l = 5: gamma(x) is last read by its MMAs, which have
+    // completed when its accumulator is signalled), and
+    // signalled once the previous unit's last accumulator has been read out
+    // of TMEM: the next unit's first MMAs then run while this unit's RGB
+    // head and ray epilogue are computed.
+    float nz = 0.f, ndn = 0.f;
+    if (u0 < n_units) {
+        prologue(u0, nz, ndn);
+        signal_ready<PAIR>(bar_ready, lane);
+    }
     for (long long pr = u0; pr < n_units && ok; pr += du) {
         const long long grow = pr * unit_rows + row_base + slot * 128 + r;
         const bool valid = grow < M;
         const long long ray = valid ? grow / p.S : 0;
-        float zrow = 0.f, dnrow = 0.f;
-        // ---- prologue: this thread's halves of gamma(x) into the tile's
-        //      gamma(x) buffer
-        {
-            float x[3] = {0.f, 0.f, 0.f};
-            if (valid) {
-                const Ray R = p.rays[ray];
-                const float zz = p.z[grow];
-                zrow = zz;
-                dnrow = R.dnorm;
-                x[0] = fmaf(zz, R.dx, R.ox);
-                x[1] = fmaf(zz, R.dy, R.oy);
-                x[2] = fmaf(zz, R.dz, R.oz);
-            }
-            for (int half = h0; half < h1; ++half) {
-                float v[32];
-                if (valid) {
-                    if (half == 0) pe_half<0>(x, v);
-                    else pe_half<1>(x, v);
-                } else {
-#pragma unroll
-                    for (int i = 0; i < 32; ++i) v[i] = 0.0f;
-                }
-                if constexpr (F8) {
-                    const float sg = p.s_gx;
-#pragma unroll
-                    for (int j = 0; j < 2; ++j) {
-                        uint32_t w[4];
-#pragma unroll
-                        for (int e = 0; e < 4; ++e) {
-                            const int i = 16 * j + 4 * e;
-                            w[e] = pack_e4m3x4(v[i] * sg, v[i + 1] * sg, v[i + 2] * sg,
-                                               v[i + 3] * sg);
-                        }
-                        st_shared_v4(g_base + sw128_offset(r, 2 * half + j), w[0], w[1], w[2], w[3]);
-                    }
-                } else {
-#pragma unroll
-                    for (int j = 0; j < 4; ++j)
-                        st_shared_v4(g_base + sw128_offset(r, 4 * half + j),
-                                     pack_bf16x2(v[8 * j], v[8 * j + 1]),
-                                     pack_bf16x2(v[8 * j + 2], v[8 * j + 3]),
-                                     pack_bf16x2(v[8 * j + 4], v[8 * j + 5]),
-                                     pack_bf16x2(v[8 * j + 6], v[8 * j + 7]));
-                }
-            }
-            signal_ready<PAIR>(bar_ready, lane);
-        }
-        if constexpr (FUSE != 0) {
-            // (a failure leaves the function at once: no path from inside
-            // the layer loop reaches a use of the pending-ray state, so that
-            // state is live only between the last layer and the tail)
-            if (pend) {
-                pend = false;
-                if (!run_tail()) {
-                    record_abort(p);
-                    return;
-                }
-            }
-        }
-        float sigma = 0.0f;
+        const bool has_next = pr + du < n_units;
+        const float zrow = nz, dnrow = ndn;
         float4 res = make_float4(0.f, 0.f, 0.f, 0.f);
         for (int l = 0; l < kLayers && ok; ++l) {
             const bool got = PAIR ? mbar_wait_cluster<true>(bar_acc, acc_ph, abort_flag)
@@ -699,102 +696,111 @@ __device__ __forceinline__ void epilogue_warps(const Params& p, int warp, int wa
                     tmem_ld32(t_acc, va);
                     if constexpr (F8) {
                         // h = relu(acc alpha + beta) in FP32, stored as E4M3:
-                        // columns 128 half .. +127 are K-block `half`, chunks 0..7
+                        // columns 128 half .. +127 are K-block `half`, chunks 0..7;
+                        // beta: with 4 warps per tile (a whole row per
+                        // thread) from global memory, with 8 from the
+                        // parameter block (the faster of the two measured
+                        // for each)
+                        constexpr bool kBg = EPIW == 4;
                         const float alpha = p.alpha[l];
-                        const float4* b4 =
-                            reinterpret_cast<const float4*>(p.beta + l * 256 + half * 128);
+                        const float* bc = (kBg ? p.beta_g + l * 256 : p.ec.beta[l]) + half * 128;
                         const uint32_t blk = a_base + half * 16384;
 #pragma unroll 1
                         for (int c32 = 0; c32 < 4; c32 += 2) {
                             tmem_ld_wait();
                             tmem_ld32(t_acc + (c32 + 1) * 32, vb);
-                            epi_chunk_store_f8(va, alpha, b4 + c32 * 8, blk, r, c32 * 2);
+                            epi_chunk_store_f8<kBg>(va, alpha, bc + c32 * 32, blk, r, c32 * 2);
                             tmem_ld_wait();
                             if (c32 + 2 < 4) tmem_ld32(t_acc + (c32 + 2) * 32, va);
-                            epi_chunk_store_f8(vb, alpha, b4 + (c32 + 1) * 8, blk, r,
-                                               (c32 + 1) * 2);
+                            epi_chunk_store_f8<kBg>(vb, alpha, bc + (c32 + 1) * 32, blk, r,
+                                                    (c32 + 1) * 2);
                         }
                     } else {
                         // h = relu(acc + b): accumulators rounded to BF16 pairs,
                         // bias added and ReLU applied in packed BF16 arithmetic;
                         // columns 128 half .. +127 are K-blocks 2 half, 2 half + 1
-                        const uint4* b4 =
-                            reinterpret_cast<const uint4*>(p.bias2 + l * 128 + half * 64);
+                        const uint32_t* bb = p.ec.bias2[l] + half * 64;
 #pragma unroll 1
                         for (int c32 = 0; c32 < 4; c32 += 2) {
                             tmem_ld_wait();
                             tmem_ld32(t_acc + (c32 + 1) * 32, vb);
                             const uint32_t blk = a_base + (2 * half + (c32 >> 1)) * 16384;
-                            epi_chunk_store(va, b4 + c32 * 4, blk, r, 0);
+                            epi_chunk_store(va, bb + c32 * 16, blk, r, 0);
                             tmem_ld_wait();
                             if (c32 + 2 < 4) tmem_ld32(t_acc + (c32 + 2) * 32, va);
-                            epi_chunk_store(vb, b4 + (c32 + 1) * 4, blk, r, 4);
+                            epi_chunk_store(vb, bb + (c32 + 1) * 16, blk, r, 4);
                         }
                     }
                 }
                 signal_ready<PAIR>(bar_ready, lane);
-            } else if (h0 == 0) {
-                const float4* rb4 = reinterpret_cast<const float4*>(p.ray_bias + ray * 128);
-                const float4* wo4 = reinterpret_cast<const float4*>(p.w_out);
-                const float4* al4 = reinterpret_cast<const float4*>(p.alpha_last);
-                float o0 = 0.f, o1 = 0.f, o2 = 0.f;
-                uint32_t va[32], vb[32];
-                tmem_ld32(t_row, va);
-#pragma unroll 1
-                for (int c32 = 0; c32 < 4; c32 += 2) {
+                if (l == 5 && has_next) prologue(pr + du, nz, ndn);
+            } else {
+                if (h0 == 0) {
+                    // the RGB hidden layer (128 columns) and the density
+                    // (column 128) read out of TMEM in two bursts, so that
+                    // the accumulator is soon free for the next unit's
+                    // first layer
+                    const float4* rb4 = reinterpret_cast<const float4*>(p.ray_bias + ray * 128);
+                    const float* wo = &p.ec.w_out[0][0];
+                    float o0 = 0.f, o1 = 0.f, o2 = 0.f;
+                    uint32_t va[32], vb[32];
+                    uint32_t vs;
+                    tmem_ld32(t_row, va);
+                    tmem_ld32(t_row + 32, vb);
                     tmem_ld_wait();
-                    tmem_ld32(t_row + (c32 + 1) * 32, vb);
-                    rgb_group<F8>(va, rb4, wo4, al4, c32, o0, o1, o2);
+                    rgb_group<F8>(va, rb4, wo, p.ec.alpha_last, 0, o0, o1, o2);
+                    rgb_group<F8>(vb, rb4, wo, p.ec.alpha_last, 1, o0, o1, o2);
+                    tmem_ld32(t_row + 64, va);
+                    tmem_ld32(t_row + 96, vb);
+                    tmem_ld1(t_row + 128, vs);
                     tmem_ld_wait();
-                    if (c32 + 2 < 4) tmem_ld32(t_row + (c32 + 2) * 32, va);
-                    rgb_group<F8>(vb, rb4, wo4, al4, c32 + 1, o0, o1, o2);
-                }
-                {
-                    // density head: accumulator column 128 of the last MMA
-                    uint32_t vs[32];
-                    tmem_ld32(t_row + 128, vs);
-                    tmem_ld_wait();
-                    sigma = __uint_as_float(vs[0]);
+                    if (has_next) signal_ready<PAIR>(bar_ready, lane);
+                    rgb_group<F8>(va, rb4, wo, p.ec.alpha_last, 2, o0, o1, o2);
+                    rgb_group<F8>(vb, rb4, wo, p.ec.alpha_last, 3, o0, o1, o2);
+                    float sigma = __uint_as_float(vs);
                     if constexpr (F8) sigma *= p.alpha_sigma;
+                    res.x = sigma + p.b_sigma;
+                    res.y = 1.0f / (1.0f + __expf(-(o0 + p.b_out0)));
+                    res.z = 1.0f / (1.0f + __expf(-(o1 + p.b_out1)));
+                    res.w = 1.0f / (1.0f + __expf(-(o2 + p.b_out2)));
+                    if (valid && FUSE != 2) p.out[grow] = res;
+                } else if (has_next) {
+                    // (8 warps per tile: the second column half reads no
+                    // TMEM in the last layer)
+                    signal_ready<PAIR>(bar_ready, lane);
                 }
-                tc_fence_before();
-                res.x = sigma + p.b_sigma;
-                res.y = 1.0f / (1.0f + __expf(-(o0 + p.b_out0)));
-                res.z = 1.0f / (1.0f + __expf(-(o1 + p.b_out1)));
-                res.w = 1.0f / (1.0f + __expf(-(o2 + p.b_out2)));
-                if (valid && FUSE != 2) p.out[grow] = res;
             }
         }
         if constexpr (FUSE != 0) {
-            // the unit's ray epilogue runs after the next unit's prologue
-            pend = true;
-            pend_ray0 = (pr * unit_rows + row_base + slot * 128) / p.S;
-            pz = zrow;
-            pdn = dnrow;
-            pv = valid ? res : make_float4(0.f, 0.f, 0.f, 0.f);
-            if constexpr (FUSE == 2) {
-                // first-pass samples q = r, r + 128 of this tile's rays, in
-                // flight while the next unit's prologue runs
-                const int R1 = (128 / p.S) * p.S1;
+            // the unit's ray epilogue, under the next unit's first MMAs
+            if (ok) {
+                const long long ray0 = (pr * unit_rows + row_base + slot * 128) / p.S;
+                bool good;
+                if constexpr (FUSE == 1) {
+                    good = tail_importance(p, es, scr, (int)r, lane, quad, ray0, n_rays, zrow,
+                                           valid ? res.x : 0.f, dnrow);
+                } else {
+                    // first-pass samples q = r, r + 128 of this tile's rays and
+                    // the observed colour of the ray this warp composites
+                    const int R1 = (128 / p.S) * p.S1;
 #pragma unroll
-                for (int i = 0; i < 2; ++i) {
-                    const int q = (int)r + 128 * i;
-                    if (q < R1 && pend_ray0 + q / p.S1 < n_rays) {
-                        const long long idx = (pend_ray0 + q / p.S1) * p.S1 + q % p.S1;
-                        fz[i] = p.z_first[idx];
-                        fo[i] = p.out_first[idx];
+                    for (int i = 0; i < 2; ++i) {
+                        const int q = (int)r + 128 * i;
+                        if (q < R1 && ray0 + q / p.S1 < n_rays) {
+                            const long long idx = (ray0 + q / p.S1) * p.S1 + q % p.S1;
+                            fz[i] = p.z_first[idx];
+                            fo[i] = p.out_first[idx];
+                        }
                     }
+                    if (p.obs && quad < 128 / p.S && ray0 + quad < n_rays) ob = p.obs[ray0 + quad];
+                    good = tail_final(p, es, scr, (int)r, lane, quad, ray0, n_rays, zrow,
+                                      valid ? res : make_float4(0.f, 0.f, 0.f, 0.f), dnrow, fz, fo, ob);
                 }
-                // observed colour of the ray this warp will composite
-                if (p.obs && quad < 128 / p.S && pend_ray0 + quad < n_rays)
-                    ob = p.obs[pend_ray0 + quad];
+                if (!good) {
+                    record_abort(p);
+                    return;
+                }
             }
-        }
-    }
-    if constexpr (FUSE != 0) {
-        if (pend && !run_tail()) {
-            record_abort(p);
-            return;
         }
     }
     if (!ok) record_abort(p);
@@ -857,17 +863,8 @@ __global__ void __launch_bounds__(Variant<F8, EPIW, STAG>::kThreads, 1)
                 ++g;
                 return true;
             };
-            for (long long pr = blockIdx.x; pr < n_pairs && ok; pr += gridDim.x) {
-                if constexpr (STAG && !F8) {
-                    // each layer's blocks twice: for tile 0, then for tile 1
-                    for (int l = 0; l < kLayers && ok; ++l)
-                        for (int t = 0; t < 2 && ok; ++t)
-                            for (int c = 0; c < c_chunks[0][l] && ok; ++c)
-                                ok = stream(c_block0_bf16[l] + c);
-                } else {
-                    for (int b = 0; b < Fm::kBlocks && ok; ++b) ok = stream(b);
-                }
-            }
+            for (long long pr = blockIdx.x; pr < n_pairs && ok; pr += gridDim.x)
+                for (int b = 0; b < Fm::kBlocks && ok; ++b) ok = stream(b);
             if (!ok) record_abort(p);
             // every issued copy lands before the CTA may exit: the last copy
             // of each stage (earlier ones were consumed before it was issued)
@@ -919,49 +916,40 @@ __global__ void __launch_bounds__(Variant<F8, EPIW, STAG>::kThreads, 1)
             for (int l = 0; l < kLayers && ok; ++l) {
                 const int nch = c_chunks[F8 ? 1 : 0][l];
                 const uint32_t idesc = (l == 8) ? id144 : id256;
-                if constexpr (STAG && !F8) {
-                    // Staggered tiles, BF16: all of layer l for tile 0, then
-                    // all of it for tile 1, each from its own stream of the
-                    // layer's blocks; a stage is released after its MMAs.
-                    for (int t = 0; t < 2 && ok; ++t)
-                        for (int c = 0; c < nch; ++c, ++g) {
+                if constexpr (STAG) {
+                    // Staggered tiles: the layer's blocks in parts of at most
+                    // kStages (the ring holds a whole part; the last parts are
+                    // full), each part run by tile 0 and then by tile 1 on
+                    // the same resident blocks, so that tile 0's epilogue
+                    // runs under tile 1's last part and tile 1's under tile
+                    // 0's first part of the next layer.  A stage is released
+                    // after tile 1's MMAs.  (FP8: a layer is at most 5 of the
+                    // 8 stages, one part; BF16: 4-block parts.)
+                    for (int c0 = 0; c0 < nch && ok;) {
+                        const int np = (c0 == 0 && nch % kStages) ? nch % kStages : kStages;
+                        for (int c = c0; c < c0 + np; ++c) {
                             if (!gate()) { ok = false; break; }
                             if (lane == 0) {
                                 tc_fence_after();
-                                const uint32_t st = g % kStages;
-                                issue(l, t, c, st, idesc);
-                                mma_commit(smem_u32(&bars.empty[st]));
-                                if (c == nch - 1) mma_commit(smem_u32(&bars.acc_full[t]));
+                                issue(l, 0, c, (g + c) % kStages, idesc);
+                                if (c == nch - 1) mma_commit(smem_u32(&bars.acc_full[0]));
                             }
                             __syncwarp();
                         }
-                } else if constexpr (STAG) {
-                    // Staggered tiles: all of layer l for tile 0, then all of
-                    // it for tile 1 from the same resident weight blocks (a
-                    // layer is at most 5 of the 8 stages), so tile 0's
-                    // epilogue runs under tile 1's MMAs and vice versa.  A
-                    // stage is released after tile 1's MMAs.
-                    for (int c = 0; c < nch; ++c) {
+                        if (!ok) break;
                         if (!gate()) { ok = false; break; }
                         if (lane == 0) {
                             tc_fence_after();
-                            issue(l, 0, c, (g + c) % kStages, idesc);
-                            if (c == nch - 1) mma_commit(smem_u32(&bars.acc_full[0]));
+                            for (int c = c0; c < c0 + np; ++c) {
+                                const uint32_t st = (g + c) % kStages;
+                                issue(l, 1, c, st, idesc);
+                                mma_commit(smem_u32(&bars.empty[st]));
+                            }
+                            if (c0 + np == nch) mma_commit(smem_u32(&bars.acc_full[1]));
                         }
                         __syncwarp();
+                        c0 += np;
                     }
-                    if (!ok) break;
-                    if (!gate()) { ok = false; break; }
-                    if (lane == 0) {
-                        tc_fence_after();
-                        for (int c = 0; c < nch; ++c) {
-                            const uint32_t st = (g + c) % kStages;
-                            issue(l, 1, c, st, idesc);
-                            mma_commit(smem_u32(&bars.empty[st]));
-                        }
-                        mma_commit(smem_u32(&bars.acc_full[1]));
-                    }
-                    __syncwarp();
                     g += nch;
                 } else {
                     // Lockstep tiles: each weight block serves both tiles at
@@ -1026,23 +1014,19 @@ __global__ void __launch_bounds__(Variant<F8, EPIW, STAG>::kThreads, 1)
         for (long long pr = blockIdx.x; pr < n_pairs && ok; pr += gridDim.x) {
             for (int l = 0; l < kLayers && ok; ++l) {
                 const int nch = c_chunks[F8 ? 1 : 0][l];
-                if constexpr (STAG && !F8) {
-                    for (int t = 0; t < 2 && ok; ++t)
-                        for (int c = 0; c < nch; ++c, ++g) {
+                if constexpr (STAG) {
+                    for (int c0 = 0; c0 < nch && ok;) {
+                        const int np = (c0 == 0 && nch % kStages) ? nch % kStages : kStages;
+                        for (int c = c0; c < c0 + np; ++c) {
                             bool good = true;
-                            if (c == 0) good = wait_ready(t);
-                            good = good && wait_block(g);
+                            if (c == 0) good = wait_ready(0);
+                            good = good && wait_block(g + c);
                             if (!release(good)) { ok = false; break; }
                         }
-                } else if constexpr (STAG) {
-                    for (int c = 0; c < nch; ++c) {
-                        bool good = true;
-                        if (c == 0) good = wait_ready(0);
-                        good = good && wait_block(g + c);
-                        if (!release(good)) { ok = false; break; }
+                        if (!ok) break;
+                        if (!release(c0 == 0 ? wait_ready(1) : true)) { ok = false; break; }
+                        c0 += np;
                     }
-                    if (!ok) break;
-                    if (!release(wait_ready(1))) { ok = false; break; }
                     g += nch;
                 } else {
                     for (int c = 0; c < nch; ++c, ++g) {
@@ -1542,7 +1526,7 @@ __global__ void __launch_bounds__(kSplitThreads, 1) k_mlp_tc_split(const __grid_
             }
             float o0 = 0.f, o1 = 0.f, o2 = 0.f;
             const float4* rb4 = reinterpret_cast<const float4*>(p.ray_bias + ray * 128);
-            const float4* wo4 = reinterpret_cast<const float4*>(p.w_out);
+            const float* wo = &p.ec.w_out[0][0];
             for (int l = 0; l < kLayers && ok; ++l) {
                 for (int h = 0; h < 2 && ok; ++h) {
                     if (!mbar_wait(h ? b_hi : b_lo, h ? ph_hi : ph_lo, abort_flag)) {
@@ -1554,7 +1538,7 @@ __global__ void __launch_bounds__(kSplitThreads, 1) k_mlp_tc_split(const __grid_
                     tc_fence_after();
                     const uint32_t t_acc = t_row + h * 128;
                     if (l < 8) {
-                        const uint4* b4 = reinterpret_cast<const uint4*>(p.bias2 + l * 128 + h * 64);
+                        const uint32_t* bb = p.ec.bias2[l] + h * 64;
                         uint32_t va[32], vb[32];
                         tmem_ld32(t_acc, va);
 #pragma unroll 1
@@ -1562,10 +1546,10 @@ __global__ void __launch_bounds__(kSplitThreads, 1) k_mlp_tc_split(const __grid_
                             tmem_ld_wait();
                             tmem_ld32(t_acc + (c32 + 1) * 32, vb);
                             const uint32_t blk = a_base + (2 * h + (c32 >> 1)) * 16384;
-                            epi_chunk_store(va, b4 + c32 * 4, blk, r, 0);
+                            epi_chunk_store(va, bb + c32 * 16, blk, r, 0);
                             tmem_ld_wait();
                             if (c32 + 2 < 4) tmem_ld32(t_acc + (c32 + 2) * 32, va);
-                            epi_chunk_store(vb, b4 + (c32 + 1) * 4, blk, r, 4);
+                            epi_chunk_store(vb, bb + (c32 + 1) * 16, blk, r, 4);
                         }
                         fence_proxy_async_smem();
                         tc_fence_before();
@@ -1577,10 +1561,10 @@ __global__ void __launch_bounds__(kSplitThreads, 1) k_mlp_tc_split(const __grid_
                         for (int c32 = 0; c32 < 4; c32 += 2) {
                             tmem_ld_wait();
                             tmem_ld32(t_acc + (c32 + 1) * 32, vb);
-                            rgb_group<false>(va, rb4, wo4, nullptr, c32, o0, o1, o2);
+                            rgb_group<false>(va, rb4, wo, nullptr, c32, o0, o1, o2);
                             tmem_ld_wait();
                             if (c32 + 2 < 4) tmem_ld32(t_acc + (c32 + 2) * 32, va);
-                            rgb_group<false>(vb, rb4, wo4, nullptr, c32 + 1, o0, o1, o2);
+                            rgb_group<false>(vb, rb4, wo, nullptr, c32 + 1, o0, o1, o2);
                         }
                     } else {
                         // density head: accumulator column 128 of the last layer
@@ -1792,7 +1776,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_mlp_tc_pipe(const __grid_co
                 if (l < 8) {
                     // 64 columns at a time (one 128-byte K block of the next
                     // layer), each released to the MMAs as soon as it is stored
-                    const uint4* b4 = reinterpret_cast<const uint4*>(p.bias2 + l * 128);
+                    const uint32_t* bb = p.ec.bias2[l];
                     uint32_t va[32], vb[32];
                     tmem_ld32(t_acc, va);
 #pragma unroll 1
@@ -1800,17 +1784,17 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_mlp_tc_pipe(const __grid_co
                         tmem_ld_wait();
                         tmem_ld32(t_acc + (2 * q + 1) * 32, vb);
                         const uint32_t blk = s_act + q * 16384;
-                        epi_chunk_store(va, b4 + (2 * q) * 4, blk, r, 0);
+                        epi_chunk_store(va, bb + (2 * q) * 16, blk, r, 0);
                         tmem_ld_wait();
                         if (q + 1 < 4) tmem_ld32(t_acc + (2 * q + 2) * 32, va);
-                        epi_chunk_store(vb, b4 + (2 * q + 1) * 4, blk, r, 4);
+                        epi_chunk_store(vb, bb + (2 * q + 1) * 16, blk, r, 4);
                         fence_proxy_async_smem();
                         tc_fence_before();
                         mbar_arrive(smem_u32(&bars.q_ready[q]));
                     }
                 } else {
                     const float4* rb4 = reinterpret_cast<const float4*>(p.ray_bias + ray * 128);
-                    const float4* wo4 = reinterpret_cast<const float4*>(p.w_out);
+                    const float* wo = &p.ec.w_out[0][0];
                     float o0 = 0.f, o1 = 0.f, o2 = 0.f;
                     uint32_t va[32], vb[32];
                     tmem_ld32(t_acc, va);
@@ -1818,10 +1802,10 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_mlp_tc_pipe(const __grid_co
                     for (int c32 = 0; c32 < 4; c32 += 2) {
                         tmem_ld_wait();
                         tmem_ld32(t_acc + (c32 + 1) * 32, vb);
-                        rgb_group<false>(va, rb4, wo4, nullptr, c32, o0, o1, o2);
+                        rgb_group<false>(va, rb4, wo, nullptr, c32, o0, o1, o2);
                         tmem_ld_wait();
                         if (c32 + 2 < 4) tmem_ld32(t_acc + (c32 + 2) * 32, va);
-                        rgb_group<false>(vb, rb4, wo4, nullptr, c32 + 1, o0, o1, o2);
+                        rgb_group<false>(vb, rb4, wo, nullptr, c32 + 1, o0, o1, o2);
                     }
                     uint32_t vs[32];
                     tmem_ld32(t_acc + 128, vs);
@@ -1893,16 +1877,17 @@ const TcVariant kVariants[] = {
     make_pair_variant<true, true>(),     make_variant<false, 4, true>(),
 };
 // Fused passes (Params::fuse 1, 2) run on the single-CTA kernel with 4
-// epilogue warps per tile, in lockstep (BF16) or staggered (FP8): the
-// autotuner's choice at every size measured.
+// epilogue warps per tile (the fused ray epilogues need one thread per row)
+// and staggered tiles.
 void (*const kFusedKernels[2][2])(Params) = {
-    {&k_mlp_tc<false, 4, false, 1>, &k_mlp_tc<false, 4, false, 2>},
+    {&k_mlp_tc<false, 4, true, 1>, &k_mlp_tc<false, 4, true, 2>},
     {&k_mlp_tc<true, 4, true, 1>, &k_mlp_tc<true, 4, true, 2>}};
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 static_assert(kNumVariants == MCL_MLP_VARIANTS, "variant table");
-// untuned choice per precision (fastest measured at all sizes on GB300):
-// BF16 4 warps lockstep, FP8 4 warps staggered
-constexpr int kDefaultVariant[3] = {-1, 0, 4};
+// untuned choice per precision: BF16 4 warps staggered (fastest measured at
+// all sizes on GB300), FP8 4 warps staggered (the fused passes' kernel; 8
+// warps staggered measures about 7 % faster on plain MLP launches)
+constexpr int kDefaultVariant[3] = {-1, 11, 4};
 
 struct TcForm {
     uint8_t* wblocks = nullptr;  // weight blocks in consumption order, 64-byte swizzled
@@ -1914,11 +1899,9 @@ struct TcState {
     float* aux = nullptr;      // fp32 biases, scales and small heads
     float* ray_bias = nullptr; // [max_rays][128]
     int* abort_flag = nullptr;
-    const uint32_t* bias2 = nullptr;
-    const float* beta = nullptr;
-    const float* alpha_last = nullptr;
+    EpiConsts ec;              // copied into every launch's parameter block
+    const float* beta_g = nullptr;
     float alpha[8] = {1, 1, 1, 1, 1, 1, 1, 1};
-    const float* w_out = nullptr;
     const float* Wd = nullptr;
     const float* bprime = nullptr;
     float b_sigma = 0.f, b_out[3] = {0.f, 0.f, 0.f};
@@ -2099,24 +2082,22 @@ int mlp_tc_prepare(mcl_map* m, const float* blob) {
         }
     }
     if (b != nb8) return fail(MCL_ERR_UNSUPPORTED, "internal: FP8 weight block count %d", b);
-    // ---- aux: BF16 trunk biases as pairs [8][128] (bit patterns stored in
-    //      floats), FP8 beta [8][256], FP8 alpha of the RGB
-    //      hidden layer [128], w_out [3][128], W_d [128][27], b' [128]
-    std::vector<float> aux;
-    const size_t o_bias = aux.size();
+    // ---- per-column epilogue constants (parameter block): BF16 trunk
+    //      biases as pairs [8][128], FP8 beta [8][256], FP8 alpha of the RGB
+    //      hidden layer [128], w_out [3][128]
     for (int l = 0; l < kDepth; ++l)
-        for (int j = 0; j < kWidth / 2; ++j) {
-            const uint32_t pr = (uint32_t)f2bf(bp[l][2 * j]) | ((uint32_t)f2bf(bp[l][2 * j + 1]) << 16);
-            float f;
-            memcpy(&f, &pr, 4);
-            aux.push_back(f);
-        }
+        for (int j = 0; j < kWidth / 2; ++j)
+            st->ec.bias2[l][j] = (uint32_t)f2bf(bp[l][2 * j]) | ((uint32_t)f2bf(bp[l][2 * j + 1]) << 16);
+    for (int l = 0; l < kDepth; ++l)
+        for (int n = 0; n < kWidth; ++n) st->ec.beta[l][n] = beta[(size_t)l * kWidth + n];
+    for (int n = 0; n < kRgbW; ++n) st->ec.alpha_last[n] = alpha_last[n];
+    for (int c = 0; c < 3; ++c)
+        for (int n = 0; n < kRgbW; ++n) st->ec.w_out[c][n] = Wp[11][(size_t)c * kRgbW + n];
+    // ---- aux (device): FP8 beta [8][256], W_d [128][27], b' [128] of the
+    //      per-ray colour bias
+    std::vector<float> aux;
     const size_t o_beta = aux.size();
     aux.insert(aux.end(), beta.begin(), beta.end());
-    const size_t o_al = aux.size();
-    aux.insert(aux.end(), alpha_last.begin(), alpha_last.end());
-    const size_t o_wout = aux.size();
-    aux.insert(aux.end(), Wp[11], Wp[11] + 3 * kRgbW);
     const size_t o_wd = aux.size();
     for (int o = 0; o < kRgbW; ++o)
         for (int i = 0; i < kGd; ++i) aux.push_back(Wp[10][(size_t)o * fin[10] + kWidth + i]);
@@ -2178,10 +2159,7 @@ int mlp_tc_prepare(mcl_map* m, const float* blob) {
         (rc = cuda_check(cudaMalloc(&st->ray_bias, (size_t)m->cfg.max_rays * 128 * 4), "ray bias")) ||
         (rc = cuda_check(cudaMalloc(&st->abort_flag, sizeof(int)), "abort flag")))
         return rc;
-    st->bias2 = reinterpret_cast<const uint32_t*>(st->aux + o_bias);
-    st->beta = st->aux + o_beta;
-    st->alpha_last = st->aux + o_al;
-    st->w_out = st->aux + o_wout;
+    st->beta_g = st->aux + o_beta;
     st->Wd = st->aux + o_wd;
     st->bprime = st->aux + o_bp;
 
@@ -2295,15 +2273,13 @@ static cudaError_t mlp_tc_variant(mcl_map* m, int precision, int variant, const 
     p.M = (long long)n_rays * S;
     p.n_pairs = (p.M + 255) / 256;
     p.M_dev = rows_dev;
-    p.bias2 = st->bias2;
-    p.beta = st->beta;
     for (int l = 0; l < 8; ++l) p.alpha[l] = st->alpha[l];
-    p.alpha_last = st->alpha_last;
+    p.ec = st->ec;
+    p.beta_g = st->beta_g;
     p.alpha_sigma = st->alpha_sigma;
     p.s_gx = st->s_gx;
     p.b_sigma = st->b_sigma;
     p.ray_bias = st->ray_bias;
-    p.w_out = st->w_out;
     p.b_out0 = st->b_out[0];
     p.b_out1 = st->b_out[1];
     p.b_out2 = st->b_out[2];
