@@ -88,8 +88,9 @@ struct Variant {
 // layer has N = 144: rows 0..127 are the RGB hidden layer (feature layer
 // folded in), row 128 the density head, so sigma_raw arrives as accumulator
 // column 128 of the last MMA.
-__constant__ int c_chunks[2][kLayers] = {{2, 8, 8, 8, 8, 10, 8, 8, 8},
-                                         {1, 4, 4, 4, 4, 5, 4, 4, 4}};
+__host__ __device__ constexpr int layer_chunks(bool f8, int l) {
+    return (l == 0 ? 2 : l == 5 ? 10 : 8) >> (f8 ? 1 : 0);
+}
 
 struct EpiConsts {
     uint32_t bias2[8][128];   // BF16: trunk biases as BF16 pairs
@@ -885,19 +886,20 @@ __global__ void __launch_bounds__(Variant<F8, EPIW, STAG>::kThreads, 1)
         // Operand descriptors: the bases are built once; an operand at byte
         // offset o from a base is base + o / 16 (the 14-bit start-address
         // field does not overflow: all of shared memory is below 256 KB), so
-        // the issuing lane does one add per operand between MMAs.
-        const uint64_t d_act[2] = {smem_desc(s_act, 1024, kLayoutSw128),
-                                   smem_desc(s_act + kActBytes, 1024, kLayoutSw128)};
-        const uint64_t d_gx[2] = {smem_desc(s_gx, 1024, kLayoutSw128),
-                                  smem_desc(s_gx + kGxBytes, 1024, kLayoutSw128)};
+        // the issuing lane does one add per operand between MMAs.  Nothing
+        // here is indexed at run time: a local-memory load in the issuing
+        // thread would wait behind its queued MMAs.
+        const uint64_t d_act = smem_desc(s_act, 1024, kLayoutSw128);
+        const uint64_t d_gx = smem_desc(s_gx, 1024, kLayoutSw128);
         const uint64_t d_ring = smem_desc(s_ring, 512, kLayoutSw64);
         // A operand of tile s, chunk c (two 32-byte K steps) of layer l:
         // gamma(x) for layer 1 and the skip layer's last chunks, else the
         // activation tile (K-blocks of 128-byte rows, 16 KB apart)
         auto a_desc = [&](int l, int s, int c) -> uint64_t {
-            if (l == 0) return d_gx[s] + (uint64_t)(c * 4);
-            if (l == 5 && c >= Fm::kActChunks) return d_gx[s] + (uint64_t)((c - Fm::kActChunks) * 4);
-            return d_act[s] + (uint64_t)((c >> 1) * 1024 + (c & 1) * 4);
+            if (l == 0) return d_gx + (uint64_t)(s * (kGxBytes >> 4) + c * 4);
+            if (l == 5 && c >= Fm::kActChunks)
+                return d_gx + (uint64_t)(s * (kGxBytes >> 4) + (c - Fm::kActChunks) * 4);
+            return d_act + (uint64_t)(s * (kActBytes >> 4) + (c >> 1) * 1024 + (c & 1) * 4);
         };
         auto issue = [&](int l, int s, int c, uint32_t st, uint32_t idesc) {
             const uint64_t ad = a_desc(l, s, c);
@@ -914,7 +916,7 @@ __global__ void __launch_bounds__(Variant<F8, EPIW, STAG>::kThreads, 1)
         auto gate = [&]() -> bool { return !named_bar_or(1, 64, false); };
         for (long long pr = blockIdx.x; pr < n_pairs && ok; pr += gridDim.x) {
             for (int l = 0; l < kLayers && ok; ++l) {
-                const int nch = c_chunks[F8 ? 1 : 0][l];
+                const int nch = layer_chunks(F8, l);
                 const uint32_t idesc = (l == 8) ? id144 : id256;
                 if constexpr (STAG) {
                     // Staggered tiles: the layer's blocks in parts of at most
@@ -924,23 +926,68 @@ __global__ void __launch_bounds__(Variant<F8, EPIW, STAG>::kThreads, 1)
                     // runs under tile 1's last part and tile 1's under tile
                     // 0's first part of the next layer.  A stage is released
                     // after tile 1's MMAs.  (FP8: a layer is at most 5 of the
-                    // 8 stages, one part; BF16: 4-block parts.)
+                    // 8 stages, one part; BF16: 4-block parts.)  Tile 0 takes
+                    // the part's blocks in runs: each release of the gate
+                    // carries the number of consecutive blocks that have
+                    // landed (FP8; one block for BF16), all issued at once,
+                    // so that the MMA queue stays ahead of the release round
+                    // trip (a group of G MMAs leaves about G / 2 of them
+                    // queued when the issuing thread moves on).
                     for (int c0 = 0; c0 < nch && ok;) {
                         const int np = (c0 == 0 && nch % kStages) ? nch % kStages : kStages;
-                        for (int c = c0; c < c0 + np; ++c) {
-                            if (!gate()) { ok = false; break; }
-                            if (lane == 0) {
-                                tc_fence_after();
-                                issue(l, 0, c, (g + c) % kStages, idesc);
-                                if (c == nch - 1) mma_commit(smem_u32(&bars.acc_full[0]));
+                        for (int c = c0; c < c0 + np;) {
+                            if constexpr (!F8) {
+                                // one block per release: its operands and
+                                // flags computed before the wait, so that
+                                // only the MMAs follow the release
+                                const uint64_t ad = a_desc(l, 0, c);
+                                const uint64_t bd = d_ring + (uint64_t)(((g + c) % kStages) * (kStageBytes >> 4));
+                                const uint32_t accum = c ? 1u : 0u;
+                                const bool last = c == nch - 1;
+                                if (!gate()) { ok = false; break; }
+                                if (lane == 0) {
+                                    tc_fence_after();
+                                    mma_bf16(tmem, ad, bd, idesc, accum);
+                                    mma_bf16(tmem, ad + 2, bd + 2, idesc, 1u);
+                                    if (last) mma_commit(smem_u32(&bars.acc_full[0]));
+                                }
+                                __syncwarp();
+                                ++c;
+                            } else {
+                                // (the run's first operands computed before the wait)
+                                const uint64_t ad0 = a_desc(l, 0, c);
+                                const uint64_t bd0 = d_ring + (uint64_t)(((g + c) % kStages) * (kStageBytes >> 4));
+                                const int k = (int)named_bar_popc(1, 64, false);
+                                if (k < 1 || k > c0 + np - c) { ok = false; break; }
+                                if (lane == 0) {
+                                    tc_fence_after();
+                                    mma_f8(tmem, ad0, bd0, idesc, c ? 1u : 0u);
+                                    mma_f8(tmem, ad0 + 2, bd0 + 2, idesc, 1u);
+                                    if (c == nch - 1) mma_commit(smem_u32(&bars.acc_full[0]));
+                                    for (int j = 1; j < k; ++j) {
+                                        issue(l, 0, c + j, (g + c + j) % kStages, idesc);
+                                        if (c + j == nch - 1) mma_commit(smem_u32(&bars.acc_full[0]));
+                                    }
+                                }
+                                __syncwarp();
+                                c += k;
                             }
-                            __syncwarp();
                         }
                         if (!ok) break;
+                        const uint64_t ad1 = a_desc(l, 1, c0);
+                        const uint64_t bd1 = d_ring + (uint64_t)(((g + c0) % kStages) * (kStageBytes >> 4));
                         if (!gate()) { ok = false; break; }
                         if (lane == 0) {
                             tc_fence_after();
-                            for (int c = c0; c < c0 + np; ++c) {
+                            if constexpr (F8) {
+                                mma_f8(tmem + 256, ad1, bd1, idesc, c0 ? 1u : 0u);
+                                mma_f8(tmem + 256, ad1 + 2, bd1 + 2, idesc, 1u);
+                            } else {
+                                mma_bf16(tmem + 256, ad1, bd1, idesc, c0 ? 1u : 0u);
+                                mma_bf16(tmem + 256, ad1 + 2, bd1 + 2, idesc, 1u);
+                            }
+                            mma_commit(smem_u32(&bars.empty[(g + c0) % kStages]));
+                            for (int c = c0 + 1; c < c0 + np; ++c) {
                                 const uint32_t st = (g + c) % kStages;
                                 issue(l, 1, c, st, idesc);
                                 mma_commit(smem_u32(&bars.empty[st]));
@@ -954,18 +1001,23 @@ __global__ void __launch_bounds__(Variant<F8, EPIW, STAG>::kThreads, 1)
                 } else {
                     // Lockstep tiles: each weight block serves both tiles at
                     // once; the first block of a layer waits for each tile's
-                    // activations separately.
-                    for (int c = 0; c < nch; ++c, ++g) {
-                        const uint32_t st = g % kStages;
-                        if (!gate()) { ok = false; break; }
+                    // activations separately, later blocks come in runs of
+                    // landed blocks (as tile 0's in the staggered schedule).
+                    for (int c = 0; c < nch;) {
+                        const int k = (int)named_bar_popc(1, 64, false);
+                        if (k < 1 || k > nch - c) { ok = false; break; }
                         if (lane == 0) {
                             tc_fence_after();
-                            issue(l, 0, c, st, idesc);
-                            if (c == nch - 1) mma_commit(smem_u32(&bars.acc_full[0]));
-                            if (c > 0) {
-                                issue(l, 1, c, st, idesc);
-                                if (c == nch - 1) mma_commit(smem_u32(&bars.acc_full[1]));
-                                mma_commit(smem_u32(&bars.empty[st]));
+                            for (int j = 0; j < k; ++j) {
+                                const int cc = c + j;
+                                const uint32_t st = (g + cc) % kStages;
+                                issue(l, 0, cc, st, idesc);
+                                if (cc == nch - 1) mma_commit(smem_u32(&bars.acc_full[0]));
+                                if (cc > 0) {
+                                    issue(l, 1, cc, st, idesc);
+                                    if (cc == nch - 1) mma_commit(smem_u32(&bars.acc_full[1]));
+                                    mma_commit(smem_u32(&bars.empty[st]));
+                                }
                             }
                         }
                         __syncwarp();
@@ -973,13 +1025,16 @@ __global__ void __launch_bounds__(Variant<F8, EPIW, STAG>::kThreads, 1)
                             if (!gate()) { ok = false; break; }
                             if (lane == 0) {
                                 tc_fence_after();
+                                const uint32_t st = g % kStages;
                                 issue(l, 1, 0, st, idesc);
                                 if (nch == 1) mma_commit(smem_u32(&bars.acc_full[1]));
                                 mma_commit(smem_u32(&bars.empty[st]));
                             }
                             __syncwarp();
                         }
+                        c += k;
                     }
+                    g += nch;
                 }
             }
         }
@@ -995,11 +1050,11 @@ __global__ void __launch_bounds__(Variant<F8, EPIW, STAG>::kThreads, 1)
         // Waits (all lanes) for what each MMA group of the schedule needs,
         // then releases the MMA warp at named barrier 1, or stops it.
         uint32_t g = 0;
-        uint32_t rdy_ph[2] = {0, 0};
+        uint32_t rdy_ph = 0;   // bit s: phase parity of a_ready[s]
         bool ok = true;
         auto wait_ready = [&](int s) -> bool {
-            const bool r = mbar_wait(smem_u32(&bars.a_ready[s]), rdy_ph[s], abort_flag, p.wait_ns);
-            rdy_ph[s] ^= 1u;
+            const bool r = mbar_wait(smem_u32(&bars.a_ready[s]), (rdy_ph >> s) & 1u, abort_flag, p.wait_ns);
+            rdy_ph ^= 1u << s;
             return r;
         };
         auto wait_block = [&](uint32_t gi) -> bool {
@@ -1013,15 +1068,39 @@ __global__ void __launch_bounds__(Variant<F8, EPIW, STAG>::kThreads, 1)
         };
         for (long long pr = blockIdx.x; pr < n_pairs && ok; pr += gridDim.x) {
             for (int l = 0; l < kLayers && ok; ++l) {
-                const int nch = c_chunks[F8 ? 1 : 0][l];
+                const int nch = layer_chunks(F8, l);
                 if constexpr (STAG) {
                     for (int c0 = 0; c0 < nch && ok;) {
                         const int np = (c0 == 0 && nch % kStages) ? nch % kStages : kStages;
-                        for (int c = c0; c < c0 + np; ++c) {
+                        for (int c = c0; c < c0 + np;) {
+                            // wait for block c (and, for a layer's first
+                            // block, tile 0's activations); lane j > 0 tests
+                            // block c + j of the part without waiting; the
+                            // release counts the run of landed blocks from c
+                            // (0 on failure, which stops the MMA warp).
+                            // BF16: one block per release, the faster
+                            // measured (its blocks land just in time: the
+                            // 4-stage ring holds only the current part).
                             bool good = true;
                             if (c == 0) good = wait_ready(0);
                             good = good && wait_block(g + c);
-                            if (!release(good)) { ok = false; break; }
+                            if constexpr (!F8) {
+                                if (!release(good)) { ok = false; break; }
+                                ++c;
+                            } else {
+                                const int rem = c0 + np - c;
+                                bool landed = lane == 0;
+                                if (lane > 0 && lane < rem) {
+                                    const uint32_t gi = g + c + lane;
+                                    landed = mbar_try_wait(smem_u32(&bars.full[gi % kStages]), (gi / kStages) & 1u);
+                                }
+                                const uint32_t m = __ballot_sync(0xffffffffu, landed);
+                                const int k = good ? __ffs(~m) - 1 : 0;
+                                __syncwarp();
+                                named_bar_popc(1, 64, lane < k);
+                                if (!good) { ok = false; break; }
+                                c += k;
+                            }
                         }
                         if (!ok) break;
                         if (!release(c0 == 0 ? wait_ready(1) : true)) { ok = false; break; }
@@ -1029,12 +1108,29 @@ __global__ void __launch_bounds__(Variant<F8, EPIW, STAG>::kThreads, 1)
                     }
                     g += nch;
                 } else {
-                    for (int c = 0; c < nch; ++c, ++g) {
-                        bool good = wait_block(g);
+                    for (int c = 0; c < nch;) {
+                        // block c (and, for the first, tile 0's activations);
+                        // after the first, the run of landed blocks from c,
+                        // probed without waiting by lanes 1 .. (a probe stays
+                        // within the ring: block c + kStages would share
+                        // block c's stage)
+                        bool good = wait_block(g + c);
                         if (c == 0) good = good && wait_ready(0);
-                        if (!release(good)) { ok = false; break; }
+                        const int rem = c == 0 ? 1 : min(nch - c, kStages);
+                        bool landed = lane == 0;
+                        if (lane > 0 && lane < rem) {
+                            const uint32_t gi = g + c + lane;
+                            landed = mbar_try_wait(smem_u32(&bars.full[gi % kStages]), (gi / kStages) & 1u);
+                        }
+                        const uint32_t m = __ballot_sync(0xffffffffu, landed);
+                        const int k = good ? __ffs(~m) - 1 : 0;
+                        __syncwarp();
+                        named_bar_popc(1, 64, lane < k);
+                        if (!good) { ok = false; break; }
                         if (c == 0 && !release(wait_ready(1))) { ok = false; break; }
+                        c += k;
                     }
+                    g += nch;
                 }
             }
         }
@@ -1186,15 +1282,14 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kPairThreads, 1)
         const uint32_t id256 = F8 ? idesc_e4m3(256, 256) : idesc_bf16(256, 256);
         const uint32_t id144 = F8 ? idesc_e4m3(256, 144) : idesc_bf16(256, 144);
         constexpr uint16_t kBoth = 3;
-        const uint64_t d_act[2] = {smem_desc(s_act, 1024, kLayoutSw128),
-                                   smem_desc(s_act + kActBytes, 1024, kLayoutSw128)};
-        const uint64_t d_gx[2] = {smem_desc(s_gx, 1024, kLayoutSw128),
-                                  smem_desc(s_gx + kGxBytes, 1024, kLayoutSw128)};
+        const uint64_t d_act = smem_desc(s_act, 1024, kLayoutSw128);
+        const uint64_t d_gx = smem_desc(s_gx, 1024, kLayoutSw128);
         const uint64_t d_ring = smem_desc(s_ring, 512, kLayoutSw64);
         auto a_desc = [&](int l, int s, int c) -> uint64_t {
-            if (l == 0) return d_gx[s] + (uint64_t)(c * 4);
-            if (l == 5 && c >= Fm::kActChunks) return d_gx[s] + (uint64_t)((c - Fm::kActChunks) * 4);
-            return d_act[s] + (uint64_t)((c >> 1) * 1024 + (c & 1) * 4);
+            if (l == 0) return d_gx + (uint64_t)(s * (kGxBytes >> 4) + c * 4);
+            if (l == 5 && c >= Fm::kActChunks)
+                return d_gx + (uint64_t)(s * (kGxBytes >> 4) + (c - Fm::kActChunks) * 4);
+            return d_act + (uint64_t)(s * (kActBytes >> 4) + (c >> 1) * 1024 + (c & 1) * 4);
         };
         auto issue = [&](int l, int s, int c, uint32_t st, uint32_t idesc) {
             const uint64_t ad = a_desc(l, s, c);
@@ -1211,7 +1306,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kPairThreads, 1)
         auto gate = [&]() -> bool { return !named_bar_or(1, 64, false); };
         for (long long u = u0; u < n_units && ok; u += du) {
             for (int l = 0; l < kLayers && ok; ++l) {
-                const int nch = c_chunks[F8 ? 1 : 0][l];
+                const int nch = layer_chunks(F8, l);
                 const uint32_t idesc = (l == 8) ? id144 : id256;
                 if constexpr (STAG) {
                     for (int c = 0; c < nch; ++c) {
@@ -1277,11 +1372,11 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kPairThreads, 1)
         // ------------------------------------------------ gate (even CTA)
         if (rank == 0) {
             uint32_t g = 0;
-            uint32_t rdy_ph[2] = {0, 0};
+            uint32_t rdy_ph = 0;   // bit s: phase parity of a_ready[s]
             bool ok = true;
             auto wait_ready = [&](int s) -> bool {
-                const bool r = mbar_wait_cluster<false>(smem_u32(&bars.a_ready[s]), rdy_ph[s], abort_flag);
-                rdy_ph[s] ^= 1u;
+                const bool r = mbar_wait_cluster<false>(smem_u32(&bars.a_ready[s]), (rdy_ph >> s) & 1u, abort_flag);
+                rdy_ph ^= 1u << s;
                 return r;
             };
             // block gi present in both CTAs
@@ -1297,7 +1392,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kPairThreads, 1)
             };
             for (long long u = u0; u < n_units && ok; u += du) {
                 for (int l = 0; l < kLayers && ok; ++l) {
-                    const int nch = c_chunks[F8 ? 1 : 0][l];
+                    const int nch = layer_chunks(F8, l);
                     if constexpr (STAG) {
                         for (int c = 0; c < nch; ++c) {
                             bool good = true;
@@ -1676,7 +1771,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_mlp_tc_pipe(const __grid_co
             const uint32_t id256 = idesc_bf16(128, 256), id144 = idesc_bf16(128, 144);
             for (long long t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
                 for (int l = 0; l < kLayers && ok; ++l) {
-                    const int nch = c_chunks[0][l];
+                    const int nch = layer_chunks(false, l);
                     const uint32_t idesc = (l == 8) ? id144 : id256;
                     const uint32_t d = tmem + (l & 1) * 256;
                     for (int c = 0; c < nch && ok; ++c) {

@@ -124,6 +124,22 @@ __device__ __forceinline__ bool named_bar_or(uint32_t id, uint32_t nthreads, boo
     return r != 0;
 }
 
+// Named barrier `id` over `nthreads` threads (whole warps) that counts the
+// participants whose predicate is set: every participant receives the count.
+__device__ __forceinline__ uint32_t named_bar_popc(uint32_t id, uint32_t nthreads, bool pred) {
+    uint32_t r;
+    asm volatile(
+        "{\n"
+        ".reg .pred q;\n"
+        "setp.ne.u32 q, %1, 0;\n"
+        "bar.red.popc.u32 %0, %2, %3, q;\n"
+        "}\n"
+        : "=r"(r)
+        : "r"((uint32_t)pred), "r"(id), "r"(nthreads)
+        : "memory");
+    return r;
+}
+
 // ---- CTA pairs (clusters of 2) ----------------------------------------------
 // Waits on barriers that a peer CTA arrives on (release at cluster scope)
 // acquire at cluster scope; otherwise as mbar_wait / mbar_wait_sleep.
