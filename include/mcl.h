@@ -413,7 +413,7 @@ int mcl_get_map_weights(mcl_map* map, float* host_out, size_t n);
  *   3 FP8 8 lockstep    4 FP8 4 staggered   5 FP8 8 staggered
  *   6 BF16 4 split      7 BF16 4 pipelined (one tile per CTA)
  *   8 BF16 4 lockstep, CTA pair   9 FP8 4 lockstep, CTA pair
- *  10 FP8 4 staggered, CTA pair   11 BF16 4 staggered
+ *  10 FP8 4 staggered, CTA pair   11 BF16 4 staggered   12 BF16 8 staggered
  * Lockstep: each streamed weight block serves both tiles of a pair at once;
  * staggered: the second tile runs each part of a layer (the blocks the
  * weight ring holds: a whole FP8 layer, four BF16 blocks) after the first on
@@ -426,7 +426,7 @@ int mcl_get_map_weights(mcl_map* map, float* host_out, size_t n);
  * the two SMs of a TPC issue 256-row MMAs (tcgen05 cta_group::2), each CTA
  * streaming half of every weight block.  All variants of a precision give
  * bit-identical results.  Untuned defaults: 11 (BF16) and 4 (FP8). */
-#define MCL_MLP_VARIANTS 12
+#define MCL_MLP_VARIANTS 13
 
 /* Autotuner: time every variant of `precision` (MCL_PREC_BF16 or _FP8) on
  * `rows` synthetic samples (256 <= rows <= max_rays * min(64, max_samples);
@@ -466,6 +466,20 @@ int mcl_set_fused_epilogue(mcl_map* map, int enable);
 
 /* Pin the MLP kernel variant of a precision (see MCL_MLP_VARIANTS). */
 int mcl_set_mlp_variant(mcl_map* map, int precision, int variant);
+
+/* Diagnostic of the tensor-core issue path the MLP kernel's schedule is
+ * built around (no counterpart in the paper): one CTA per SM issues
+ * n_groups groups of `group` back-to-back BF16 tcgen05 MMAs (128 x 256 x 16,
+ * operands in shared memory in the MLP kernel's layouts, accumulators in
+ * TMEM) from one thread, with a dependent chain of `gap` integer
+ * multiply-adds in that thread after each group.  *clk_per_group receives
+ * the median over SMs of SM clock cycles per group, *gap_clk (optional) the
+ * cycles of one chain alone.  gap = 0 gives the per-SM MMA rate; gap > 0
+ * shows how much work a group leaves queued while the thread is busy.
+ * 1 <= group <= 64, 0 <= gap <= 4096, 1 <= n_groups <= 100000.
+ * Synchronous, on the legacy default stream; sm_103 only
+ * (MCL_ERR_UNSUPPORTED otherwise). */
+int mcl_probe_mma_rate(int group, int gap, int n_groups, double* clk_per_group, double* gap_clk);
 
 /* Phases timed when profiling is on (indices into the array of
  * mcl_profile_read). */

@@ -161,6 +161,8 @@ def lib():
             L.mcl_fit_map.argtypes = [vp, vp, vp, vp, i32, C.POINTER(FitCfg), vp, vp]
             L.mcl_map_loss_grad.argtypes = [vp, vp, vp, vp, i32, f32, vp, vp, vp]
             L.mcl_get_map_weights.argtypes = [vp, vp, C.c_size_t]
+            L.mcl_probe_mma_rate.argtypes = [i32, i32, i32, C.POINTER(C.c_double),
+                                             C.POINTER(C.c_double)]
             L.mcl_last_error.restype = C.c_char_p
             L.mcl_last_error.argtypes = []
             _lib = L
@@ -170,6 +172,14 @@ def lib():
 def _check(rc):
     if rc != MCL_OK:
         raise MclError(rc, lib().mcl_last_error().decode())
+
+
+def probe_mma_rate(group: int = 4, gap: int = 0, n_groups: int = 4000):
+    """(SM cycles per group of `group` back-to-back BF16 128x256x16 MMAs,
+    cycles of the `gap`-long chain between groups) (mcl_probe_mma_rate)."""
+    clk, gclk = C.c_double(0.0), C.c_double(0.0)
+    _check(lib().mcl_probe_mma_rate(int(group), int(gap), int(n_groups), C.byref(clk), C.byref(gclk)))
+    return clk.value, gclk.value
 
 
 def synth_blob_size(arch) -> int:
@@ -598,18 +608,19 @@ EXPORTED = ("mcl_init_map", "mcl_destroy_map", "mcl_update", "mcl_render", "mcl_
             "mcl_proposal_loss_grad", "mcl_proposal_train", "mcl_proposal_query", "mcl_autotune",
             "mcl_predict_odom",
             "mcl_set_mlp_variant", "mcl_inject_weight_stall", "mcl_set_fused_epilogue",
-            "mcl_fit_map", "mcl_map_loss_grad", "mcl_get_map_weights")
+            "mcl_fit_map", "mcl_map_loss_grad", "mcl_get_map_weights", "mcl_probe_mma_rate")
 
 # Kernel variants of the tensor-core MLP (include/mcl.h, MCL_MLP_VARIANTS):
 # (precision, epilogue warps per tile, staggered tiles)
-MLP_VARIANTS = 12
+MLP_VARIANTS = 13
 # index: (precision, epilogue warps per tile, schedule)
 MLP_VARIANT_TABLE = {0: ("bf16", 4, "lockstep"), 1: ("bf16", 8, "lockstep"),
                      2: ("fp8", 4, "lockstep"), 3: ("fp8", 8, "lockstep"),
                      4: ("fp8", 4, "staggered"), 5: ("fp8", 8, "staggered"),
                      6: ("bf16", 4, "split"), 7: ("bf16", 4, "pipelined"),
                      8: ("bf16", 4, "lockstep pair"), 9: ("fp8", 4, "lockstep pair"),
-                     10: ("fp8", 4, "staggered pair"), 11: ("bf16", 4, "staggered")}
+                     10: ("fp8", 4, "staggered pair"), 11: ("bf16", 4, "staggered"),
+                     12: ("bf16", 8, "staggered")}
 
 # Weights of the learned proposal (gamma(x) with 6 frequencies -> 4 x 64 ReLU
 # -> density): 64*39+64 + 3*(64*64+64) + 64+1.

@@ -931,8 +931,8 @@ __global__ void __launch_bounds__(Variant<F8, EPIW, STAG>::kThreads, 1)
                     // carries the number of consecutive blocks that have
                     // landed (FP8; one block for BF16), all issued at once,
                     // so that the MMA queue stays ahead of the release round
-                    // trip (a group of G MMAs leaves about G / 2 of them
-                    // queued when the issuing thread moves on).
+                    // trip (a group of G MMAs leaves only a third to a half
+                    // of them queued when the issuing thread moves on).
                     for (int c0 = 0; c0 < nch && ok;) {
                         const int np = (c0 == 0 && nch % kStages) ? nch % kStages : kStages;
                         for (int c = c0; c < c0 + np;) {
@@ -1970,6 +1970,7 @@ const TcVariant kVariants[] = {
     TcVariant{MCL_PREC_BF16, 4, false, &k_mlp_tc_pipe, kPipeThreads, kPipeSmem, 1},
     make_pair_variant<false, false>(), make_pair_variant<true, false>(),
     make_pair_variant<true, true>(),     make_variant<false, 4, true>(),
+    make_variant<false, 8, true>(),
 };
 // Fused passes (Params::fuse 1, 2) run on the single-CTA kernel with 4
 // epilogue warps per tile (the fused ray epilogues need one thread per row)
