@@ -415,6 +415,15 @@ def run_batched(M, seed, W, H, focal, use_proposal_blob=None):
     recs = M.Map.decode_log(log, Q, iters)
     lat = _update_latencies(recs[0])
     samples = sum(r["n_particles"] * r["n_pixels"] * 64 for q in range(Q) for r in recs[q])
+    # work of each update (rays of all queries) against its latency: the
+    # queries move between levels independently, so an update's work varies
+    rays = [sum(recs[q][t]["n_particles"] * recs[q][t]["n_pixels"] for q in range(Q))
+            for t in range(iters - 1)]
+    per_mray = [l / (r / 1e6) for l, r in zip(lat, rays) if r > 0]
+    corr = float(np.corrcoef(np.array(lat), np.array(rays, dtype=float))[0, 1]) if len(lat) > 2 else None
+    # least-squares latency = fixed + per-ray x rays: the fixed part is what
+    # launches, idle grid blocks and the graph's control add to an update
+    fit = np.polyfit(np.array(rays, dtype=float) / 1e6, np.array(lat), 1) if len(lat) > 2 else None
     errs = [_pose_error(recs[q][-1]["est"], synth.gt_pose(seed + 100 + q)[1],
                         synth.gt_pose(seed + 100 + q)[2]) for q in range(Q)]
     gm.close()
@@ -422,6 +431,12 @@ def run_batched(M, seed, W, H, focal, use_proposal_blob=None):
                         "100 iterations, FP8 + learned proposal (64 -> 32 + 32), one CUDA graph",
             "initial_particles": n0, "run_ms": total, "ms_per_batched_update": total / iters,
             "update_ms_p50": _pct(lat, 50), "update_ms_p99": _pct(lat, 99),
+            "rays_per_update_p50": _pct(rays, 50), "rays_per_update_p99": _pct(rays, 99),
+            "ms_per_million_rays_p50": _pct(per_mray, 50),
+            "ms_per_million_rays_p99": _pct(per_mray, 99),
+            "latency_vs_rays_correlation": corr,
+            "latency_fit_ms": ({"fixed_per_update": float(fit[1]), "per_million_rays": float(fit[0])}
+                               if fit is not None else None),
             "ray_samples_per_s": samples / (total / 1e3),
             "final_position_error_median": float(np.median([e[0] for e in errs])),
             "final_yaw_error_deg_median": float(np.median([e[1] for e in errs]))}
