@@ -148,3 +148,58 @@ def test_fitted_weights_drive_every_form(fitted, precision):
         print(f"\n{name}: gpu mean {eg.mean():.3g} max {eg.max():.3g}; "
               f"floor mean {ef.mean():.3g} max {ef.max():.3g}")
         assert eg.mean() <= 2 * ef.mean() and eg.max() <= 2 * ef.max()
+
+
+def test_adam_steps_match_the_published_update(M):
+    """Two Adam steps of mcl_fit_map over one full batch (the optimiser the
+    proposal training uses too) against Adam as Kingma and Ba define it, in
+    FP64, driven by the library's own gradients at w0 and w1 (the fit sums
+    its batch in a shuffled order, so its gradients differ from loss_grad's
+    by FP32 rounding: weights whose gradient is within 1e-5 of the layer's
+    largest of zero, where that rounding could move the step, are left out)."""
+    import torch
+    import synth
+    n = 1024
+    x, d, tgt = _points(n, 17)
+    xt, dt, tt = (torch.tensor(a, device="cuda") for a in (x, d, tgt))
+    w0 = synth.he_init_weights(6, bias_std=0.05)
+    lr, b1, b2, eps = 1e-3, 0.9, 0.999, 1e-8
+
+    def fitted(steps):
+        gm = M.Map(w0, max_rays=4096)
+        try:
+            gm.fit(xt, dt, tt, steps=steps, batch=n, lr=lr, lr_end=lr, beta1=b1, beta2=b2, eps=eps,
+                   sigma_weight=WS, seed=9)
+            return gm.weights().astype(np.float64)
+        finally:
+            gm.close()
+
+    def grad(w):
+        gm = M.Map(np.asarray(w, np.float32), max_rays=4096)
+        try:
+            return gm.loss_grad(xt, dt, tt, sigma_weight=WS)[1].cpu().numpy().astype(np.float64)
+        finally:
+            gm.close()
+
+    w1, w2 = fitted(1), fitted(2)
+    g0, g1 = grad(w0), grad(w1)
+    w0d = w0.astype(np.float64)
+    # step 1: m = (1 - b1) g, v = (1 - b2) g^2, bias-corrected by 1 - b^1
+    m = (1 - b1) * g0
+    v = (1 - b2) * g0 * g0
+    w1_ref = w0d - lr * (m / (1 - b1)) / (np.sqrt(v / (1 - b2)) + eps)
+    # step 2 from the library's w1
+    m = b1 * m + (1 - b1) * g1
+    v = b2 * v + (1 - b2) * g1 * g1
+    w2_ref = w1 - lr * (m / (1 - b1 ** 2)) / (np.sqrt(v / (1 - b2 ** 2)) + eps)
+    keep = (np.abs(g0) > 1e-5 * np.abs(g0).max()) & (np.abs(g1) > 1e-5 * np.abs(g1).max())
+    tol = 1e-3 * lr + 4 * np.spacing(np.abs(w0d).astype(np.float32)).astype(np.float64)
+    e1 = np.abs(w1 - w1_ref)[keep]
+    e2 = np.abs(w2 - w2_ref)[keep]
+    print(f"\n{keep.sum()} of {keep.size} weights: step 1 max |dw| {e1.max():.3g}, "
+          f"step 2 {e2.max():.3g} (lr {lr})")
+    assert keep.mean() > 0.95
+    assert np.all(e1 <= tol[keep])
+    assert np.all(e2 <= tol[keep])
+    # and the steps moved the weights by about lr
+    assert 0.5 * lr <= np.median(np.abs(w1 - w0d)[keep]) <= 1.01 * lr
