@@ -74,11 +74,15 @@ __global__ __launch_bounds__(256, 2) void k_sgemm(const float* __restrict__ A1, 
     const int K = K1 + K2;
     const int lr = tid >> 2, lk = (tid & 3) << 2;
     const int tx = tid & 15, ty = tid >> 4;
-    float acc[8][8];
+    // acc[p][j]: rows 2p, 2p + 1 of the thread's 8 x 8 outputs, column j;
+    // each pair is updated by one packed FP32 FMA (two independent FMAs with
+    // round-to-nearest, the arithmetic of two fmaf calls), which halves the
+    // instructions of this issue-bound loop
+    float2 acc[4][8];
 #pragma unroll
-    for (int i = 0; i < 8; ++i)
+    for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+        for (int j = 0; j < 8; ++j) acc[i][j] = make_float2(0.f, 0.f);
     float4 ra[2], rb[2];
     auto load = [&](int k0) {
 #pragma unroll
@@ -121,12 +125,15 @@ __global__ __launch_bounds__(256, 2) void k_sgemm(const float* __restrict__ A1, 
             const float4 a1 = *reinterpret_cast<const float4*>(&As[cur][kk][64 + ty * 4]);
             const float4 b0 = *reinterpret_cast<const float4*>(&Bs[cur][kk][tx * 4]);
             const float4 b1 = *reinterpret_cast<const float4*>(&Bs[cur][kk][64 + tx * 4]);
-            const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            const float2 a[4] = {make_float2(a0.x, a0.y), make_float2(a0.z, a0.w),
+                                 make_float2(a1.x, a1.y), make_float2(a1.z, a1.w)};
             const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
-            for (int i = 0; i < 8; ++i)
+            for (int j = 0; j < 8; ++j) {
+                const float2 bj = make_float2(b[j], b[j]);
 #pragma unroll
-                for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+                for (int i = 0; i < 4; ++i) acc[i][j] = __ffma2_rn(a[i], bj, acc[i][j]);
+            }
         }
         if (more) {
             // the other buffer was last read before the previous barrier
@@ -143,10 +150,11 @@ __global__ __launch_bounds__(256, 2) void k_sgemm(const float* __restrict__ A1, 
         for (int h = 0; h < 2; ++h) {
             const int col = n0 + h * 64 + tx * 4;
             float4 v;
-            v.x = acc[i][h * 4 + 0] + bias[col + 0];
-            v.y = acc[i][h * 4 + 1] + bias[col + 1];
-            v.z = acc[i][h * 4 + 2] + bias[col + 2];
-            v.w = acc[i][h * 4 + 3] + bias[col + 3];
+            const float2* ar = acc[i >> 1];
+            v.x = ((i & 1) ? ar[h * 4 + 0].y : ar[h * 4 + 0].x) + bias[col + 0];
+            v.y = ((i & 1) ? ar[h * 4 + 1].y : ar[h * 4 + 1].x) + bias[col + 1];
+            v.z = ((i & 1) ? ar[h * 4 + 2].y : ar[h * 4 + 2].x) + bias[col + 2];
+            v.w = ((i & 1) ? ar[h * 4 + 3].y : ar[h * 4 + 3].x) + bias[col + 3];
             if (RELU) {
                 v.x = fmaxf(v.x, 0.f); v.y = fmaxf(v.y, 0.f);
                 v.z = fmaxf(v.z, 0.f); v.w = fmaxf(v.w, 0.f);
