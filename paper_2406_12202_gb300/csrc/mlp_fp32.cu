@@ -31,21 +31,29 @@ __global__ void k_pe_xyz(const Ray* __restrict__ rays, const float* __restrict__
                          (double)ray.oy + zz * ((double)ray.dy + (double)ray.ly),
                          (double)ray.oz + zz * ((double)ray.dz + (double)ray.lz)};
     const double two_pi = 6.283185307179586476925286766559;
-    float* g = gx + (size_t)t * kGxPad;
-    g[0] = (float)p[0]; g[1] = (float)p[1]; g[2] = (float)p[2];
+    const double inv_two_pi = 0.15915494309189533576888376337251;
+    float v[kGxPad];
+    v[0] = (float)p[0]; v[1] = (float)p[1]; v[2] = (float)p[2];
 #pragma unroll
     for (int k = 0; k < kLxyz; ++k) {
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
+            // n = rint(a / 2 pi) from a product with 1 / (2 pi) (an n off by
+            // one leaves rr one period further, still within 2 pi of 0);
+            // a - 2 pi n is formed with a single rounding in FP64
             const double a = ldexp(p[c], k);
-            const double rr = a - two_pi * rint(a / two_pi);
+            const double rr = fma(-two_pi, rint(a * inv_two_pi), a);
             float sn, cs;
             sincosf((float)rr, &sn, &cs);
-            g[3 + 6 * k + c] = sn;
-            g[6 + 6 * k + c] = cs;
+            v[3 + 6 * k + c] = sn;
+            v[6 + 6 * k + c] = cs;
         }
     }
-    g[kGx] = 0.f;
+    v[kGx] = 0.f;
+    // the row as 16-byte stores (rows are 256 bytes, 16-byte aligned)
+    float4* g = reinterpret_cast<float4*>(gx + (size_t)t * kGxPad);
+#pragma unroll
+    for (int q = 0; q < kGxPad / 4; ++q) g[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
 }
 
 // C[M, N] = act([A1 | A2] W^T + b).  A1: [M, K1] (lda1); A2 row for output
@@ -164,38 +172,62 @@ __global__ __launch_bounds__(256, 2) void k_sgemm(const float* __restrict__ A1, 
     }
 }
 
-// sigma_raw = w_sigma . h + b_sigma, one warp per row.
+// sigma_raw = w_sigma . h + b_sigma, one half-warp per row: lane l of the
+// half takes the 16-byte groups l, l + 16, l + 32, l + 48 of the row (each
+// load instruction of the warp reads two rows' 256 contiguous bytes), then a
+// butterfly over the 16 lanes.
 __global__ void k_sigma_head(const float* __restrict__ h, int ldh, const float* __restrict__ w,
                              const float* __restrict__ b, int n, const int* __restrict__ rows_dev,
                              long r0, float4* __restrict__ out) {
-    const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (row >= rows_in_chunk(n, r0, rows_dev)) return;
-    const float* x = h + (size_t)row * ldh;
+    const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 4;
+    const int l = threadIdx.x & 15;
+    const bool live = row < rows_in_chunk(n, r0, rows_dev);
     float s = 0.f;
-    for (int k = lane; k < kWidth; k += 32) s = fmaf(w[k], x[k], s);
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) reinterpret_cast<float*>(out)[4 * (size_t)row] = s + b[0];
+    if (live) {
+        const float4* x = reinterpret_cast<const float4*>(h + (size_t)row * ldh);
+        const float4* w4 = reinterpret_cast<const float4*>(w);
+#pragma unroll
+        for (int q = 0; q < kWidth / 64; ++q) {
+            const float4 xv = x[l + 16 * q], wv = __ldg(w4 + l + 16 * q);
+            s = fmaf(wv.x, xv.x, s);
+            s = fmaf(wv.y, xv.y, s);
+            s = fmaf(wv.z, xv.z, s);
+            s = fmaf(wv.w, xv.w, s);
+        }
+    }
+    for (int o = 8; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (live && l == 0) reinterpret_cast<float*>(out)[4 * (size_t)row] = s + b[0];
 }
 
-// rgb = sigmoid(W_out h + b_out), one warp per row.
+// rgb = sigmoid(W_out h + b_out), one half-warp per row (the 128 hidden
+// values as 16-byte groups l and l + 16 of lane l).
 __global__ void k_rgb_head(const float* __restrict__ h, int ldh, const float* __restrict__ W,
                            const float* __restrict__ b, int n, const int* __restrict__ rows_dev,
                            long r0, float4* __restrict__ out) {
-    const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (row >= rows_in_chunk(n, r0, rows_dev)) return;
-    const float* x = h + (size_t)row * ldh;
+    const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 4;
+    const int l = threadIdx.x & 15;
+    const bool live = row < rows_in_chunk(n, r0, rows_dev);
     float s[3] = {0.f, 0.f, 0.f};
-    for (int k = lane; k < kRgbW; k += 32) {
-        const float xv = x[k];
+    if (live) {
+        const float4* x = reinterpret_cast<const float4*>(h + (size_t)row * ldh);
+        const float4* W4 = reinterpret_cast<const float4*>(W);
 #pragma unroll
-        for (int c = 0; c < 3; ++c) s[c] = fmaf(W[c * kRgbW + k], xv, s[c]);
+        for (int q = 0; q < kRgbW / 64; ++q) {
+            const float4 xv = x[l + 16 * q];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const float4 wv = __ldg(W4 + c * (kRgbW / 4) + l + 16 * q);
+                s[c] = fmaf(wv.x, xv.x, s[c]);
+                s[c] = fmaf(wv.y, xv.y, s[c]);
+                s[c] = fmaf(wv.z, xv.z, s[c]);
+                s[c] = fmaf(wv.w, xv.w, s[c]);
+            }
+        }
     }
 #pragma unroll
     for (int c = 0; c < 3; ++c)
-        for (int o = 16; o > 0; o >>= 1) s[c] += __shfl_xor_sync(0xffffffffu, s[c], o);
-    if (lane == 0) {
+        for (int o = 8; o > 0; o >>= 1) s[c] += __shfl_xor_sync(0xffffffffu, s[c], o);
+    if (live && l == 0) {
         float* dst = reinterpret_cast<float*>(out) + 4 * (size_t)row;
 #pragma unroll
         for (int c = 0; c < 3; ++c) dst[1 + c] = 1.0f / (1.0f + expf(-(s[c] + b[c])));
@@ -222,8 +254,8 @@ cudaError_t fp32_pe(const Ray* rays, const float* z, int n, float* gx, cudaStrea
 cudaError_t fp32_heads(const float* h, const LayerF32& sigma, const float* hid, const LayerF32& rgb,
                        int n, float4* out, cudaStream_t s) {
     note_launch(2);
-    k_sigma_head<<<(n * 32 + 255) / 256, 256, 0, s>>>(h, kWidth, sigma.W, sigma.b, n, nullptr, 0, out);
-    k_rgb_head<<<(n * 32 + 255) / 256, 256, 0, s>>>(hid, kWidth, rgb.W, rgb.b, n, nullptr, 0, out);
+    k_sigma_head<<<(n * 16 + 255) / 256, 256, 0, s>>>(h, kWidth, sigma.W, sigma.b, n, nullptr, 0, out);
+    k_rgb_head<<<(n * 16 + 255) / 256, 256, 0, s>>>(hid, kWidth, rgb.W, rgb.b, n, nullptr, 0, out);
     return cudaGetLastError();
 }
 
@@ -269,7 +301,7 @@ cudaError_t mlp_fp32(mcl_map* m, const Ray* rays, const float* gd, const float* 
         }
         // a = trunk output
         note_launch();
-        k_sigma_head<<<(n * 32 + 255) / 256, 256, 0, s>>>(a, kWidth, m->L[8].W, m->L[8].b, n,
+        k_sigma_head<<<(n * 16 + 255) / 256, 256, 0, s>>>(a, kWidth, m->L[8].W, m->L[8].b, n,
                                                           rows_dev, r0, out + r0);
         if ((e = gemm(a, kWidth, kWidth, nullptr, 0, 0, 0, 1, m->L[9], b, kWidth, n, false,
                       rows_dev, r0, s)))
@@ -279,7 +311,7 @@ cudaError_t mlp_fp32(mcl_map* m, const Ray* rays, const float* gd, const float* 
                       rows_dev, r0, s)))
             return e;
         note_launch();
-        k_rgb_head<<<(n * 32 + 255) / 256, 256, 0, s>>>(a, kWidth, m->L[11].W, m->L[11].b, n,
+        k_rgb_head<<<(n * 16 + 255) / 256, 256, 0, s>>>(a, kWidth, m->L[11].W, m->L[11].b, n,
                                                         rows_dev, r0, out + r0);
         if ((e = cudaGetLastError())) return e;
     }
