@@ -748,6 +748,24 @@ __device__ __forceinline__ void epilogue_warps(const Params& p, int warp, int wa
                     uint32_t vs;
                     tmem_ld32(t_row, va);
                     tmem_ld32(t_row + 32, vb);
+                    if constexpr (FUSE == 2) {
+                        // the ray tail's global inputs, in flight during the
+                        // RGB head: first-pass samples q = r, r + 128 of this
+                        // tile's rays and the observed colour of the ray this
+                        // warp composites
+                        const long long ray0 = (pr * unit_rows + row_base + slot * 128) / p.S;
+                        const int R1 = (128 / p.S) * p.S1;
+#pragma unroll
+                        for (int i = 0; i < 2; ++i) {
+                            const int q = (int)r + 128 * i;
+                            if (q < R1 && ray0 + q / p.S1 < n_rays) {
+                                const long long idx = (ray0 + q / p.S1) * p.S1 + q % p.S1;
+                                fz[i] = p.z_first[idx];
+                                fo[i] = p.out_first[idx];
+                            }
+                        }
+                        if (p.obs && quad < 128 / p.S && ray0 + quad < n_rays) ob = p.obs[ray0 + quad];
+                    }
                     tmem_ld_wait();
                     rgb_group<F8>(va, rb4, wo, p.ec.alpha_last, 0, o0, o1, o2);
                     rgb_group<F8>(vb, rb4, wo, p.ec.alpha_last, 1, o0, o1, o2);
@@ -781,19 +799,6 @@ __device__ __forceinline__ void epilogue_warps(const Params& p, int warp, int wa
                     good = tail_importance(p, es, scr, (int)r, lane, quad, ray0, n_rays, zrow,
                                            valid ? res.x : 0.f, dnrow);
                 } else {
-                    // first-pass samples q = r, r + 128 of this tile's rays and
-                    // the observed colour of the ray this warp composites
-                    const int R1 = (128 / p.S) * p.S1;
-#pragma unroll
-                    for (int i = 0; i < 2; ++i) {
-                        const int q = (int)r + 128 * i;
-                        if (q < R1 && ray0 + q / p.S1 < n_rays) {
-                            const long long idx = (ray0 + q / p.S1) * p.S1 + q % p.S1;
-                            fz[i] = p.z_first[idx];
-                            fo[i] = p.out_first[idx];
-                        }
-                    }
-                    if (p.obs && quad < 128 / p.S && ray0 + quad < n_rays) ob = p.obs[ray0 + quad];
                     good = tail_final(p, es, scr, (int)r, lane, quad, ray0, n_rays, zrow,
                                       valid ? res : make_float4(0.f, 0.f, 0.f, 0.f), dnrow, fz, fo, ob);
                 }
