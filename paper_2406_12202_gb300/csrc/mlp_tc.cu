@@ -1944,7 +1944,7 @@ __global__ void k_ray_bias(const float* __restrict__ gd, int n_rays, const int* 
     const float* g = gd + ray * kGdPad;
     float s = bprime[o];
 #pragma unroll
-    for (int i = 0; i < kGd; ++i) s = fmaf(Wd[o * kGd + i], g[i], s);
+    for (int i = 0; i < kGd; ++i) s = fmaf(Wd[i * 128 + o], g[i], s);   // Wd: [27][128]
     out[t] = s;
 }
 
@@ -2194,14 +2194,14 @@ int mlp_tc_prepare(mcl_map* m, const float* blob) {
     for (int n = 0; n < kRgbW; ++n) st->ec.alpha_last[n] = alpha_last[n];
     for (int c = 0; c < 3; ++c)
         for (int n = 0; n < kRgbW; ++n) st->ec.w_out[c][n] = Wp[11][(size_t)c * kRgbW + n];
-    // ---- aux (device): FP8 beta [8][256], W_d [128][27], b' [128] of the
-    //      per-ray colour bias
+    // ---- aux (device): FP8 beta [8][256], W_d transposed [27][128], b' [128]
+    //      of the per-ray colour bias
     std::vector<float> aux;
     const size_t o_beta = aux.size();
     aux.insert(aux.end(), beta.begin(), beta.end());
     const size_t o_wd = aux.size();
-    for (int o = 0; o < kRgbW; ++o)
-        for (int i = 0; i < kGd; ++i) aux.push_back(Wp[10][(size_t)o * fin[10] + kWidth + i]);
+    for (int i = 0; i < kGd; ++i)
+        for (int o = 0; o < kRgbW; ++o) aux.push_back(Wp[10][(size_t)o * fin[10] + kWidth + i]);
     const size_t o_bp = aux.size();
     for (int o = 0; o < kRgbW; ++o) aux.push_back((float)bfold[o]);
     st->b_sigma = bp[8][0];
