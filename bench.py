@@ -338,24 +338,30 @@ def run_proposal_fp8(M, gm, img, K, seed, steps, warmup, wl):
     idx = torch.empty(N, dtype=torch.int32, device="cuda")
     Pn = torch.empty_like(P)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    ms = []
-    for t in range(warmup + steps):
-        if t == warmup:
-            gm.profile_read(reset=True)
-            gm.profile(True)
-        flush.zero_()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record()
-        gm.update(P, img, K, wl["level"], pxs[t], prop, out=out)
-        gm.resample(out["w"], N, 0.5, idx=idx)
-        M.predict(P, idx, N, wl["sigma_t"], wl["sigma_yaw"], seed, t, out=Pn)
-        b.record()
-        torch.cuda.synchronize()
-        if t >= warmup:
-            ms.append(a.elapsed_time(b))
-    phases, _ = gm.profile_read(reset=True)
-    gm.profile(False)
-    mean_ms = sum(ms) / len(ms)
+    def timed_prop(fused):
+        gm.set_fused_epilogue(fused)
+        ms = []
+        for t in range(warmup + steps):
+            if t == warmup:
+                gm.profile_read(reset=True)
+                gm.profile(True)
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            gm.update(P, img, K, wl["level"], pxs[t], prop, out=out)
+            gm.resample(out["w"], N, 0.5, idx=idx)
+            M.predict(P, idx, N, wl["sigma_t"], wl["sigma_yaw"], seed, t, out=Pn)
+            b.record()
+            torch.cuda.synchronize()
+            if t >= warmup:
+                ms.append(a.elapsed_time(b))
+        phases, _ = gm.profile_read(reset=True)
+        gm.profile(False)
+        gm.set_fused_epilogue(False)
+        return sum(ms) / len(ms), phases
+
+    mean_ms, phases = timed_prop(False)
+    fused_ms, fused_phases = timed_prop(True)
     res = {"workload": "learned proposal (64 -> 32 guided + 32 importance) + FP8 MLP, "
                        "600 particles x 64 px of 400x400",
            "ms_per_step": mean_ms, "ray_samples_per_s": N * Bpx * 64 / (mean_ms / 1e3),
@@ -363,6 +369,10 @@ def run_proposal_fp8(M, gm, img, K, seed, steps, warmup, wl):
            "phases_ms_per_step": {k: v / steps for k, v in phases.items()},
            "phase_note": "sample = proposal MLP + inverse-CDF sampling; mlp_coarse = NeRF MLP on "
                          "the guided samples",
+           "ray_epilogue": "separate sampling / composite kernels (the default)",
+           "fused_epilogue": {"ms_per_step": fused_ms,
+                              "ray_samples_per_s": N * Bpx * 64 / (fused_ms / 1e3),
+                              "phases_ms_per_step": {k: v / steps for k, v in fused_phases.items()}},
            "train_s": train_s, "train_rays": 2000 * Bpx,
            "train_loss_first_last": [float(losses[0]), float(losses[-1])]}
     return res, gm.proposal_get()
@@ -877,7 +887,18 @@ def run_ours(args):
         forms[prec] = {"ms_per_step": m_, "ray_samples_per_s": N * Bpx * ns / (m_ / 1e3),
                        "speedup_vs_fp32_form": (sum(ms) / len(ms)) / m_,
                        "phases_ms_per_step": {k: v / args.steps for k, v in ph_p.items()},
+                       "ray_epilogue": "separate sampling / composite kernels (the default)",
                        "roofline": roof}
+        # the same step with the ray epilogues fused into the MLP kernel
+        # (mcl_set_fused_epilogue; opt-in: slower on GB300, less DRAM traffic)
+        gm.set_fused_epilogue(True)
+        ms_f, ph_f, _ = timed(o, args.steps, args.warmup, profile=True)
+        gm.set_fused_epilogue(False)
+        mf = sum(ms_f) / len(ms_f)
+        forms[prec]["fused_epilogue"] = {
+            "ms_per_step": mf, "ray_samples_per_s": N * Bpx * ns / (mf / 1e3),
+            "mlp_ms_per_step": (ph_f["mlp_coarse"] + ph_f["mlp_fine"]) / args.steps,
+            "phases_ms_per_step": {k: v / args.steps for k, v in ph_f.items()}}
         form_opts[prec] = o
     prop_blob = None
     if "fp8" in tc and world == 1 and not args.no_extra:

@@ -414,9 +414,11 @@ int mcl_get_map_weights(mcl_map* map, float* host_out, size_t n);
  *   6 BF16 4 split      7 BF16 4 pipelined (one tile per CTA)
  *   8 BF16 4 lockstep, CTA pair   9 FP8 4 lockstep, CTA pair
  *  10 FP8 4 staggered, CTA pair   11 BF16 4 staggered   12 BF16 8 staggered
+ *  13 BF16 4 staggered, CTA pair
  * Lockstep: each streamed weight block serves both tiles of a pair at once;
  * staggered: the second tile runs each part of a layer (the blocks the
- * weight ring holds: a whole FP8 layer, four BF16 blocks) after the first on
+ * weight ring holds: a whole FP8 layer, four BF16 blocks; with CTA pairs a
+ * whole BF16 layer but the skip layer's, run as 2 + 8 blocks) after the first on
  * the same resident blocks, so one tile's epilogue overlaps the other's
  * MMAs; split: lockstep, each layer as two
  * 128-column halves whose epilogues overlap the MMAs of the other half and
@@ -426,7 +428,7 @@ int mcl_get_map_weights(mcl_map* map, float* host_out, size_t n);
  * the two SMs of a TPC issue 256-row MMAs (tcgen05 cta_group::2), each CTA
  * streaming half of every weight block.  All variants of a precision give
  * bit-identical results.  Untuned defaults: 11 (BF16) and 4 (FP8). */
-#define MCL_MLP_VARIANTS 13
+#define MCL_MLP_VARIANTS 14
 
 /* Autotuner: time every variant of `precision` (MCL_PREC_BF16 or _FP8) on
  * `rows` synthetic samples (256 <= rows <= max_rays * min(64, max_samples);
@@ -451,7 +453,7 @@ int mcl_autotune(mcl_map* map, int precision, long long rows, int* chosen, float
  * 0 <= n_launches; 0.01 <= wait_ms <= 2000. */
 int mcl_inject_weight_stall(mcl_map* map, int n_launches, double wait_ms);
 
-/* Fused ray epilogues of the tensor-core forms (on by default): when the
+/* Fused ray epilogues of the tensor-core forms (off by default): when the
  * pass shapes allow it (n_coarse -- or n_guided with the proposal -- and
  * n_fine divide 128, and a ray's merged samples fit the kernel's staging
  * buffer), the NeRF MLP kernel's epilogue draws the importance samples of
@@ -459,9 +461,12 @@ int mcl_inject_weight_stall(mcl_map* map, int n_launches, double wait_ms);
  * (Eq. 1), applies Eq. 5 / F and the photometric E (Eq. 6), so the fine
  * pass's per-sample outputs never leave the chip.  The arithmetic is that of
  * the separate kernels in another order (warp-shuffle scans instead of one
- * thread walking a ray), so results agree to FP32 rounding.  enable = 0
- * runs the separate kernels (mcl_update, mcl_render and mcl_localize on
- * this map). */
+ * thread walking a ray), so results agree to FP32 rounding.  enable = 1
+ * fuses, enable = 0 runs the separate kernels (mcl_update, mcl_render and
+ * mcl_localize on this map).  The separate kernels are the default: on
+ * GB300 the fused form moves less data but takes 2-8 % longer per update,
+ * its ray tails running in the epilogue warps that the tensor pipe waits
+ * for. */
 int mcl_set_fused_epilogue(mcl_map* map, int enable);
 
 /* Pin the MLP kernel variant of a precision (see MCL_MLP_VARIANTS). */

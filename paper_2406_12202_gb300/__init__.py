@@ -509,7 +509,8 @@ class Map:
 
     def set_fused_epilogue(self, enable: bool):
         """Fused ray epilogues of the tensor-core forms on / off
-        (mcl_set_fused_epilogue; on by default)."""
+        (mcl_set_fused_epilogue; off by default: the separate kernels are
+        faster on GB300)."""
         _check(lib().mcl_set_fused_epilogue(self.handle, int(bool(enable))))
 
     def set_mlp_variant(self, precision: str, variant: int):
@@ -612,7 +613,7 @@ EXPORTED = ("mcl_init_map", "mcl_destroy_map", "mcl_update", "mcl_render", "mcl_
 
 # Kernel variants of the tensor-core MLP (include/mcl.h, MCL_MLP_VARIANTS):
 # (precision, epilogue warps per tile, staggered tiles)
-MLP_VARIANTS = 13
+MLP_VARIANTS = 14
 # index: (precision, epilogue warps per tile, schedule)
 MLP_VARIANT_TABLE = {0: ("bf16", 4, "lockstep"), 1: ("bf16", 8, "lockstep"),
                      2: ("fp8", 4, "lockstep"), 3: ("fp8", 8, "lockstep"),
@@ -620,7 +621,7 @@ MLP_VARIANT_TABLE = {0: ("bf16", 4, "lockstep"), 1: ("bf16", 8, "lockstep"),
                      6: ("bf16", 4, "split"), 7: ("bf16", 4, "pipelined"),
                      8: ("bf16", 4, "lockstep pair"), 9: ("fp8", 4, "lockstep pair"),
                      10: ("fp8", 4, "staggered pair"), 11: ("bf16", 4, "staggered"),
-                     12: ("bf16", 8, "staggered")}
+                     12: ("bf16", 8, "staggered"), 13: ("bf16", 4, "staggered pair")}
 
 # Weights of the learned proposal (gamma(x) with 6 frequencies -> 4 x 64 ReLU
 # -> density): 64*39+64 + 3*(64*64+64) + 64+1.

@@ -129,7 +129,7 @@ struct mcl_map {
     uint16_t* prop_packed = nullptr;   // BF16 weights of the tensor-core proposal kernel
     int* prop_abort = nullptr;         // per-launch abort flag of that kernel
     int n_sm = 0;
-    bool fuse_epilogue = true;         // tensor-core forms: fused ray epilogues
+    bool fuse_epilogue = false;        // tensor-core forms: fused ray epilogues (opt-in)
 };
 
 namespace mcl {

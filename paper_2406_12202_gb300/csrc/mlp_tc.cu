@@ -317,6 +317,22 @@ __device__ __forceinline__ float warp_sum(float v) {
     return v;
 }
 
+// cnt[t] += the number of the warp's values <= uu[t], the values being
+// vals[0 .. C-1] of every lane: each lane's values are broadcast in turn.
+template <int C>
+__device__ __forceinline__ void warp_count_le(const float (&vals)[5], const float (&uu)[4],
+                                              int (&cnt)[4]) {
+#pragma unroll 4
+    for (int src = 0; src < 32; ++src) {
+#pragma unroll
+        for (int i = 0; i < C; ++i) {
+            const float e = __shfl_sync(0xffffffffu, vals[i], src);
+#pragma unroll
+            for (int t = 0; t < 4; ++t) cnt[t] += e <= uu[t] ? 1 : 0;
+        }
+    }
+}
+
 // Staging in the tile's activation buffer.  Warp q (the warp of TMEM lane
 // quadrant q) rewrites only its own rows in the next unit's first epilogue:
 // bytes [q 4096, +4096) of each 16 KB K-block.  Ray g of a tile (at most 4)
@@ -333,40 +349,90 @@ __device__ __forceinline__ float* warp_part(float* scr, int q) {
 // ray's S samples, pdf over the interior bins (between midpoints of
 // consecutive samples) proportional to w_1 .. w_{S-2} + 1e-5, inverse CDF at
 // u_j = j / (nf - 1) (bin: first CDF entry strictly greater than u_j, linear
-// interpolation inside it).  Row thread r holds (z, sigma_raw) of row r.
-// R = 128 / S <= 4 rays per tile; one barrier.
-__device__ __forceinline__ bool tail_importance(const Params& p, EpiSync& es, float* scr, int r,
-                                                int lane, int quad, long long ray0,
-                                                long long n_rays, float z, float sg, float dn_row) {
-    const int S = p.S, R = 128 / S, nf = p.nf_out, ne = S - 1;
+// interpolation inside it).  In two steps, so that the arithmetic runs off
+// the tensor pipe's critical path:
+//   tail_importance_stage (every row thread, right after the last layer):
+//     the rows' (z, sigma_raw) meet in shared memory at one barrier and the
+//     compositing warp of each ray copies its contiguous chunk of the ray
+//     (lane l: samples l c .. l c + c - 1, c = S / 32, and the next z) into
+//     registers; the staging area may then be overwritten;
+//   tail_importance_finish (the compositing warps, once the next unit's
+//     first-layer epilogue has been signalled): the rest, from registers
+//     and warp shuffles.
+struct TailImp {
+    float zc[5];      // z of the chunk's samples and of the sample after it
+    float sc[4];      // sigma_raw of the chunk's samples
+    float dn;         // |d| of the ray
+    long long ray;    // -1: this warp composites no ray
+};
+
+// Row thread r holds (z, sigma_raw) of row r.  R = 128 / S <= 4 rays per
+// tile; one barrier.  Returns false if the barrier's wait gave up.
+__device__ __forceinline__ bool tail_importance_stage(const Params& p, EpiSync& es, float* scr, int r,
+                                                      int lane, int quad, long long ray0,
+                                                      long long n_rays, float z, float sg, float dn_row,
+                                                      TailImp& ti) {
+    const int S = p.S, R = 128 / S;
     {
-        // ray g's part: z [S], sigma [S], cdf [S], |d|
+        // ray g's part: z [S], sigma [S], |d|
         const int g = r / S, k = r - g * S;
         float* part = warp_part(scr, g);
         part[k] = z;
         part[S + k] = sg;
-        if (k == 0) part[3 * S] = dn_row;
+        if (k == 0) part[2 * S] = dn_row;
     }
+    ti.ray = -1;
     if (!es.sync()) return false;
-    if (quad >= R) return true;
-    const long long ray = ray0 + quad;
-    if (ray >= n_rays) return true;
-    float* part = warp_part(scr, quad);
-    const float* z_ = part;
-    const float* s_ = part + S;
-    float* cdf = part + 2 * S;
-    const float dn = part[3 * S];
-    const int c = (S + 31) >> 5;
-    const int k0 = lane * c, k1 = min(k0 + c, S);
+    if (quad >= R || ray0 + quad >= n_rays) return true;
+    const float* part = warp_part(scr, quad);
+    const int c = S >> 5;   // S = 32, 64, 128
+    const int k0 = lane * c;
+#pragma unroll
+    for (int i = 0; i < 5; ++i) ti.zc[i] = (i <= c && k0 + i < S) ? part[k0 + i] : 0.0f;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) ti.sc[i] = i < c ? part[S + k0 + i] : 0.0f;
+    ti.dn = part[2 * S];
+    ti.ray = ray0 + quad;
+    // the loads above are complete before any lane of this warp rewrites
+    // its rows of the buffer (the next unit's first epilogue)
+    __syncwarp();
+    return true;
+}
+
+// Entry k of values held c per lane (entry k in lane k / c, element k % c);
+// every lane takes part, each with its own k.
+__device__ __forceinline__ float warp_entry(const float (&v)[5], int c, int k) {
+    const int lc = c == 4 ? 2 : c - 1;
+    const int src = k >> lc, e = k & (c - 1);
+    float x = __shfl_sync(0xffffffffu, v[0], src);
+    if (c >= 2) {
+        const float x1 = __shfl_sync(0xffffffffu, v[1], src);
+        if (e == 1) x = x1;
+    }
+    if (c == 4) {
+        const float x2 = __shfl_sync(0xffffffffu, v[2], src);
+        const float x3 = __shfl_sync(0xffffffffu, v[3], src);
+        if (e == 2) x = x2;
+        if (e == 3) x = x3;
+    }
+    return x;
+}
+
+// The compositing warp of a ray (ti.ray >= 0), all 32 lanes.
+__device__ __forceinline__ void tail_importance_finish(const Params& p, const TailImp& ti, int lane) {
+    const int S = p.S, nf = p.nf_out, ne = S - 1;
+    const int c = S >> 5;
+    const int k0 = lane * c;
+    const float dn = ti.dn;
     float wl[4];
     float Tl = 1.0f;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         const int k = k0 + i;
         wl[i] = 0.0f;
-        if (i < c && k < k1) {
-            const float delta = (k < S - 1) ? (z_[k + 1] - z_[k]) * dn : 1e10f;
-            const float a = 1.0f - expf(-fmaxf(s_[k], 0.0f) * delta);
+        if (i < c) {
+            const float delta = (k < S - 1) ? (ti.zc[i + 1] - ti.zc[i]) * dn : 1e10f;
+            const float a = 1.0f - expf(-fmaxf(ti.sc[i], 0.0f) * delta);
             wl[i] = Tl * a;
             Tl *= 1.0f - a;
         }
@@ -377,51 +443,60 @@ __device__ __forceinline__ bool tail_importance(const Params& p, EpiSync& es, fl
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         const int k = k0 + i;
-        pl[i] = (i < c && k < k1 && k >= 1 && k <= S - 2) ? T0 * wl[i] + 1e-5f : 0.0f;
+        pl[i] = (i < c && k >= 1 && k <= S - 2) ? T0 * wl[i] + 1e-5f : 0.0f;
         psum += pl[i];
     }
     const float incl = warp_incl_sum(psum, lane);
     const float tot = __shfl_sync(0xffffffffu, incl, 31);
     float run = incl - psum;
+    // CDF entries 0 .. ne - 1 (entry 0 is 0), c per lane; +inf past the last
+    float ce[5];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) ce[i] = __int_as_float(0x7f800000);
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         const int k = k0 + i;
-        if (i < c && k < k1 && k >= 1 && k <= S - 2) {
+        if (i < c && k >= 1 && k <= S - 2) {
             run += pl[i];
-            cdf[k] = run / tot;
+            ce[i] = run / tot;
+        } else if (i < c && k == 0) {
+            ce[i] = 0.0f;
         }
     }
-    if (lane == 0) cdf[0] = 0.0f;
-    __syncwarp();
-    // lane l: outputs j = d l .. d l + d - 1 (u increasing): one binary search,
-    // then forward steps
-    const int d = (nf + 31) >> 5;
-    int idx = 0;
-    for (int t = 0; t < d; ++t) {
+    // Lane l: outputs j = d l .. d l + d - 1.  The bin of u_j, the first
+    // entry with cdf > u_j, is the number of entries <= u_j (the CDF does
+    // not decrease): each lane's entries are broadcast in turn and every
+    // lane counts them against its own u_j.
+    const int d = (nf + 31) >> 5;   // <= 4 (the launch checks nf <= 128)
+    float uu[4];
+    int cnt[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
         const int j = lane * d + t;
-        if (j >= nf) break;
-        const float u = nf > 1 ? (float)j / (float)(nf - 1) : 0.0f;
-        if (t == 0) {
-            int lo = 0, hi = ne;   // first index in [0, ne) with cdf > u, ne if none
-            while (lo < hi) {
-                const int mid = (lo + hi) >> 1;
-                if (cdf[mid] > u) hi = mid;
-                else lo = mid + 1;
-            }
-            idx = lo;
-        } else {
-            while (idx < ne && cdf[idx] <= u) ++idx;
-        }
+        uu[t] = (nf > 1 && j < nf) ? (float)j / (float)(nf - 1) : 0.0f;
+        cnt[t] = 0;
+    }
+    if (c == 1) warp_count_le<1>(ce, uu, cnt);
+    else if (c == 2) warp_count_le<2>(ce, uu, cnt);
+    else warp_count_le<4>(ce, uu, cnt);
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        if (t >= d) break;   // (d is the same in every lane)
+        const int j = lane * d + t;
+        const float u = uu[t];
+        const int idx = cnt[t];
         const int below = idx - 1 < 0 ? 0 : idx - 1;
         const int above = idx > ne - 1 ? ne - 1 : idx;
-        float denom = cdf[above] - cdf[below];
+        const float cb = warp_entry(ce, c, below), ca = warp_entry(ce, c, above);
+        const float zb0 = warp_entry(ti.zc, c, below), zb1 = warp_entry(ti.zc, c, below + 1);
+        const float za0 = warp_entry(ti.zc, c, above), za1 = warp_entry(ti.zc, c, above + 1);
+        float denom = ca - cb;
         if (denom < 1e-5f) denom = 1.0f;
-        const float tt = (u - cdf[below]) / denom;
-        const float eb = 0.5f * (z_[below] + z_[below + 1]);
-        const float ea = 0.5f * (z_[above] + z_[above + 1]);
-        p.z_out[ray * nf + j] = eb + tt * (ea - eb);
+        const float tt = (u - cb) / denom;
+        const float eb = 0.5f * (zb0 + zb1);
+        const float ea = 0.5f * (za0 + za1);
+        if (j < nf) p.z_out[ti.ray * nf + j] = eb + tt * (ea - eb);
     }
-    return true;
 }
 
 // Last pass, fused: merge each ray's S samples of this pass with the S1
@@ -664,6 +739,9 @@ __device__ __forceinline__ void epilogue_warps(const Params& p, int warp, int wa
     // of TMEM: the next unit's first MMAs then run while this unit's RGB
     // head and ray epilogue are computed.
     float nz = 0.f, ndn = 0.f;
+    // FUSE == 1: a unit's staged ray tail, finished during the next unit
+    TailImp tail_in;
+    tail_in.ray = -1;
     if (u0 < n_units) {
         prologue(u0, nz, ndn);
         signal_ready<PAIR>(bar_ready, lane);
@@ -734,6 +812,14 @@ __device__ __forceinline__ void epilogue_warps(const Params& p, int warp, int wa
                     }
                 }
                 signal_ready<PAIR>(bar_ready, lane);
+                if constexpr (FUSE == 1 && !F8) {
+                    // the previous unit's deferred ray tail (its warp's
+                    // rows: the pending state is the same in all lanes)
+                    if (l == 0 && tail_in.ray >= 0) {
+                        tail_importance_finish(p, tail_in, lane);
+                        tail_in.ray = -1;
+                    }
+                }
                 if (l == 5 && has_next) prologue(pr + du, nz, ndn);
             } else {
                 if (h0 == 0) {
@@ -796,8 +882,17 @@ __device__ __forceinline__ void epilogue_warps(const Params& p, int warp, int wa
                 const long long ray0 = (pr * unit_rows + row_base + slot * 128) / p.S;
                 bool good;
                 if constexpr (FUSE == 1) {
-                    good = tail_importance(p, es, scr, (int)r, lane, quad, ray0, n_rays, zrow,
-                                           valid ? res.x : 0.f, dnrow);
+                    // staged now; BF16: computed once the next unit's
+                    // first epilogue is signalled (at once after the last
+                    // unit), in the epilogue warps' idle time between
+                    // layers; FP8, whose epilogues bound the tensor pipe,
+                    // computes it at once (measured faster for each)
+                    good = tail_importance_stage(p, es, scr, (int)r, lane, quad, ray0, n_rays, zrow,
+                                                 valid ? res.x : 0.f, dnrow, tail_in);
+                    if (good && tail_in.ray >= 0 && (F8 || !has_next)) {
+                        tail_importance_finish(p, tail_in, lane);
+                        tail_in.ray = -1;
+                    }
                 } else {
                     good = tail_final(p, es, scr, (int)r, lane, quad, ray0, n_rays, zrow,
                                       valid ? res : make_float4(0.f, 0.f, 0.f, 0.f), dnrow, fz, fo, ob);
@@ -1194,7 +1289,6 @@ struct __align__(8) PairBars {
 template <bool F8, bool STAG>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kPairThreads, 1)
     k_mlp_tc2(const __grid_constant__ Params p) {
-    static_assert(!STAG || F8, "a BF16 layer does not fit in the weight ring");
     using Fm = Form<F8>;
     using Pf = PairForm<F8>;
     constexpr int kStages = Pf::kStages;
@@ -1314,27 +1408,43 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kPairThreads, 1)
                 const int nch = layer_chunks(F8, l);
                 const uint32_t idesc = (l == 8) ? id144 : id256;
                 if constexpr (STAG) {
-                    for (int c = 0; c < nch; ++c) {
+                    // Staggered tiles over parts of at most kStages half-blocks
+                    // (the ring holds a whole part: a whole layer but the
+                    // skip layer's, which runs as 2 + 8 blocks in BF16), each
+                    // part run by tile 0 and then by tile 1 on the same
+                    // resident blocks, so each tile's epilogue overlaps the
+                    // other tile's whole layer.  Tile 0 takes the part's
+                    // blocks in runs of landed blocks (the count the gate
+                    // releases), tile 1 the whole part at once.
+                    for (int c0 = 0; c0 < nch && ok;) {
+                        const int np = (c0 == 0 && nch % kStages) ? nch % kStages : kStages;
+                        for (int c = c0; c < c0 + np;) {
+                            const int k = (int)named_bar_popc(1, 64, false);
+                            if (k < 1 || k > c0 + np - c) { ok = false; break; }
+                            if (lane == 0) {
+                                tc_fence_after();
+                                for (int j = 0; j < k; ++j) {
+                                    issue(l, 0, c + j, (g + c + j) % kStages, idesc);
+                                    if (c + j == nch - 1) mma_commit2_mc(smem_u32(&bars.acc_full[0]), kBoth);
+                                }
+                            }
+                            __syncwarp();
+                            c += k;
+                        }
+                        if (!ok) break;
                         if (!gate()) { ok = false; break; }
                         if (lane == 0) {
                             tc_fence_after();
-                            issue(l, 0, c, (g + c) % kStages, idesc);
-                            if (c == nch - 1) mma_commit2_mc(smem_u32(&bars.acc_full[0]), kBoth);
+                            for (int c = c0; c < c0 + np; ++c) {
+                                const uint32_t st = (g + c) % kStages;
+                                issue(l, 1, c, st, idesc);
+                                mma_commit2_mc(smem_u32(&bars.empty[st]), kBoth);
+                            }
+                            if (c0 + np == nch) mma_commit2_mc(smem_u32(&bars.acc_full[1]), kBoth);
                         }
                         __syncwarp();
+                        c0 += np;
                     }
-                    if (!ok) break;
-                    if (!gate()) { ok = false; break; }
-                    if (lane == 0) {
-                        tc_fence_after();
-                        for (int c = 0; c < nch; ++c) {
-                            const uint32_t st = (g + c) % kStages;
-                            issue(l, 1, c, st, idesc);
-                            mma_commit2_mc(smem_u32(&bars.empty[st]), kBoth);
-                        }
-                        mma_commit2_mc(smem_u32(&bars.acc_full[1]), kBoth);
-                    }
-                    __syncwarp();
                     g += nch;
                 } else {
                     for (int c = 0; c < nch; ++c, ++g) {
@@ -1399,14 +1509,36 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kPairThreads, 1)
                 for (int l = 0; l < kLayers && ok; ++l) {
                     const int nch = layer_chunks(F8, l);
                     if constexpr (STAG) {
-                        for (int c = 0; c < nch; ++c) {
-                            bool good = true;
-                            if (c == 0) good = wait_ready(0);
-                            good = good && wait_block(g + c);
-                            if (!release(good)) { ok = false; break; }
+                        for (int c0 = 0; c0 < nch && ok;) {
+                            const int np = (c0 == 0 && nch % kStages) ? nch % kStages : kStages;
+                            for (int c = c0; c < c0 + np;) {
+                                // block c (and, for the layer's first, tile 0's
+                                // activations) in both CTAs; lane j > 0 probes
+                                // block c + j of the part without waiting; the
+                                // release counts the run of landed blocks (0 on
+                                // failure, which stops the MMA warp)
+                                bool good = true;
+                                if (c == 0) good = wait_ready(0);
+                                good = good && wait_block(g + c);
+                                const int rem = c0 + np - c;
+                                bool landed = lane == 0;
+                                if (lane > 0 && lane < rem) {
+                                    const uint32_t gi = g + c + lane;
+                                    const uint32_t st = gi % kStages, ph = (gi / kStages) & 1u;
+                                    landed = mbar_try_wait(smem_u32(&bars.full[st]), ph) &&
+                                             mbar_try_wait_cluster(smem_u32(&bars.pfull[st]), ph);
+                                }
+                                const uint32_t m = __ballot_sync(0xffffffffu, landed);
+                                const int k = good ? __ffs(~m) - 1 : 0;
+                                __syncwarp();
+                                named_bar_popc(1, 64, lane < k);
+                                if (!good) { ok = false; break; }
+                                c += k;
+                            }
+                            if (!ok) break;
+                            if (!release(c0 == 0 ? wait_ready(1) : true)) { ok = false; break; }
+                            c0 += np;
                         }
-                        if (!ok) break;
-                        if (!release(wait_ready(1))) { ok = false; break; }
                         g += nch;
                     } else {
                         for (int c = 0; c < nch; ++c, ++g) {
@@ -1975,7 +2107,7 @@ const TcVariant kVariants[] = {
     TcVariant{MCL_PREC_BF16, 4, false, &k_mlp_tc_pipe, kPipeThreads, kPipeSmem, 1},
     make_pair_variant<false, false>(), make_pair_variant<true, false>(),
     make_pair_variant<true, true>(),     make_variant<false, 4, true>(),
-    make_variant<false, 8, true>(),
+    make_variant<false, 8, true>(),      make_pair_variant<false, true>(),
 };
 // Fused passes (Params::fuse 1, 2) run on the single-CTA kernel with 4
 // epilogue warps per tile (the fused ray epilogues need one thread per row)
@@ -2386,6 +2518,9 @@ static cudaError_t mlp_tc_variant(mcl_map* m, int precision, int variant, const 
     p.b_out2 = st->b_out[2];
     p.out = out;
     if (fuse) {
+        // the first pass's tail writes at most 4 samples per lane (the
+        // importance samples are the last pass's S <= 128 samples)
+        if (fuse->mode == 1 && (fuse->nf_out < 1 || fuse->nf_out > 128)) return cudaErrorInvalidValue;
         p.fuse = fuse->mode;
         p.nf_out = fuse->nf_out;
         p.z_out = fuse->z_out;

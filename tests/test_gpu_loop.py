@@ -61,7 +61,17 @@ def _observation(M, gm, gt):
     return img.reshape(H, W, 3).contiguous(), K
 
 
-def test_one_iteration_equals_single_step_entry_points(M, gm):
+@pytest.fixture(params=[False, True], ids=["separate", "fused"])
+def fused(request, gm):
+    """Both ray-epilogue settings of the tensor-core forms: the separate
+    sampling / composite kernels (the default) and the fused MLP epilogue
+    (mcl_set_fused_epilogue)."""
+    gm.set_fused_epilogue(request.param)
+    yield request.param
+    gm.set_fused_epilogue(False)
+
+
+def test_one_iteration_equals_single_step_entry_points(M, gm, fused):
     import torch
     N, seed = 300, 1234
     P0, gt = _query(M, 41, N)
@@ -88,7 +98,7 @@ def test_one_iteration_equals_single_step_entry_points(M, gm):
     assert np.allclose(rec["est"][:3], est, atol=1e-5)
 
 
-def test_schedule_invariants_uneven_queries_and_graph_replay(M, gm):
+def test_schedule_invariants_uneven_queries_and_graph_replay(M, gm, fused):
     import torch
     Q, stride = 2, 700
     n0 = [700, 450]
