@@ -418,8 +418,13 @@ __device__ __forceinline__ float warp_entry(const float (&v)[5], int c, int k) {
     return x;
 }
 
-// The compositing warp of a ray (ti.ray >= 0), all 32 lanes.
-__device__ __forceinline__ void tail_importance_finish(const Params& p, const TailImp& ti, int lane) {
+// The compositing warp of a ray (ti.ray >= 0), all 32 lanes.  part: the
+// ray's staged part, still intact (the tail finishes right after the stage):
+// the CDF goes there too and the interpolation reads it and z from shared
+// memory; NULL (deferred: the part may have been overwritten): they come
+// from the lanes' registers through warp shuffles.
+__device__ __forceinline__ void tail_importance_finish(const Params& p, const TailImp& ti, int lane,
+                                                       float* part) {
     const int S = p.S, nf = p.nf_out, ne = S - 1;
     const int c = S >> 5;
     const int k0 = lane * c;
@@ -479,6 +484,13 @@ __device__ __forceinline__ void tail_importance_finish(const Params& p, const Ta
     if (c == 1) warp_count_le<1>(ce, uu, cnt);
     else if (c == 2) warp_count_le<2>(ce, uu, cnt);
     else warp_count_le<4>(ce, uu, cnt);
+    float* cdf = part ? part + 2 * S + 1 : nullptr;   // [ne] after z, sigma, |d|
+    if (part) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            if (i < c && k0 + i < ne) cdf[k0 + i] = ce[i];
+        __syncwarp();
+    }
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
         if (t >= d) break;   // (d is the same in every lane)
@@ -487,9 +499,16 @@ __device__ __forceinline__ void tail_importance_finish(const Params& p, const Ta
         const int idx = cnt[t];
         const int below = idx - 1 < 0 ? 0 : idx - 1;
         const int above = idx > ne - 1 ? ne - 1 : idx;
-        const float cb = warp_entry(ce, c, below), ca = warp_entry(ce, c, above);
-        const float zb0 = warp_entry(ti.zc, c, below), zb1 = warp_entry(ti.zc, c, below + 1);
-        const float za0 = warp_entry(ti.zc, c, above), za1 = warp_entry(ti.zc, c, above + 1);
+        float cb, ca, zb0, zb1, za0, za1;
+        if (part) {
+            cb = cdf[below]; ca = cdf[above];
+            zb0 = part[below]; zb1 = part[below + 1];
+            za0 = part[above]; za1 = part[above + 1];
+        } else {
+            cb = warp_entry(ce, c, below); ca = warp_entry(ce, c, above);
+            zb0 = warp_entry(ti.zc, c, below); zb1 = warp_entry(ti.zc, c, below + 1);
+            za0 = warp_entry(ti.zc, c, above); za1 = warp_entry(ti.zc, c, above + 1);
+        }
         float denom = ca - cb;
         if (denom < 1e-5f) denom = 1.0f;
         const float tt = (u - cb) / denom;
@@ -816,7 +835,7 @@ __device__ __forceinline__ void epilogue_warps(const Params& p, int warp, int wa
                     // the previous unit's deferred ray tail (its warp's
                     // rows: the pending state is the same in all lanes)
                     if (l == 0 && tail_in.ray >= 0) {
-                        tail_importance_finish(p, tail_in, lane);
+                        tail_importance_finish(p, tail_in, lane, nullptr);
                         tail_in.ray = -1;
                     }
                 }
@@ -890,7 +909,7 @@ __device__ __forceinline__ void epilogue_warps(const Params& p, int warp, int wa
                     good = tail_importance_stage(p, es, scr, (int)r, lane, quad, ray0, n_rays, zrow,
                                                  valid ? res.x : 0.f, dnrow, tail_in);
                     if (good && tail_in.ray >= 0 && (F8 || !has_next)) {
-                        tail_importance_finish(p, tail_in, lane);
+                        tail_importance_finish(p, tail_in, lane, F8 ? warp_part(scr, quad) : nullptr);
                         tail_in.ray = -1;
                     }
                 } else {
