@@ -619,7 +619,7 @@ def run_fitted_map(M, Q=10, iters=45, n_points=1 << 20, steps=3000, batch=16384)
     return out
 
 
-def run_pose_error(M, Q=10, iters=45):
+def run_pose_error(M, Q=20, iters=45):
     """Equal-pose-error comparison (Sec. IV-A accuracy definition: position
     error < 5 cm and rotation error < 5 deg) on the analytic room map, whose
     pose landscape has a unique optimum: Q queries from the global spread
