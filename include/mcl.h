@@ -427,7 +427,7 @@ int mcl_get_map_weights(mcl_map* map, float* host_out, size_t n);
  * at a time as the epilogue writes them; CTA pair: clusters of two CTAs on
  * the two SMs of a TPC issue 256-row MMAs (tcgen05 cta_group::2), each CTA
  * streaming half of every weight block.  All variants of a precision give
- * bit-identical results.  Untuned defaults: 11 (BF16) and 4 (FP8). */
+ * bit-identical results.  Untuned defaults: 12 (BF16) and 5 (FP8). */
 #define MCL_MLP_VARIANTS 14
 
 /* Autotuner: time every variant of `precision` (MCL_PREC_BF16 or _FP8) on

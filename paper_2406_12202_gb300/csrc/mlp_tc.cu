@@ -2136,10 +2136,14 @@ void (*const kFusedKernels[2][2])(Params) = {
     {&k_mlp_tc<true, 4, true, 1>, &k_mlp_tc<true, 4, true, 2>}};
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 static_assert(kNumVariants == MCL_MLP_VARIANTS, "variant table");
-// untuned choice per precision: BF16 4 warps staggered (fastest measured at
-// all sizes on GB300), FP8 4 warps staggered (the fused passes' kernel; 8
-// warps staggered measures about 7 % faster on plain MLP launches)
-constexpr int kDefaultVariant[3] = {-1, 11, 4};
+// untuned choice per precision: 8 epilogue warps per tile, staggered tiles
+// (the autotuner's pick on GB300 at 0.3 M and 2.5 M rows: BF16 about 1.5 %,
+// FP8 about 7 % faster than with 4 warps).
+constexpr int kDefaultVariant[3] = {-1, 12, 5};
+// The variant whose launch shape (threads, shared memory) the fused passes'
+// kernels (kFusedKernels: staggered, 4 epilogue warps per tile) share:
+// checked when the map's forms are set up.
+constexpr int kFusedVariant[3] = {-1, 11, 4};
 
 struct TcForm {
     uint8_t* wblocks = nullptr;  // weight blocks in consumption order, 64-byte swizzled
@@ -2427,11 +2431,15 @@ int mlp_tc_prepare(mcl_map* m, const float* blob) {
                                                   (int)v.smem),
                              "smem attribute")))
             return rc;
+    // the fused kernels launch with their shape variant's threads and smem
+    if (kVariants[kFusedVariant[MCL_PREC_BF16]].fn != &k_mlp_tc<false, 4, true> ||
+        kVariants[kFusedVariant[MCL_PREC_FP8]].fn != &k_mlp_tc<true, 4, true>)
+        return fail(MCL_ERR_UNSUPPORTED, "fused-pass launch shape: variant table mismatch");
     for (int f8 = 0; f8 < 2; ++f8)
         for (int mode = 0; mode < 2; ++mode)
             if ((rc = cuda_check(cudaFuncSetAttribute(kFusedKernels[f8][mode],
                                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                      (int)kVariants[kDefaultVariant[f8 + 1]].smem),
+                                                      (int)kVariants[kFusedVariant[f8 + 1]].smem),
                                  "smem attribute (fused)")))
                 return rc;
     {
@@ -2513,9 +2521,9 @@ static cudaError_t mlp_tc_variant(mcl_map* m, int precision, int variant, const 
     Params p;
     memset(&p, 0, sizeof(p));
     int vi = variant >= 0 ? variant : st->variant[precision];
-    // fused passes run on their own instantiation of the untuned single-CTA
-    // kernel (kFusedKernels)
-    if (fuse) vi = kDefaultVariant[precision];
+    // fused passes run on their own instantiations of the staggered
+    // single-CTA kernel with 4 epilogue warps per tile (kFusedKernels)
+    if (fuse) vi = kFusedVariant[precision];
     p.wblocks = precision == MCL_PREC_FP8 ? st->fp8.wblocks
                 : kVariants[vi].fn == &k_mlp_tc_split ? st->bf16_split.wblocks
                                                       : st->bf16.wblocks;
@@ -2568,7 +2576,7 @@ static cudaError_t mlp_tc_variant(mcl_map* m, int precision, int variant, const 
         --st->hold_launches;
         p.hold_weights = 1;
         p.wait_ns = st->hold_wait_ns;
-        vsel = kDefaultVariant[precision];
+        vsel = fuse ? kFusedVariant[precision] : kDefaultVariant[precision];
         p.wblocks = precision == MCL_PREC_FP8 ? st->fp8.wblocks : st->bf16.wblocks;
     }
     cudaError_t e = cudaMemsetAsync(st->abort_flag, 0, sizeof(int), s);
