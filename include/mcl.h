@@ -464,7 +464,7 @@ int mcl_inject_weight_stall(mcl_map* map, int n_launches, double wait_ms);
  * thread walking a ray), so results agree to FP32 rounding.  enable = 1
  * fuses, enable = 0 runs the separate kernels (mcl_update, mcl_render and
  * mcl_localize on this map).  The separate kernels are the default: on
- * GB300 the fused form moves less data but takes 2-8 % longer per update,
+ * GB300 the fused form moves less data but takes 4-17 % longer per update,
  * its ray tails running in the epilogue warps that the tensor pipe waits
  * for. */
 int mcl_set_fused_epilogue(mcl_map* map, int enable);
